@@ -1,0 +1,8 @@
+"""FP64 CPU oracle of the SHG split-step Fourier path and its heat loop.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py``, never by the product package.
+It is plain PyTorch CPU code in float64/complex128 and shares no code with
+the CUDA path.
+"""
+from . import ssfm, heat  # noqa: F401

@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against results fixed by the paper and by mathematics.
+
+Each test targets one piece of the oracle so that a dropped term, a wrong sign
+or a transposed operand fails at least one of them:
+
+* FFT step and K convention        -> brute-force DFT, plane-wave bin
+* initial pump (Eq. 5/6)           -> analytic Gaussian, discrete power = P1
+* diffraction (App. A, reading 1)  -> analytic Gaussian beam at z, w(z) law
+* linear absorption in L           -> Beer-Lambert
+* coupling terms (Eq. 1/2, kappa)  -> plane-wave tanh^2 law, Manley-Rowe,
+                                      Boyd-Kleinman h(sigma, xi)
+* phase sign and Dk (Eq. 3/4)      -> Boyd-Kleinman at sigma = +-0.57
+* TPA term                         -> closed-form plane-wave decay
+* temperature tables / lens phase  -> exact trilinear of affine maps,
+                                      uniform dT == shifted dk0, e^{i psi z}
+* heat solve (Eq. 16)              -> direct sparse solve, discrete eigenmode
+* heat source deposits (Eq. 8)     -> energy balance
+* gradients (autograd of the map)  -> central finite differences
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import heat, ssfm
+from tests import pins
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_values.json")
+
+
+def _p(w):
+    return ssfm.params_from_workload(w)
+
+
+# ------------------------------------------------------------------ FFT ----
+
+@pytest.mark.parametrize("shape", [(8, 8), (16, 8)])
+def test_fft_step_matches_brute_force_dft(shape):
+    rng = np.random.default_rng(3)
+    a = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    ref = pins.brute_dft2(a)
+    got = torch.fft.fft2(torch.tensor(a)).numpy()
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+    back = torch.fft.ifft2(torch.tensor(got)).numpy()
+    assert np.max(np.abs(back - a)) < 1e-13
+
+
+def test_wavenumber_bins_match_plane_waves():
+    n, L = 16, 1e-3
+    x = ssfm.axis(n, L).numpy()
+    K = ssfm.wavenumbers(n, L).numpy()
+    for b in (0, 1, 5, 8, 9, 15):
+        wave = np.exp(1j * K[b] * x)
+        spec = pins.brute_dft2(wave[None, :])[0]
+        assert np.argmax(np.abs(spec)) == b
+        assert abs(abs(spec[b]) - n) < 1e-9
+
+
+# ----------------------------------------------------------------- init ----
+
+def test_initial_pump_is_eq5_with_discrete_power():
+    w = W.plain_focused(n=64, nz=10)
+    p = _p(w)
+    A = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus).numpy()
+    x = ssfm.axis(p.nx, p.lx).numpy()
+    y = ssfm.axis(p.ny, p.ly).numpy()
+    g = pins.gaussian_beam(x, y, 0.0, w.w0, w.z_focus, p.k_f)
+    ratio = A / g
+    assert np.allclose(ratio, ratio[0, 0], rtol=1e-13, atol=0)
+    assert abs(ratio[0, 0].imag) < 1e-12 * abs(ratio[0, 0])
+    P = 0.5 * pins.EPS0 * pins.C_LIGHT * p.n_f * np.sum(np.abs(A) ** 2) * p.dx * p.dy
+    assert abs(P / w.p1 - 1) < 1e-13
+
+
+# ----------------------------------------------------------- diffraction ----
+
+def _free_run(w):
+    p = _p(w)
+    AF0 = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus)
+    AS0 = torch.zeros_like(AF0)
+    temp = ssfm.TemperatureField(p, None, 0, 0, 0.0)
+    AF, AS = ssfm.propagate(p, AF0, AS0, temp)
+    return p, AF0, AF
+
+
+def test_diffraction_reproduces_gaussian_beam():
+    w = W.plain_focused(n=128, nz=20, xi=2.84).with_(d_eff=0.0)
+    p, AF0, AF = _free_run(w)
+    x = ssfm.axis(p.nx, p.lx).numpy()
+    y = ssfm.axis(p.ny, p.ly).numpy()
+    g0 = pins.gaussian_beam(x, y, 0.0, w.w0, w.z_focus, p.k_f)
+    a0 = (AF0.numpy() / g0)[p.ny // 2, p.nx // 2]
+    ref = a0 * pins.gaussian_beam(x, y, p.L, w.w0, w.z_focus, p.k_f)
+    err = np.linalg.norm(AF.numpy() - ref) / np.linalg.norm(ref)
+    assert err < 1e-9
+    # second-moment radius w(z)^2 = 2 <r^2>
+    I = np.abs(AF.numpy()) ** 2
+    r2 = x[None, :] ** 2 + y[:, None] ** 2
+    wz = math.sqrt(2 * np.sum(r2 * I) / np.sum(I))
+    z_r = w.w0 ** 2 * p.k_f / 2
+    assert abs(wz / (w.w0 * math.sqrt(1 + ((p.L - w.z_focus) / z_r) ** 2)) - 1) < 1e-6
+    # unitary propagator
+    P0 = ssfm.power(AF0, p.n_f, p.dx, p.dy)
+    P1 = ssfm.power(AF, p.n_f, p.dx, p.dy)
+    assert abs(float(P1 / P0) - 1) < 1e-13
+
+
+def test_beer_lambert_decay_of_both_waves():
+    w = W.plain_focused(n=32, nz=40).with_(d_eff=0.0, alpha_f=7.0, alpha_sh=19.0)
+    p = _p(w)
+    AF0 = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus)
+    AS0 = 0.3 * AF0.roll(3, 1)
+    temp = ssfm.TemperatureField(p, None, 0, 0, 0.0)
+    AF, AS = ssfm.propagate(p, AF0, AS0, temp)
+    for A0, A, n, a in ((AF0, AF, p.n_f, p.alpha_f), (AS0, AS, p.n_sh, p.alpha_sh)):
+        ratio = float(ssfm.power(A, n, p.dx, p.dy) / ssfm.power(A0, n, p.dx, p.dy))
+        assert abs(ratio / math.exp(-a * p.L) - 1) < 1e-12
+
+
+# -------------------------------------------------------------- coupling ----
+
+def _uniform_run(w, AF0, AS0):
+    p = _p(w)
+    temp = ssfm.TemperatureField(p, None, 0, 0, w.t_off)
+    return p, ssfm.propagate(p, AF0, AS0, temp)
+
+
+def test_plane_wave_conversion_follows_tanh_squared():
+    w = W.plain_focused(n=8, nz=1000)
+    p = _p(w)
+    gamma_L = 1.5
+    a0 = gamma_L / (p.L * math.sqrt(p.kappa_f * p.kappa_sh))
+    AF0 = torch.full((8, 8), a0, dtype=torch.complex128)
+    AS0 = torch.zeros_like(AF0)
+    p, (AF, AS) = _uniform_run(w, AF0, AS0)
+    eta = float(ssfm.power(AS, p.n_sh, p.dx, p.dy) / ssfm.power(AF0, p.n_f, p.dx, p.dy))
+    assert abs(eta - math.tanh(gamma_L) ** 2) < 1e-10
+
+
+def test_manley_rowe_without_losses():
+    """P_F + P_SH is conserved up to the RK4 error, which falls as dz^4."""
+    def defect(w):
+        AF, AS, eta = ssfm.run(w)
+        p = _p(w)
+        tot = float(ssfm.power(AF, p.n_f, p.dx, p.dy) + ssfm.power(AS, p.n_sh, p.dx, p.dy))
+        assert float(eta) > 0.01
+        return abs(tot / w.p1 - 1)
+
+    assert defect(W.plain_focused(n=32, nz=100)) < 1e-10
+    lossless = W.depleted_absorbing(n=32, nz=100, tgrid=(16, 16, 24)).with_(
+        alpha_f=0.0, alpha_sh=0.0, beta_sh=0.0)
+    e100 = defect(lossless)
+    e200 = defect(lossless.with_(nz=200))
+    assert e200 < 1e-10
+    assert e100 / e200 > 10.0
+
+
+@pytest.mark.parametrize("xi,sigma", [(2.84, 0.0), (2.84, 0.5736), (2.84, -0.5736),
+                                      (1.0, 0.5736)])
+def test_boyd_kleinman_undepleted(xi, sigma):
+    """Eq. (17) with h(sigma, xi) from independent quadrature.  BK assume the
+    harmonic diffracts like the driving polarisation (k_SH = 2 k_F), so the pin
+    uses n_SH = n_F; sigma = b Dk / 2 with b = L / xi."""
+    w = W.plain_focused(n=128, nz=100, xi=xi, undepleted=True).with_(n_sh=W.N_F)
+    b = w.L / xi
+    w = w.with_(dk0=2 * sigma / b)
+    _, _, eta = ssfm.run(w)
+    ref = pins.bk_constant(w.d_eff, w.L, w.n_f, w.n_sh, w.lambda_f) * w.p1 * pins.bk_h(sigma, xi)
+    assert abs(float(eta) / ref - 1) < 5e-4
+
+
+def test_paper_optimum_focusing_from_bk_quadrature():
+    """The paper's optimum xi = 2.84 (Sec. 5.1) and 29 um waist pin the BK
+    reference and the xi = L/(2 z_R) convention."""
+    gold = json.load(open(GOLDEN))
+    from scipy.optimize import minimize_scalar
+
+    def hmax(xi):
+        r = minimize_scalar(lambda s: -pins.bk_h(s, xi), bounds=(0, 2), method="bounded",
+                            options={"xatol": 1e-7})
+        return -r.fun
+
+    r = minimize_scalar(lambda xi: -hmax(xi), bounds=(1.5, 4.5), method="bounded",
+                        options={"xatol": 1e-4})
+    assert abs(r.x - gold["xi_opt"]["value"]) < 0.01
+    assert abs(-r.fun - 1.068) < 1e-3
+    w0 = W.waist_for_xi(gold["xi_opt"]["value"], gold["crystal_length_m"]["value"])
+    assert abs(w0 * 1e6 - gold["w_F_at_xi_opt_um"]["value"]) < 0.5
+    # h(0, xi) = arctan(xi)^2 / xi in closed form
+    assert abs(pins.bk_h(0.0, 2.84) - math.atan(2.84) ** 2 / 2.84) < 1e-10
+
+
+def test_two_photon_absorption_closed_form():
+    """Uniform SH only, alpha_SH and beta_SH: second-order convergence to
+    I0 e^{-a z} / (1 + b I0 (1 - e^{-a z}) / a)."""
+    errs = []
+    for nz in (50, 100):
+        w = W.plain_focused(n=8, nz=nz).with_(alpha_sh=20.0, beta_sh=2e-12)
+        p = _p(w)
+        a = 3e7
+        AF0 = torch.zeros((8, 8), dtype=torch.complex128)
+        AS0 = torch.full((8, 8), a, dtype=torch.complex128)
+        p, (AF, AS) = _uniform_run(w, AF0, AS0)
+        I0 = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * p.n_sh * a * a
+        I = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * p.n_sh * float(AS[0, 0].abs() ** 2)
+        ref = pins.tpa_plane_wave(I0, p.alpha_sh, p.beta_sh, p.L)
+        assert ref < 0.5 * I0   # strong absorption regime
+        errs.append(abs(I / ref - 1))
+    assert errs[1] < 1e-5
+    assert 3.5 < errs[0] / errs[1] < 4.5
+
+
+# ------------------------------------------------------------ temperature ----
+
+def test_trilinear_tables_exact_for_affine_maps():
+    w = W.plain_focused(n=16, nz=10)
+    p = _p(w)
+    tx, ty, tz = 5, 6, 7
+    t_lx, t_ly = 1.5 * p.lx, 1.5 * p.ly
+    X = -t_lx / 2 + np.arange(tx) * t_lx / (tx - 1)
+    Y = -t_ly / 2 + np.arange(ty) * t_ly / (ty - 1)
+    Z = np.arange(tz) * p.L / (tz - 1)
+    a, bx, cy, dz = 0.3, 1.7e3, -2.1e3, 40.0
+    dT = a + bx * X[None, None, :] + cy * Y[None, :, None] + dz * Z[:, None, None]
+    temp = ssfm.TemperatureField(p, torch.tensor(dT), t_lx, t_ly, 0.0)
+    x = ssfm.axis(p.nx, p.lx).numpy()
+    y = ssfm.axis(p.ny, p.ly).numpy()
+    for z in (0.0, 0.3 * p.L, Z[3], p.L):
+        d, c = temp.at(z)
+        ref = a + bx * x[None, :] + cy * y[:, None] + dz * z
+        assert np.max(np.abs(d.numpy() - ref)) < 1e-12
+    # the trapezoid cumulative integral of a linear-in-z map is exact at nodes
+    d, c = temp.at(Z[4])
+    refc = (a + bx * x[None, :] + cy * y[:, None]) * Z[4] + dz * Z[4] ** 2 / 2
+    assert np.max(np.abs(c.numpy() - refc)) < 1e-12
+
+
+def test_uniform_temperature_equals_shifted_mismatch():
+    base = W.plain_focused(n=32, nz=30).with_(ddk_dT=-0.6 * 300, dn_dT=0.0)
+    c = 1.7
+    m = np.full((3, 4, 5), c)
+    with_map = base.with_(dT=m, t_lx=base.lx, t_ly=base.ly)
+    shifted = base.with_(dk0=base.dk0 + base.ddk_dT * c, ddk_dT=0.0)
+    offset = base.with_(t_off=c)
+    _, AS1, e1 = ssfm.run(with_map)
+    _, AS2, e2 = ssfm.run(shifted)
+    _, AS3, e3 = ssfm.run(offset)
+    assert abs(float(e1) / float(e2) - 1) < 1e-12
+    assert abs(float(e3) / float(e2) - 1) < 1e-12
+    assert abs(float(e2) / float(ssfm.run(base)[2]) - 1) > 1e-3   # the shift matters
+
+
+def test_uniform_lens_phase_rotates_fields():
+    w = W.plain_focused(n=32, nz=100).with_(d_eff=0.0, dn_dT=1e-5)
+    c = 2.0
+    _, AF_free = _free_run(w)[0], _free_run(w)[2]
+    AF, _, _ = ssfm.run(w.with_(t_off=c))
+    k0 = 2 * math.pi / w.lambda_f
+    ref = AF_free * np.exp(1j * k0 * w.dn_dT * c * w.L)
+    err = float((AF - ref).abs().max() / ref.abs().max())
+    assert err < 1e-8
+
+
+# ------------------------------------------------------------------ heat ----
+
+def _assemble(hx, hy, hz, dx, dy, dz):
+    import scipy.sparse as sp
+    n = (hz - 2) * (hy - 2) * (hx - 2)
+    idx = -np.ones((hz, hy, hx), dtype=np.int64)
+    idx[1:-1, 1:-1, 1:-1] = np.arange(n).reshape(hz - 2, hy - 2, hx - 2)
+    rows, cols, vals = [], [], []
+    for l in range(1, hz - 1):
+        for j in range(1, hy - 1):
+            for i in range(1, hx - 1):
+                r = idx[l, j, i]
+                rows.append(r); cols.append(r)
+                vals.append(-2 / dx ** 2 - 2 / dy ** 2 - 2 / dz ** 2)
+                for (ll, jj, ii, d) in ((l, j, i + 1, dx), (l, j, i - 1, dx), (l, j + 1, i, dy),
+                                        (l, j - 1, i, dy), (l + 1, j, i, dz), (l - 1, j, i, dz)):
+                    if idx[ll, jj, ii] >= 0:
+                        rows.append(r); cols.append(idx[ll, jj, ii]); vals.append(1 / d ** 2)
+    return sp.csr_matrix((vals, (rows, cols)), shape=(n, n)), idx
+
+
+def test_sor_matches_direct_sparse_solve():
+    from scipy.sparse.linalg import spsolve
+    hx, hy, hz = 10, 8, 12
+    wx, wy, L, kappa = 2e-3, 1e-3, 0.03, 8.4
+    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    rng = np.random.default_rng(5)
+    q = rng.uniform(0, 1e8, size=(hz, hy, hx))
+    T, sweeps, corr = heat.sor_solve(torch.tensor(q), kappa, wx, wy, L, tol=1e-13)
+    A, idx = _assemble(hx, hy, hz, dx, dy, dz)
+    sol = spsolve(A.tocsc(), -q[1:-1, 1:-1, 1:-1].ravel() / kappa)
+    ref = np.zeros_like(q)
+    ref[1:-1, 1:-1, 1:-1] = sol.reshape(hz - 2, hy - 2, hx - 2)
+    assert np.max(np.abs(T.numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+    assert 1 < sweeps < 5000
+
+
+def test_sor_recovers_discrete_eigenmode():
+    hx, hy, hz = 17, 9, 33
+    wx, wy, L, kappa = 2e-3, 1e-3, 0.03, 8.4
+    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    X = np.arange(hx) * dx
+    Y = np.arange(hy) * dy
+    Z = np.arange(hz) * dz
+    mode = (np.sin(np.pi * Z / L)[:, None, None] * np.sin(np.pi * Y / wy)[None, :, None]
+            * np.sin(np.pi * X / wx)[None, None, :])
+    lam = pins.discrete_laplacian_eigen(hx, hy, hz, dx, dy, dz)
+    q = -kappa * lam * 3.0 * mode       # kappa lap T + q = 0 for T = 3 * mode
+    T, _, _ = heat.sor_solve(torch.tensor(q), kappa, wx, wy, L, tol=1e-12)
+    assert np.max(np.abs(T.numpy() - 3.0 * mode)) < 1e-9
+
+
+def test_heat_deposits_balance_absorbed_power():
+    """P_in - P_out = sum of deposited q_dot dV, to the trapezoid rule's O(dz^2)."""
+    errs = []
+    for nz in (40, 80):
+        w = W.plain_focused(n=32, nz=nz, p1=2e3).with_(alpha_f=5.0, alpha_sh=30.0,
+                                                      beta_sh=5e-12, beta_f=1e-12)
+        p = _p(w)
+        dep = ssfm.HeatDeposit(p, 9, 9, 11, p.lx, p.ly)
+        AF, AS, eta = ssfm.run(w, deposit=dep)
+        lost = w.p1 - float(ssfm.power(AF, p.n_f, p.dx, p.dy) + ssfm.power(AS, p.n_sh, p.dx, p.dy))
+        assert float(eta) > 1e-3 and lost > 0.05 * w.p1
+        errs.append(abs(float(dep.Q.sum()) / lost - 1))
+    assert errs[1] < 1e-3
+    assert 3.5 < errs[0] / errs[1] < 5.0
+
+
+# ------------------------------------------------------------- gradients ----
+
+def _grad_case():
+    w = W.depleted_absorbing(n=16, nz=12, tgrid=(5, 6, 7), xi=2.0, p1=400.0)
+    return w.with_(t_off=0.3, ddk_dT=-60.0, dn_dT=3e-4)
+
+
+def _eta(w, w0, zf, toff, dT):
+    return ssfm.run(w, w0=w0, z_focus=zf, t_off=toff, dT=dT)[2]
+
+
+def test_autograd_gradients_match_central_differences():
+    w = _grad_case()
+    dT0 = torch.tensor(w.dT, dtype=torch.float64)
+    w0 = torch.tensor(w.w0, dtype=torch.float64, requires_grad=True)
+    zf = torch.tensor(w.z_focus, dtype=torch.float64, requires_grad=True)
+    to = torch.tensor(w.t_off, dtype=torch.float64, requires_grad=True)
+    dT = dT0.clone().requires_grad_(True)
+    eta = _eta(w, w0, zf, to, dT)
+    g_w0, g_zf, g_to, g_dT = torch.autograd.grad(eta, (w0, zf, to, dT))
+    # invariant: the oven offset enters as a uniform dT
+    assert abs(float(g_to) - float(g_dT.sum())) < 1e-10 * float(g_dT.abs().sum())
+
+    def fd(fun, x, h):
+        return (float(fun(x + h)) - float(fun(x - h))) / (2 * h)
+
+    with torch.no_grad():
+        cases = [
+            (g_w0, fd(lambda v: _eta(w, v, w.z_focus, w.t_off, dT0), w.w0, 1e-4 * w.w0)),
+            (g_zf, fd(lambda v: _eta(w, w.w0, v, w.t_off, dT0), w.z_focus, 1e-4 * w.z_focus)),
+            (g_to, fd(lambda v: _eta(w, w.w0, w.z_focus, v, dT0), w.t_off, 1e-4)),
+        ]
+        rng = np.random.default_rng(7)
+        d = torch.tensor(rng.normal(size=tuple(dT0.shape)))
+        cases.append(((g_dT * d).sum(),
+                      fd(lambda s: _eta(w, w.w0, w.z_focus, w.t_off, dT0 + s * d), 0.0, 1e-4)))
+    for g, ref in cases:
+        assert abs(float(g) - ref) <= 1e-6 * abs(ref) + 1e-12
