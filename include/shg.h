@@ -1,0 +1,189 @@
+/*
+ * shg.h - C ABI of the GB300 split-step Fourier SHG library (libshg.so).
+ *
+ * The library propagates the coupled fundamental (F) and second-harmonic (SH)
+ * envelopes A_F(x,y,z), A_SH(x,y,z) of focused-Gaussian-beam SHG through a
+ * chi(2) crystal, as posed in arXiv 2410.04994 ("CUDA-based focused Gaussian
+ * beams second-harmonic generation efficiency calculator"):
+ *
+ *   coupled-wave equations ............ Sec. 2.1, Eqs. (1)-(4)
+ *   focused Gaussian input ............ Eqs. (5)-(6)
+ *   operator form and split step ...... Sec. 3.1, Eqs. (11)-(15)
+ *   K-space diffraction ............... App. A, Eqs. (A.1)-(A.5)
+ *   heat equation and its FD form ..... Sec. 2.2 Eqs. (7)-(9), Sec. 3.2 Eq. (16)
+ *   self-consistent loop .............. Fig. 2 (Sec. 4.2)
+ *   efficiency ........................ Eq. (17)
+ *
+ * Discrete map (shared with the FP64 oracle that the tests compare against):
+ * every z-step of length dz = L/nz is N(dz/2) L(dz) N(dz/2); N(h) is one RK4
+ * step of the pointwise three-wave right-hand side
+ *     dA_F/dz  = i kF A_SH conj(A_F) e^{-i phi} - (1/2) beta_F I_F A_F + i psi_F A_F
+ *     dA_SH/dz = i kS A_F^2 e^{+i phi}          - (1/2) beta_SH I_SH A_SH + i psi_SH A_SH
+ * with kF = 2 pi d/(n_F lambda_F), kS = 2 pi d/(n_SH lambda_F), I = eps0 c n |A|^2/2,
+ * phi = (dk0 + g T_off) z + g C(x,y,z) (C = cumulative trapezoid integral of the
+ * temperature map along z, g = dDk/dT) and psi_j = (2 pi/lambda_j)(dn/dT)(dT + T_off);
+ * L(dz) multiplies the 2-D spectrum by exp(-i K^2 dz/(2 k_j)) exp(-alpha_j dz/2).
+ *
+ * Conventions for every entry point:
+ *   - Units are SI.  Fields are complex, stored [ny][nx] with x fastest, as
+ *     float2 (default) or double2 (SHG_FLAG_FP64) pairs (re, im).
+ *   - Pointers named *_dev are device pointers; the caller owns them and they
+ *     are only borrowed for the duration of the call.  Everything else the
+ *     plan needs (fields, tables, checkpoints, scratch) is allocated by
+ *     shg_plan_create / shg_set_temperature and owned by the plan.
+ *   - Work is enqueued on the caller's stream (a cudaStream_t; NULL is the
+ *     legacy default stream).  Calls that return host values synchronise that
+ *     stream.
+ *   - Every call returns a status.  Nothing exits or traps; a failed call
+ *     leaves the plan usable (its state is whatever the last successful call
+ *     left).
+ */
+#ifndef SHG_H
+#define SHG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *shg_stream_t; /* == cudaStream_t */
+
+typedef enum {
+    SHG_OK = 0,
+    SHG_ERR_INVALID_ARG = 1,      /* NULL pointer, non-positive size, inconsistent params */
+    SHG_ERR_UNSUPPORTED_GRID = 2, /* nx, ny not powers of two in [8, 1024] (FP64: [8, 256]) */
+    SHG_ERR_OOM = 3,              /* a device allocation failed */
+    SHG_ERR_CUDA = 4,             /* a CUDA runtime call failed (text: shg_last_error) */
+    SHG_ERR_TIMEOUT = 5,          /* a bounded device-side wait gave up */
+    SHG_ERR_NONFINITE = 6,        /* a power or efficiency came out NaN/Inf */
+    SHG_ERR_STATE = 7             /* call out of order (e.g. adjoint before a forward pass) */
+} shg_status_t;
+
+/* Transverse grid nx x ny over a window lx x ly (x_m = (m - nx/2) lx/nx),
+ * nz steps over the crystal length, and an optional heat grid of hx x hy x hz
+ * nodes including the faces (0 = no heat grid) spanning the crystal
+ * [-wx/2, wx/2] x [-wy/2, wy/2] x [0, L]. */
+typedef struct {
+    int nx, ny, nz;
+    double lx, ly;
+    int hx, hy, hz;
+} shg_grid_t;
+
+/* Crystal: length L, pump wavelength lambda_F (SH at lambda_F/2), indices,
+ * d_eff, linear (1/m, power) and two-photon (m/W) absorption of each wave,
+ * cold mismatch dk0 (1/m), its temperature slope dDk/dT (1/(m K)), the
+ * thermo-optic coefficient dn/dT (1/K, both waves), thermal conductivity
+ * kappa_th (W/(m K)) and the transverse size wx x wy used by the heat grid. */
+typedef struct {
+    double L, lambda_f, n_f, n_sh, d_eff;
+    double alpha_f, alpha_sh, beta_f, beta_sh;
+    double dk0, ddk_dT, dn_dT;
+    double kappa_th, wx, wy;
+} shg_crystal_t;
+
+/* Beams: pump power P1 (W), waist w0 (m), focus position z_focus (m from the
+ * entrance face), oven offset T_off (K, a uniform dT), and the undepleted-pump
+ * switch of Sec. 5.1 (drops only the coupling term of the pump equation). */
+typedef struct {
+    double p1, w0, z_focus, t_oven_offset;
+    int undepleted;
+} shg_beams_t;
+
+enum {
+    SHG_FLAG_FP64 = 1,    /* fields and arithmetic in double precision */
+    SHG_FLAG_THERMAL = 2, /* deposit q_dot (Eq. 8) on the heat grid while propagating */
+    SHG_FLAG_ADJOINT = 4  /* keep sqrt(nz)-spaced checkpoints for shg_propagate_adjoint */
+};
+
+typedef struct shg_plan shg_plan_t;
+
+/* Create a plan (Sec. 4: the Efields / Tfield / PhaseMatching state of the
+ * paper as one object).  Validates the grid, allocates the device state and
+ * the twiddle / propagator / phase tables (FP64-computed, rounded once).
+ * On error *out is NULL. */
+shg_status_t shg_plan_create(const shg_grid_t *grid, const shg_crystal_t *crystal,
+                             const shg_beams_t *beams, int flags, shg_plan_t **out);
+
+/* Release every device buffer of the plan.  NULL is accepted. */
+shg_status_t shg_plan_destroy(shg_plan_t *plan);
+
+/* Replace the beam parameters (Eq. 5/6 inputs, T_off, undepleted switch) and
+ * drop any fields set by shg_set_fields.  Grid and crystal are unchanged. */
+shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
+
+/* Temperature map dT (K, relative to the oven) on a node-centred grid
+ * dT_dev[tz][ty][tx] (float, device) spanning [-t_lx/2, t_lx/2] x
+ * [-t_ly/2, t_ly/2] x [0, L]; t_lx or t_ly <= 0 means the field window.
+ * Copied into the plan together with its cumulative z-integral (Eq. 3,
+ * trapezoid on the nodes).  tx, ty, tz >= 2.  dT_dev == NULL clears the map
+ * (uniform temperature T_off). */
+shg_status_t shg_set_temperature(shg_plan_t *plan, const float *dT_dev, int tx, int ty,
+                                 int tz, double t_lx, double t_ly, shg_stream_t stream);
+
+/* Use the given fields (device, [ny][nx], the plan's precision) as the state
+ * at z = 0 instead of the Gaussian pump of Eq. (6) and a zero SH.  Either
+ * pointer may be NULL (zero field). */
+shg_status_t shg_set_fields(shg_plan_t *plan, const void *a_f_dev, const void *a_sh_dev,
+                            shg_stream_t stream);
+
+/* Propagate z = 0 -> L (Eq. 15 marched nz times, Fig. 2 "Compute CWEs"):
+ * initial fields, 2 nz + 1 fused passes, and the FP64 power reductions.
+ * Asynchronous on `stream`. */
+shg_status_t shg_propagate(shg_plan_t *plan, shg_stream_t stream);
+
+/* eta = P_SH(L)/P1 and the powers P_F(L), P_SH(L) (W) of the last
+ * propagation (Eq. 17 with discrete powers (1/2) eps0 c n sum|A|^2 dx dy).
+ * Synchronises the stream of the last propagation.  Any output may be NULL. */
+shg_status_t shg_efficiency(shg_plan_t *plan, double *eta, double *p_f, double *p_sh);
+
+/* Copy the current fields (device, [ny][nx], the plan's precision) out. */
+shg_status_t shg_get_fields(shg_plan_t *plan, void *a_f_dev, void *a_sh_dev,
+                            shg_stream_t stream);
+
+/* Reverse sweep of the exact discrete forward map (conjugate propagator,
+ * transposed RK4 with Wirtinger calculus), seeded with d_eta = dJ/deta, using
+ * the sqrt(nz) checkpoints of the last shg_propagate (needs SHG_FLAG_ADJOINT).
+ * Outputs d_eta * deta/dw0, deta/dz_focus, deta/dT_off (host doubles) and
+ * deta/d(dT node) into g_dT_dev[tz][ty][tx] (device float, may be NULL).
+ * Grid and window are held fixed.  Synchronises `stream`. */
+shg_status_t shg_propagate_adjoint(shg_plan_t *plan, double d_eta, double *g_w0,
+                                   double *g_zf, double *g_toven, float *g_dT_dev,
+                                   shg_stream_t stream);
+
+/* Propagate n independent plans together (a focusing / power / oven sweep):
+ * the plans are grouped by grid, and the whole sweep runs as one CUDA-graph
+ * launch (captured on first use of this plan set and reused).  Writes
+ * eta_host_out[n] and synchronises `stream`. */
+shg_status_t shg_batch_submit(shg_plan_t *const *plans, int n, double *eta_host_out,
+                              shg_stream_t stream);
+
+/* Solve kappa lap dT = -q_dot (Eq. 7/16, Dirichlet dT = 0 on all faces) on
+ * the heat grid by red-black SOR from the q_dot deposited by the last
+ * THERMAL propagation, until the largest Jacobi correction is below tol (K)
+ * or max_sweeps sweeps.  Installs dT as the plan's temperature map.
+ * Returns the final correction and sweep count.  Synchronises `stream`. */
+shg_status_t shg_heat_solve(shg_plan_t *plan, int max_sweeps, double tol, double *resid,
+                            int *sweeps, shg_stream_t stream);
+
+/* The self-consistent loop of Fig. 2 with n_outer fixed iterations:
+ * q_dot = 0 -> dT -> (Dk, lens) -> propagate (depositing q_dot) -> ...
+ * eta_out[i] and change_out[i] = max|dT_i - dT_{i-1}| per iteration (host
+ * arrays of n_outer doubles, may be NULL).  Needs SHG_FLAG_THERMAL. */
+shg_status_t shg_thermal_loop(shg_plan_t *plan, int n_outer, int max_sweeps, double tol,
+                              double *eta_out, double *change_out, shg_stream_t stream);
+
+/* Heat-grid state for inspection: the deposited heat per node q_dev (W, the
+ * sum of q_dot dV, double [hz][hy][hx]) and the last solved dT (float).
+ * Either pointer may be NULL. */
+shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
+                          shg_stream_t stream);
+
+/* Static description of a status code. */
+const char *shg_status_string(shg_status_t status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char *shg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SHG_H */

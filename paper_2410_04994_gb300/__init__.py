@@ -1,0 +1,292 @@
+"""GB300 split-step Fourier SHG library: thin Python binding of libshg.so.
+
+Every function named ``shg_*`` here marshals its arguments and calls the C
+entry point of the same name declared in ``include/shg.h``; all arithmetic of
+the propagation runs in the library's CUDA kernels.  PyTorch supplies device
+memory (tensors whose ``data_ptr`` is passed through) and streams.
+
+The library is built in-tree by :func:`paper_2410_04994_gb300.build.build`;
+loading fails loudly if it is missing, and there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libshg.so")
+
+SHG_OK = 0
+SHG_ERR_INVALID_ARG = 1
+SHG_ERR_UNSUPPORTED_GRID = 2
+SHG_ERR_OOM = 3
+SHG_ERR_CUDA = 4
+SHG_ERR_TIMEOUT = 5
+SHG_ERR_NONFINITE = 6
+SHG_ERR_STATE = 7
+
+SHG_FLAG_FP64 = 1
+SHG_FLAG_THERMAL = 2
+SHG_FLAG_ADJOINT = 4
+
+
+class shg_grid_t(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("lx", ctypes.c_double), ("ly", ctypes.c_double),
+                ("hx", ctypes.c_int), ("hy", ctypes.c_int), ("hz", ctypes.c_int)]
+
+
+class shg_crystal_t(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in (
+        "L", "lambda_f", "n_f", "n_sh", "d_eff", "alpha_f", "alpha_sh", "beta_f", "beta_sh",
+        "dk0", "ddk_dT", "dn_dT", "kappa_th", "wx", "wy")]
+
+
+class shg_beams_t(ctypes.Structure):
+    _fields_ = [("p1", ctypes.c_double), ("w0", ctypes.c_double), ("z_focus", ctypes.c_double),
+                ("t_oven_offset", ctypes.c_double), ("undepleted", ctypes.c_int)]
+
+
+class ShgError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = _lib().shg_status_string(status).decode()
+        detail = _lib().shg_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({detail})" if detail else ""))
+
+
+_LIB: Optional[ctypes.CDLL] = None
+
+_P = ctypes.c_void_p
+_D = ctypes.c_double
+_I = ctypes.c_int
+_DP = ctypes.POINTER(ctypes.c_double)
+_IP = ctypes.POINTER(ctypes.c_int)
+_SIGS = {
+    "shg_plan_create": [ctypes.POINTER(shg_grid_t), ctypes.POINTER(shg_crystal_t),
+                        ctypes.POINTER(shg_beams_t), _I, ctypes.POINTER(_P)],
+    "shg_plan_destroy": [_P],
+    "shg_set_beams": [_P, ctypes.POINTER(shg_beams_t)],
+    "shg_set_temperature": [_P, _P, _I, _I, _I, _D, _D, _P],
+    "shg_set_fields": [_P, _P, _P, _P],
+    "shg_propagate": [_P, _P],
+    "shg_efficiency": [_P, _DP, _DP, _DP],
+    "shg_get_fields": [_P, _P, _P, _P],
+    "shg_propagate_adjoint": [_P, _D, _DP, _DP, _DP, _P, _P],
+    "shg_batch_submit": [ctypes.POINTER(_P), _I, _DP, _P],
+    "shg_heat_solve": [_P, _I, _D, _DP, _IP, _P],
+    "shg_thermal_loop": [_P, _I, _I, _D, _DP, _DP, _P],
+    "shg_get_heat": [_P, _P, _P, _P],
+}
+EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
+
+
+def _lib() -> ctypes.CDLL:
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: run paper_2410_04994_gb300.build.build() "
+                              "(nvcc, sm_103a); there is no fallback path")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+        lib.shg_status_string.argtypes = [ctypes.c_int]
+        lib.shg_status_string.restype = ctypes.c_char_p
+        lib.shg_last_error.argtypes = []
+        lib.shg_last_error.restype = ctypes.c_char_p
+        _LIB = lib
+    return _LIB
+
+
+def load():
+    """Load libshg.so (raises ImportError if it has not been built)."""
+    return _lib()
+
+
+def _check(status: int, where: str) -> None:
+    if status != SHG_OK:
+        raise ShgError(status, where)
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return t.data_ptr()
+
+
+# ------------------------------------------------- C entry points ----
+
+def shg_plan_create(grid: shg_grid_t, crystal: shg_crystal_t, beams: shg_beams_t,
+                    flags: int = 0) -> int:
+    out = _P()
+    _check(_lib().shg_plan_create(ctypes.byref(grid), ctypes.byref(crystal), ctypes.byref(beams),
+                                  int(flags), ctypes.byref(out)), "shg_plan_create")
+    return out.value
+
+
+def shg_plan_destroy(plan: int) -> None:
+    _check(_lib().shg_plan_destroy(plan), "shg_plan_destroy")
+
+
+def shg_set_beams(plan: int, beams: shg_beams_t) -> None:
+    _check(_lib().shg_set_beams(plan, ctypes.byref(beams)), "shg_set_beams")
+
+
+def shg_set_temperature(plan: int, dT, t_lx: float = 0.0, t_ly: float = 0.0, stream=None) -> None:
+    """dT: contiguous float32 CUDA tensor [tz][ty][tx], or None to clear."""
+    if dT is None:
+        _check(_lib().shg_set_temperature(plan, None, 0, 0, 0, 0.0, 0.0, _stream(stream)),
+               "shg_set_temperature")
+        return
+    tz, ty, tx = dT.shape
+    _check(_lib().shg_set_temperature(plan, _ptr(dT), tx, ty, tz, float(t_lx), float(t_ly),
+                                      _stream(stream)), "shg_set_temperature")
+
+
+def shg_set_fields(plan: int, a_f=None, a_sh=None, stream=None) -> None:
+    _check(_lib().shg_set_fields(plan, _ptr(a_f), _ptr(a_sh), _stream(stream)), "shg_set_fields")
+
+
+def shg_propagate(plan: int, stream=None) -> None:
+    _check(_lib().shg_propagate(plan, _stream(stream)), "shg_propagate")
+
+
+def shg_efficiency(plan: int):
+    eta, pf, psh = _D(), _D(), _D()
+    _check(_lib().shg_efficiency(plan, ctypes.byref(eta), ctypes.byref(pf), ctypes.byref(psh)),
+           "shg_efficiency")
+    return eta.value, pf.value, psh.value
+
+
+def shg_get_fields(plan: int, a_f=None, a_sh=None, stream=None) -> None:
+    _check(_lib().shg_get_fields(plan, _ptr(a_f), _ptr(a_sh), _stream(stream)), "shg_get_fields")
+
+
+def shg_propagate_adjoint(plan: int, d_eta: float = 1.0, g_dT=None, stream=None):
+    gw, gz, gt = _D(), _D(), _D()
+    _check(_lib().shg_propagate_adjoint(plan, float(d_eta), ctypes.byref(gw), ctypes.byref(gz),
+                                        ctypes.byref(gt), _ptr(g_dT), _stream(stream)),
+           "shg_propagate_adjoint")
+    return gw.value, gz.value, gt.value
+
+
+def shg_batch_submit(plans: Sequence[int], stream=None):
+    n = len(plans)
+    arr = (_P * n)(*plans)
+    etas = (_D * n)()
+    _check(_lib().shg_batch_submit(arr, n, etas, _stream(stream)), "shg_batch_submit")
+    return list(etas)
+
+
+def shg_heat_solve(plan: int, max_sweeps: int = 100000, tol: float = 1e-6, stream=None):
+    resid, sweeps = _D(), _I()
+    _check(_lib().shg_heat_solve(plan, int(max_sweeps), float(tol), ctypes.byref(resid),
+                                 ctypes.byref(sweeps), _stream(stream)), "shg_heat_solve")
+    return resid.value, sweeps.value
+
+
+def shg_thermal_loop(plan: int, n_outer: int, max_sweeps: int = 100000, tol: float = 1e-6,
+                     stream=None):
+    etas = (_D * n_outer)()
+    changes = (_D * n_outer)()
+    _check(_lib().shg_thermal_loop(plan, int(n_outer), int(max_sweeps), float(tol), etas, changes,
+                                   _stream(stream)), "shg_thermal_loop")
+    return list(etas), list(changes)
+
+
+def shg_get_heat(plan: int, q=None, dT=None, stream=None) -> None:
+    _check(_lib().shg_get_heat(plan, _ptr(q), _ptr(dT), _stream(stream)), "shg_get_heat")
+
+
+def shg_status_string(status: int) -> str:
+    return _lib().shg_status_string(status).decode()
+
+
+# ------------------------------------------------------ conveniences ----
+
+def structs_from(w, flags: int = 0):
+    """(grid, crystal, beams) structs from any object with the workload fields
+    (nx, ny, nz, lx, ly, L, lambda_f, ..., p1, w0, z_focus, t_off, undepleted)."""
+    grid = shg_grid_t(w.nx, w.ny, w.nz, w.lx, w.ly, getattr(w, "hx", 0), getattr(w, "hy", 0),
+                      getattr(w, "hz", 0))
+    crystal = shg_crystal_t(w.L, w.lambda_f, w.n_f, w.n_sh, w.d_eff, w.alpha_f, w.alpha_sh,
+                            w.beta_f, w.beta_sh, w.dk0, w.ddk_dT, w.dn_dT, w.kappa_th, w.wx, w.wy)
+    beams = shg_beams_t(w.p1, w.w0, w.z_focus, w.t_off, 1 if w.undepleted else 0)
+    return grid, crystal, beams
+
+
+class Plan:
+    """Owning handle around an shg plan (destroyed with the object)."""
+
+    def __init__(self, w, flags: Optional[int] = None, thermal: bool = False,
+                 adjoint: bool = False):
+        if flags is None:
+            flags = SHG_FLAG_FP64 if getattr(w, "precision", "f32") == "f64" else 0
+            if thermal:
+                flags |= SHG_FLAG_THERMAL
+            if adjoint:
+                flags |= SHG_FLAG_ADJOINT
+        self.w = w
+        self.flags = flags
+        self.fp64 = bool(flags & SHG_FLAG_FP64)
+        self.handle = shg_plan_create(*structs_from(w), flags)
+        self._dT = None
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                shg_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def set_temperature(self, dT, t_lx=0.0, t_ly=0.0, stream=None):
+        import torch
+        if dT is not None and not isinstance(dT, torch.Tensor):
+            dT = torch.as_tensor(dT, dtype=torch.float32, device="cuda")
+        if dT is not None:
+            dT = dT.to(device="cuda", dtype=torch.float32).contiguous()
+        self._dT = dT
+        shg_set_temperature(self.handle, dT, t_lx, t_ly, stream)
+
+    def set_beams(self, p1=None, w0=None, z_focus=None, t_off=None, undepleted=None):
+        w = self.w
+        b = shg_beams_t(w.p1 if p1 is None else p1, w.w0 if w0 is None else w0,
+                        w.z_focus if z_focus is None else z_focus,
+                        w.t_off if t_off is None else t_off,
+                        int(w.undepleted if undepleted is None else undepleted))
+        shg_set_beams(self.handle, b)
+
+    def set_fields(self, a_f=None, a_sh=None, stream=None):
+        shg_set_fields(self.handle, a_f, a_sh, stream)
+
+    def propagate(self, stream=None):
+        shg_propagate(self.handle, stream)
+
+    def efficiency(self):
+        return shg_efficiency(self.handle)
+
+    def fields(self, stream=None):
+        import torch
+        dt = torch.complex128 if self.fp64 else torch.complex64
+        a_f = torch.empty((self.w.ny, self.w.nx), dtype=dt, device="cuda")
+        a_sh = torch.empty_like(a_f)
+        shg_get_fields(self.handle, a_f, a_sh, stream)
+        return a_f, a_sh

@@ -1,0 +1,788 @@
+// C ABI of libshg: plan management, forward propagation and batched sweeps.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "plan.h"
+
+namespace shg {
+
+static thread_local std::string g_last_error;
+
+shg_status_t cuda_fail(cudaError_t e, const char* what) {
+    char buf[512];
+    snprintf(buf, sizeof(buf), "%s: %s", what, cudaGetErrorString(e));
+    g_last_error = buf;
+    cudaGetLastError();  // clear a non-sticky error so the context stays usable
+    return e == cudaErrorMemoryAllocation ? SHG_ERR_OOM : SHG_ERR_CUDA;
+}
+
+cudaError_t launch_copy_init(bool fp64, const InitDesc* idescs, int ninst, const void* descs,
+                             int nx, int ny, cudaStream_t st);
+
+static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
+
+static std::once_flag g_attr_once;
+static cudaError_t g_attr_err = cudaSuccess;
+
+static shg_status_t ensure_attributes() {
+    std::call_once(g_attr_once, [] { g_attr_err = setup_pass_attributes(); });
+    if (g_attr_err != cudaSuccess) return cuda_fail(g_attr_err, "setup_pass_attributes");
+    return SHG_OK;
+}
+
+// ---------------------------------------------------------- tables ----
+
+static double kvec(int k, int n, double len) {
+    // angular frequency of DFT bin k: 2 pi fftfreq(n, len/n)[k]
+    const int kk = (k < (n + 1) / 2) ? k : k - n;
+    return 2.0 * kPi * kk / len;
+}
+
+template <class C> static void put(std::vector<unsigned char>& buf, size_t i, double re, double im) {
+    C v;
+    v.x = static_cast<decltype(v.x)>(re);
+    v.y = static_cast<decltype(v.y)>(im);
+    memcpy(buf.data() + i * sizeof(C), &v, sizeof(C));
+}
+
+static void put_c(const shg_plan* p, std::vector<unsigned char>& buf, size_t i, double re,
+                  double im) {
+    if (p->fp64)
+        put<double2>(buf, i, re, im);
+    else
+        put<float2>(buf, i, re, im);
+}
+
+// K-space factor entry: double2 in FP64 plans, (hi, lo) float pairs otherwise.
+static size_t prop_size(const shg_plan*) { return 16; }  // double2 or float4
+static void put_p(const shg_plan* p, std::vector<unsigned char>& buf, size_t i, double re,
+                  double im) {
+    if (p->fp64) {
+        put<double2>(buf, i, re, im);
+        return;
+    }
+    float4 v;
+    v.x = float(re);
+    v.y = float(im);
+    v.z = float(re - double(v.x));
+    v.w = float(im - double(v.y));
+    memcpy(buf.data() + i * sizeof(float4), &v, sizeof(float4));
+}
+
+static shg_status_t upload(void* dst, const std::vector<unsigned char>& src) {
+    SHG_CK(cudaMemcpy(dst, src.data(), src.size(), cudaMemcpyHostToDevice));
+    return SHG_OK;
+}
+
+static double k_f(const shg_plan* p) { return 2 * kPi * p->c.n_f / p->c.lambda_f; }
+static double k_sh(const shg_plan* p) { return 2 * kPi * p->c.n_sh / (0.5 * p->c.lambda_f); }
+
+// Row and column K-space factors, with the linear absorption and the 1/n of
+// the inverse transforms folded in (App. A, Eq. (A.4)-(A.5), reading 1).
+static shg_status_t build_prop_tables(shg_plan* p) {
+    const int nx = p->g.nx, ny = p->g.ny;
+    const double dz = p->c.L / p->g.nz;
+    const double kj[2] = {k_f(p), k_sh(p)};
+    const double al[2] = {p->c.alpha_f, p->c.alpha_sh};
+    const size_t ps = prop_size(p);
+    std::vector<unsigned char> hx(2 * nx * ps), hy(2 * ny * ps);
+    std::vector<unsigned char> hxc(2 * nx * ps), hyc(2 * ny * ps);
+    for (int j = 0; j < 2; ++j) {
+        const double att = std::exp(-0.5 * al[j] * dz);
+        for (int k = 0; k < nx; ++k) {
+            const double K = kvec(k, nx, p->g.lx);
+            const double ph = -K * K * dz / (2 * kj[j]);
+            put_p(p, hx, j * nx + k, att * std::cos(ph) / nx, att * std::sin(ph) / nx);
+            put_p(p, hxc, j * nx + k, att * std::cos(ph) / nx, -att * std::sin(ph) / nx);
+        }
+        for (int k = 0; k < ny; ++k) {
+            const double K = kvec(k, ny, p->g.ly);
+            const double ph = -K * K * dz / (2 * kj[j]);
+            put_p(p, hy, j * ny + k, std::cos(ph) / ny, std::sin(ph) / ny);
+            put_p(p, hyc, j * ny + k, std::cos(ph) / ny, -std::sin(ph) / ny);
+        }
+    }
+    shg_status_t st;
+    if ((st = upload(p->px, hx)) != SHG_OK) return st;
+    if ((st = upload(p->py, hy)) != SHG_OK) return st;
+    if ((st = upload(p->pxc, hxc)) != SHG_OK) return st;
+    return upload(p->pyc, hyc);
+}
+
+// e^{i theta} at every quarter step, theta = (dk0 + g T_off) z reduced mod 2 pi.
+static shg_status_t build_phase_table(shg_plan* p) {
+    const int nq = 4 * p->g.nz + 1;
+    const double dq = p->c.L / p->g.nz / 4;
+    const double rate = p->c.dk0 + p->c.ddk_dT * p->b.t_oven_offset;
+    std::vector<unsigned char> h(nq * p->csize);
+    for (int q = 0; q < nq; ++q) {
+        const double th = std::fmod(rate * (q * dq), 2 * kPi);
+        put_c(p, h, q, std::cos(th), std::sin(th));
+    }
+    return upload(p->eph, h);
+}
+
+static shg_status_t build_twiddles(shg_plan* p) {
+    std::vector<unsigned char> h(1024 * prop_size(p));
+    for (int k = 0; k < 1024; ++k) {
+        const double a = -2 * kPi * k / 1024.0;
+        put_p(p, h, k, std::cos(a), std::sin(a));
+    }
+    return upload(p->tw, h);
+}
+
+static shg_status_t build_heat_index(shg_plan* p) {
+    const int hx = p->g.hx, hy = p->g.hy, hz = p->g.hz;
+    const double hdx = p->c.wx / (hx - 1), hdy = p->c.wy / (hy - 1), hdz = p->c.L / (hz - 1);
+    std::vector<int> ix(p->g.nx), iy(p->g.ny), lz(p->g.nz + 1);
+    for (int m = 0; m < p->g.nx; ++m) {
+        const double x = (m - p->g.nx / 2) * (p->g.lx / p->g.nx);
+        const int i = int(std::floor((x + p->c.wx / 2) / hdx + 0.5));
+        ix[m] = (i >= 0 && i < hx) ? i : -1;
+    }
+    for (int n = 0; n < p->g.ny; ++n) {
+        const double y = (n - p->g.ny / 2) * (p->g.ly / p->g.ny);
+        const int j = int(std::floor((y + p->c.wy / 2) / hdy + 0.5));
+        iy[n] = (j >= 0 && j < hy) ? j : -1;
+    }
+    for (int s = 0; s <= p->g.nz; ++s) {
+        const double z = s * (p->c.L / p->g.nz);
+        const int l = int(std::floor(z / hdz + 0.5));
+        lz[s] = (l >= 0 && l < hz) ? l : -1;
+    }
+    SHG_CK(cudaMemcpy(p->hix, ix.data(), ix.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SHG_CK(cudaMemcpy(p->hiy, iy.data(), iy.size() * sizeof(int), cudaMemcpyHostToDevice));
+    SHG_CK(cudaMemcpy(p->hlz, lz.data(), lz.size() * sizeof(int), cudaMemcpyHostToDevice));
+    return SHG_OK;
+}
+
+// ------------------------------------------------------ descriptors ----
+
+template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void* field) {
+    memset(d, 0, sizeof(*d));
+    const double lam_f = p->c.lambda_f, lam_s = 0.5 * p->c.lambda_f;
+    const double cF = 0.5 * kEps0 * kCLight * p->c.n_f;
+    const double cS = 0.5 * kEps0 * kCLight * p->c.n_sh;
+    d->field = static_cast<cx<R>*>(field);
+    d->px = static_cast<const pt<R>*>(p->px);
+    d->py = static_cast<const pt<R>*>(p->py);
+    d->eph = static_cast<const cx<R>*>(p->eph);
+    d->ttab = p->ttab;
+    d->tx = p->tx;
+    d->ty = p->ty;
+    d->tz = p->tz;
+    if (p->ttab) {
+        d->tx0 = float(-p->tlx / 2);
+        d->ty0 = float(-p->tly / 2);
+        d->tdx_inv = float((p->tx - 1) / p->tlx);
+        d->tdy_inv = float((p->ty - 1) / p->tly);
+        d->tdz_inv = float((p->tz - 1) / p->c.L);
+    }
+    d->dx = R(p->g.lx / p->g.nx);
+    d->dy = R(p->g.ly / p->g.ny);
+    d->x0 = R(-(p->g.nx / 2) * (p->g.lx / p->g.nx));
+    d->y0 = R(-(p->g.ny / 2) * (p->g.ly / p->g.ny));
+    d->kF = R(2 * kPi * p->c.d_eff / (p->c.n_f * lam_f));
+    d->kS = R(2 * kPi * p->c.d_eff / (p->c.n_sh * lam_f));
+    d->bF = R(0.5 * p->c.beta_f * cF);
+    d->bS = R(0.5 * p->c.beta_sh * cS);
+    d->lF = R(2 * kPi / lam_f * p->c.dn_dT);
+    d->lS = R(2 * kPi / lam_s * p->c.dn_dT);
+    d->psi0F = R(2 * kPi / lam_f * p->c.dn_dT * p->b.t_oven_offset);
+    d->psi0S = R(2 * kPi / lam_s * p->c.dn_dT * p->b.t_oven_offset);
+    d->g = R(p->c.ddk_dT);
+    d->dz = R(p->c.L / p->g.nz);
+    d->undepleted = p->b.undepleted ? 1 : 0;
+    if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
+        d->Q = p->Q;
+        d->hix = p->hix;
+        d->hiy = p->hiy;
+        d->hlz = p->hlz;
+        d->hx = p->g.hx;
+        d->hy = p->g.hy;
+        d->hz = p->g.hz;
+        d->qaF = R(p->c.alpha_f * cF);
+        d->qbF = R(p->c.beta_f * cF * cF);
+        d->qaS = R(p->c.alpha_sh * cS);
+        d->qbS = R(p->c.beta_sh * cS * cS);
+        d->dxdy = R((p->g.lx / p->g.nx) * (p->g.ly / p->g.ny));
+    }
+}
+
+void fill_desc_f32(const shg_plan* p, InstDesc<float>* d) { fill_desc<float>(p, d, p->field); }
+void fill_desc_f64(const shg_plan* p, InstDesc<double>* d) { fill_desc<double>(p, d, p->field); }
+
+void fill_init(const shg_plan* p, InitDesc* d) {
+    memset(d, 0, sizeof(*d));
+    d->dx = p->g.lx / p->g.nx;
+    d->dy = p->g.ly / p->g.ny;
+    d->x0 = -(p->g.nx / 2) * d->dx;
+    d->y0 = -(p->g.ny / 2) * d->dy;
+    d->w0 = p->b.w0;
+    d->zf = p->b.z_focus;
+    d->kF = k_f(p);
+    d->p1 = p->b.p1;
+    d->cFdxdy = 0.5 * kEps0 * kCLight * p->c.n_f * d->dx * d->dy;
+    d->cSdxdy = 0.5 * kEps0 * kCLight * p->c.n_sh * d->dx * d->dy;
+    d->red = p->red;
+    d->pw = p->pw;
+    d->f0 = p->custom_init ? p->field0 : nullptr;
+}
+
+static size_t desc_bytes(bool fp64) { return fp64 ? sizeof(InstDesc<double>) : sizeof(InstDesc<float>); }
+
+static void fill_desc_any(const shg_plan* p, void* out) {
+    if (p->fp64)
+        fill_desc_f64(p, static_cast<InstDesc<double>*>(out));
+    else
+        fill_desc_f32(p, static_cast<InstDesc<float>*>(out));
+}
+
+static shg_status_t upload_desc(shg_plan* p) {
+    std::vector<unsigned char> h(desc_bytes(p->fp64));
+    fill_desc_any(p, h.data());
+    SHG_CK(cudaMemcpy(p->desc, h.data(), h.size(), cudaMemcpyHostToDevice));
+    InitDesc id;
+    fill_init(p, &id);
+    SHG_CK(cudaMemcpy(p->idesc, &id, sizeof(id), cudaMemcpyHostToDevice));
+    return SHG_OK;
+}
+
+static shg_status_t quiesce(shg_plan* p) {
+    if (p->last_stream != nullptr || p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    return SHG_OK;
+}
+
+// ----------------------------------------------------------- forward ----
+
+shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
+                             const InitDesc* idescs, int ninst, const void* tw,
+                             const std::vector<shg_plan*>& plans, cudaStream_t st) {
+    const bool custom = plans[0]->custom_init;
+    cudaError_t e = custom ? launch_copy_init(fp64, idescs, ninst, descs, nx, ny, st)
+                           : launch_init(fp64, idescs, nullptr, ninst, descs, nx, ny, st);
+    if (e != cudaSuccess) return cuda_fail(e, "init");
+    for (shg_plan* p : plans) {
+        if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
+            e = cudaMemsetAsync(p->Q, 0, sizeof(double) * p->g.hx * p->g.hy * p->g.hz, st);
+            if (e != cudaSuccess) return cuda_fail(e, "memset Q");
+        }
+    }
+    for (int s = 0; s <= nz; ++s) {
+        e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, st);
+        if (e != cudaSuccess) return cuda_fail(e, "row pass");
+        if (s < nz) {
+            e = launch_col(fp64, ny, descs, ninst, nx, tw, st);
+            if (e != cudaSuccess) return cuda_fail(e, "column pass");
+        }
+    }
+    e = launch_power(fp64, idescs, descs, ninst, nx, ny, st);
+    if (e != cudaSuccess) return cuda_fail(e, "power");
+    return SHG_OK;
+}
+
+static bool use_graphs() {
+    const char* v = getenv("SHG_NO_GRAPH");
+    return !(v && v[0] == '1');
+}
+
+// Capture `fn(stream)` into an executable graph using the private stream.
+template <class Fn>
+static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
+    cudaGraph_t graph = nullptr;
+    SHG_CK(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+    shg_status_t st = fn(cap);
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (st != SHG_OK) {
+        if (graph) cudaGraphDestroy(graph);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(out, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
+    return SHG_OK;
+}
+
+static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
+    std::vector<shg_plan*> one{p};
+    auto body = [&](cudaStream_t s) {
+        return enqueue_forward(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, p->idesc, 1, p->tw,
+                               one, s);
+    };
+    if (!use_graphs()) return body(st);
+    if (!p->gvalid) {
+        if (p->gexec) {
+            cudaGraphExecDestroy(p->gexec);
+            p->gexec = nullptr;
+        }
+        shg_status_t s = capture(p->cap, body, &p->gexec);
+        if (s != SHG_OK) return s;
+        p->gvalid = true;
+    }
+    SHG_CK(cudaGraphLaunch(p->gexec, st));
+    return SHG_OK;
+}
+
+}  // namespace shg
+
+using namespace shg;
+
+// ============================================================ C ABI ====
+
+extern "C" {
+
+const char* shg_status_string(shg_status_t s) {
+    switch (s) {
+        case SHG_OK: return "ok";
+        case SHG_ERR_INVALID_ARG: return "invalid argument";
+        case SHG_ERR_UNSUPPORTED_GRID: return "unsupported grid (nx, ny must be powers of two in [8, 1024]; [8, 256] in FP64)";
+        case SHG_ERR_OOM: return "device allocation failed";
+        case SHG_ERR_CUDA: return "CUDA error";
+        case SHG_ERR_TIMEOUT: return "device-side wait timed out";
+        case SHG_ERR_NONFINITE: return "non-finite power or efficiency";
+        case SHG_ERR_STATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+const char* shg_last_error(void) { return g_last_error.c_str(); }
+
+static void plan_free(shg_plan* p);
+
+shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crystal,
+                             const shg_beams_t* beams, int flags, shg_plan_t** out) {
+    if (out) *out = nullptr;
+    if (!grid || !crystal || !beams || !out) return SHG_ERR_INVALID_ARG;
+    const bool fp64 = (flags & SHG_FLAG_FP64) != 0;
+    const int hi = fp64 ? 256 : 1024;
+    if (!pow2_in(grid->nx, 8, hi) || !pow2_in(grid->ny, 8, hi)) return SHG_ERR_UNSUPPORTED_GRID;
+    if (grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0)) return SHG_ERR_INVALID_ARG;
+    if (!(crystal->L > 0) || !(crystal->lambda_f > 0) || !(crystal->n_f > 0) ||
+        !(crystal->n_sh > 0) || !(beams->w0 > 0) || !(beams->p1 >= 0))
+        return SHG_ERR_INVALID_ARG;
+    if (flags & SHG_FLAG_THERMAL) {
+        if (grid->hx < 3 || grid->hy < 3 || grid->hz < 3 || !(crystal->wx > 0) ||
+            !(crystal->wy > 0) || !(crystal->kappa_th > 0))
+            return SHG_ERR_INVALID_ARG;
+        if (grid->hx > 2 * grid->nx + 64) return SHG_ERR_UNSUPPORTED_GRID;  // shared bins
+    }
+    shg_status_t st = ensure_attributes();
+    if (st != SHG_OK) return st;
+    shg_plan* p = new shg_plan();
+    p->g = *grid;
+    p->c = *crystal;
+    p->b = *beams;
+    p->flags = flags;
+    p->fp64 = fp64;
+    p->csize = fp64 ? 16 : 8;
+    cudaGetDevice(&p->device);
+    const size_t npts = size_t(grid->nx) * grid->ny;
+    auto fail = [&](cudaError_t e, const char* what) {
+        shg_status_t s = cuda_fail(e, what);
+        plan_free(p);
+        return s;
+    };
+    cudaError_t e;
+#define ALLOC(ptr, bytes)                                                   \
+    if ((e = cudaMalloc((void**)&(ptr), (bytes))) != cudaSuccess) return fail(e, "cudaMalloc " #ptr);
+    ALLOC(p->field, 2 * npts * p->csize);
+    ALLOC(p->px, 2 * grid->nx * 16);
+    ALLOC(p->py, 2 * grid->ny * 16);
+    ALLOC(p->pxc, 2 * grid->nx * 16);
+    ALLOC(p->pyc, 2 * grid->ny * 16);
+    ALLOC(p->eph, (4 * size_t(grid->nz) + 1) * p->csize);
+    ALLOC(p->tw, 1024 * 16);
+    ALLOC(p->desc, desc_bytes(fp64));
+    ALLOC(p->idesc, sizeof(InitDesc));
+    ALLOC(p->red, 2 * kRedBlocks * sizeof(double));
+    ALLOC(p->pw, 2 * sizeof(double));
+    if (flags & SHG_FLAG_THERMAL) {
+        const size_t nh = size_t(grid->hx) * grid->hy * grid->hz;
+        ALLOC(p->Q, nh * sizeof(double));
+        ALLOC(p->theat, nh * sizeof(float));
+        ALLOC(p->theat_prev, nh * sizeof(float));
+        ALLOC(p->hix, grid->nx * sizeof(int));
+        ALLOC(p->hiy, grid->ny * sizeof(int));
+        ALLOC(p->hlz, (grid->nz + 1) * sizeof(int));
+        ALLOC(p->hred, 2 * 1024 * sizeof(double));
+        if ((e = cudaMemset(p->Q, 0, nh * sizeof(double))) != cudaSuccess) return fail(e, "memset");
+        if ((e = cudaMemset(p->theat, 0, nh * sizeof(float))) != cudaSuccess) return fail(e, "memset");
+        if ((e = cudaMemset(p->theat_prev, 0, nh * sizeof(float))) != cudaSuccess)
+            return fail(e, "memset");
+    }
+#undef ALLOC
+    if ((e = cudaMemset(p->field, 0, 2 * npts * p->csize)) != cudaSuccess) return fail(e, "memset");
+    if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
+        return fail(e, "cudaStreamCreate");
+    if ((st = build_prop_tables(p)) != SHG_OK || (st = build_phase_table(p)) != SHG_OK ||
+        (st = build_twiddles(p)) != SHG_OK ||
+        ((flags & SHG_FLAG_THERMAL) && (st = build_heat_index(p)) != SHG_OK) ||
+        (st = upload_desc(p)) != SHG_OK) {
+        plan_free(p);
+        return st;
+    }
+    *out = p;
+    return SHG_OK;
+}
+
+
+static void plan_free(shg_plan* p) {
+    if (!p) return;
+    shg::forget_plan_batches(p);
+    shg::free_adjoint(p);
+    if (p->gexec) cudaGraphExecDestroy(p->gexec);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
+                    p->tw,    p->ttab,   p->tmap, p->desc, p->idesc, p->red, p->pw,
+                    p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->hred};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    delete p;
+}
+
+shg_status_t shg_plan_destroy(shg_plan_t* p) {
+    if (!p) return SHG_OK;
+    if (p->has_result || p->last_stream) cudaStreamSynchronize(p->last_stream);
+    plan_free(p);
+    return SHG_OK;
+}
+
+shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
+    if (!p || !beams || !(beams->w0 > 0) || !(beams->p1 >= 0)) return SHG_ERR_INVALID_ARG;
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    p->b = *beams;
+    if (p->custom_init) {
+        p->custom_init = false;
+        p->gvalid = false;
+    }
+    if ((st = build_phase_table(p)) != SHG_OK) return st;
+    return upload_desc(p);
+}
+
+shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int ty, int tz,
+                                 double t_lx, double t_ly, shg_stream_t stream) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (dT_dev == nullptr) {
+        if (p->ttab) {
+            cudaFree(p->ttab);
+            cudaFree(p->tmap);
+            p->ttab = nullptr;
+            p->tmap = nullptr;
+            p->tx = p->ty = p->tz = 0;
+            p->gvalid = false;
+        }
+        return upload_desc(p);
+    }
+    if (tx < 2 || ty < 2 || tz < 2) return SHG_ERR_INVALID_ARG;
+    const size_t n = size_t(tx) * ty * tz;
+    if (p->ttab == nullptr || p->tx != tx || p->ty != ty || p->tz != tz) {
+        if (p->ttab) cudaFree(p->ttab);
+        if (p->tmap) cudaFree(p->tmap);
+        p->ttab = nullptr;
+        p->tmap = nullptr;
+        SHG_CK(cudaMalloc((void**)&p->ttab, n * sizeof(float2)));
+        SHG_CK(cudaMalloc((void**)&p->tmap, n * sizeof(float)));
+        p->gvalid = false;
+    }
+    p->tx = tx;
+    p->ty = ty;
+    p->tz = tz;
+    p->tlx = t_lx > 0 ? t_lx : p->g.lx;
+    p->tly = t_ly > 0 ? t_ly : p->g.ly;
+    if (dT_dev != p->tmap)
+        SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    SHG_CK(launch_build_ttab(p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+    SHG_CK(cudaStreamSynchronize(s));
+    return upload_desc(p);
+}
+
+shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh_dev,
+                            shg_stream_t stream) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t one = size_t(p->g.nx) * p->g.ny * p->csize;
+    if (!p->field0) SHG_CK(cudaMalloc(&p->field0, 2 * one));
+    unsigned char* f0 = static_cast<unsigned char*>(p->field0);
+    if (a_f_dev)
+        SHG_CK(cudaMemcpyAsync(f0, a_f_dev, one, cudaMemcpyDeviceToDevice, s));
+    else
+        SHG_CK(cudaMemsetAsync(f0, 0, one, s));
+    if (a_sh_dev)
+        SHG_CK(cudaMemcpyAsync(f0 + one, a_sh_dev, one, cudaMemcpyDeviceToDevice, s));
+    else
+        SHG_CK(cudaMemsetAsync(f0 + one, 0, one, s));
+    SHG_CK(cudaStreamSynchronize(s));
+    if (!p->custom_init) p->gvalid = false;
+    p->custom_init = true;
+    return upload_desc(p);
+}
+
+shg_status_t shg_propagate(shg_plan_t* p, shg_stream_t stream) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    shg_status_t st = plan_forward(p, s);
+    if (st != SHG_OK) return st;
+    p->has_result = true;
+    p->batch_result = false;
+    p->last_stream = s;
+    return SHG_OK;
+}
+
+shg_status_t shg_efficiency(shg_plan_t* p, double* eta, double* p_f, double* p_sh) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    if (!p->has_result) return SHG_ERR_STATE;
+    SHG_CK(cudaStreamSynchronize(p->last_stream));
+    if (!p->batch_result)
+        SHG_CK(cudaMemcpy(p->pw_host, p->pw, 2 * sizeof(double), cudaMemcpyDeviceToHost));
+    const double e = p->b.p1 > 0 ? p->pw_host[1] / p->b.p1 : 0.0;
+    if (eta) *eta = e;
+    if (p_f) *p_f = p->pw_host[0];
+    if (p_sh) *p_sh = p->pw_host[1];
+    if (!std::isfinite(e) || !std::isfinite(p->pw_host[0])) return SHG_ERR_NONFINITE;
+    return SHG_OK;
+}
+
+shg_status_t shg_get_fields(shg_plan_t* p, void* a_f_dev, void* a_sh_dev, shg_stream_t stream) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->last_stream != s && p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    const size_t one = size_t(p->g.nx) * p->g.ny * p->csize;
+    const unsigned char* f = static_cast<const unsigned char*>(p->field);
+    if (a_f_dev) SHG_CK(cudaMemcpyAsync(a_f_dev, f, one, cudaMemcpyDeviceToDevice, s));
+    if (a_sh_dev) SHG_CK(cudaMemcpyAsync(a_sh_dev, f + one, one, cudaMemcpyDeviceToDevice, s));
+    return SHG_OK;
+}
+
+}  // extern "C"
+
+// ============================================================ batches ====
+
+namespace shg {
+
+struct BatchGroup {
+    bool fp64;
+    int nx, ny, nz;
+    bool custom;
+    std::vector<shg_plan*> plans;
+    std::vector<int> index;     // position of each plan in the caller's list
+    void* descs = nullptr;      // device InstDesc[n]
+    InitDesc* idescs = nullptr; // device InitDesc[n]
+    double* pw = nullptr;       // device [n][2]
+};
+
+struct BatchEntry {
+    std::vector<BatchGroup> groups;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;
+    double* pw_host = nullptr;  // pinned [n][2]
+    int n = 0;
+    bool valid = false;
+};
+
+static std::mutex g_batch_mu;
+static std::map<std::vector<shg_plan*>, BatchEntry*> g_batches;
+
+static void free_entry(BatchEntry* b) {
+    for (auto& g : b->groups) {
+        if (g.descs) cudaFree(g.descs);
+        if (g.idescs) cudaFree(g.idescs);
+        if (g.pw) cudaFree(g.pw);
+    }
+    if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    for (auto s : b->side) cudaStreamDestroy(s);
+    for (auto e : b->ev) cudaEventDestroy(e);
+    if (b->pw_host) cudaFreeHost(b->pw_host);
+    delete b;
+}
+
+static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry** out) {
+    BatchEntry* b = new BatchEntry();
+    b->n = int(plans.size());
+    for (int i = 0; i < b->n; ++i) {
+        shg_plan* p = plans[i];
+        BatchGroup* g = nullptr;
+        for (auto& gg : b->groups)
+            if (gg.fp64 == p->fp64 && gg.nx == p->g.nx && gg.ny == p->g.ny && gg.nz == p->g.nz &&
+                gg.custom == p->custom_init)
+                g = &gg;
+        if (!g) {
+            b->groups.push_back(BatchGroup{p->fp64, p->g.nx, p->g.ny, p->g.nz, p->custom_init});
+            g = &b->groups.back();
+        }
+        g->plans.push_back(p);
+        g->index.push_back(i);
+    }
+    cudaError_t e;
+    for (auto& g : b->groups) {
+        const int n = int(g.plans.size());
+        if ((e = cudaMalloc(&g.descs, n * desc_bytes(g.fp64))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&g.idescs, n * sizeof(InitDesc))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&g.pw, n * 2 * sizeof(double))) != cudaSuccess) {
+            free_entry(b);
+            return cuda_fail(e, "batch alloc");
+        }
+    }
+    if ((e = cudaMallocHost((void**)&b->pw_host, b->n * 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
+        free_entry(b);
+        return cuda_fail(e, "batch setup");
+    }
+    for (size_t i = 0; i < b->groups.size(); ++i) {
+        cudaStream_t s;
+        cudaEvent_t ev;
+        if ((e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) {
+            free_entry(b);
+            return cuda_fail(e, "batch streams");
+        }
+        b->side.push_back(s);
+        b->ev.push_back(ev);
+    }
+    cudaEvent_t fork;
+    if ((e = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming)) != cudaSuccess) {
+        free_entry(b);
+        return cuda_fail(e, "batch event");
+    }
+    b->ev.push_back(fork);
+    *out = b;
+    return SHG_OK;
+}
+
+// Upload the current descriptors of every plan of the entry.
+static shg_status_t refresh_entry(BatchEntry* b, cudaStream_t st) {
+    for (auto& g : b->groups) {
+        const int n = int(g.plans.size());
+        const size_t db = desc_bytes(g.fp64);
+        std::vector<unsigned char> hd(n * db);
+        std::vector<InitDesc> hi(n);
+        for (int k = 0; k < n; ++k) {
+            fill_desc_any(g.plans[k], hd.data() + k * db);
+            fill_init(g.plans[k], &hi[k]);
+            hi[k].pw = g.pw + 2 * k;
+        }
+        SHG_CK(cudaMemcpyAsync(g.descs, hd.data(), hd.size(), cudaMemcpyHostToDevice, st));
+        SHG_CK(cudaMemcpyAsync(g.idescs, hi.data(), n * sizeof(InitDesc), cudaMemcpyHostToDevice,
+                               st));
+    }
+    // the host vectors above go out of scope: make the copies complete first
+    SHG_CK(cudaStreamSynchronize(st));
+    return SHG_OK;
+}
+
+static shg_status_t enqueue_batch(BatchEntry* b, cudaStream_t st) {
+    // fork the groups onto side streams so that instances of different grids
+    // overlap, then join
+    const int ng = int(b->groups.size());
+    cudaEvent_t fork = b->ev.back();
+    SHG_CK(cudaEventRecord(fork, st));
+    for (int i = 0; i < ng; ++i) {
+        BatchGroup& g = b->groups[i];
+        cudaStream_t s = b->side[i];
+        SHG_CK(cudaStreamWaitEvent(s, fork, 0));
+        shg_status_t r = enqueue_forward(g.fp64, g.nx, g.ny, g.nz, g.descs, g.idescs,
+                                         int(g.plans.size()), g.plans[0]->tw, g.plans, s);
+        if (r != SHG_OK) return r;
+        SHG_CK(cudaEventRecord(b->ev[i], s));
+        SHG_CK(cudaStreamWaitEvent(st, b->ev[i], 0));
+    }
+    return SHG_OK;
+}
+
+}  // namespace shg
+
+namespace shg {
+void forget_plan_batches(shg_plan* p) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (auto it = g_batches.begin(); it != g_batches.end();) {
+        bool has = false;
+        for (auto q : it->first) has |= (q == p);
+        if (has) {
+            free_entry(it->second);
+            it = g_batches.erase(it);
+        } else {
+            ++it;
+        }
+    }
+}
+}  // namespace shg
+
+extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double* eta_host_out,
+                                         shg_stream_t stream) {
+    if (!plans || n <= 0) return SHG_ERR_INVALID_ARG;
+    std::vector<shg_plan*> key(plans, plans + n);
+    for (auto p : key)
+        if (!p) return SHG_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    BatchEntry*& ent = g_batches[key];
+    shg_status_t r;
+    if (ent) {
+        // the captured graph depends on each plan's init kind; rebuild if changed
+        bool stale = false;
+        for (auto& g : ent->groups)
+            for (auto p : g.plans) stale |= (p->custom_init != g.custom);
+        if (stale) {
+            free_entry(ent);
+            ent = nullptr;
+        }
+    }
+    if (!ent) {
+        if ((r = build_entry(key, &ent)) != SHG_OK) {
+            g_batches.erase(key);
+            return r;
+        }
+    }
+    for (auto p : key)
+        if (p->has_result) cudaStreamSynchronize(p->last_stream);
+    if ((r = refresh_entry(ent, st)) != SHG_OK) return r;
+    if (use_graphs()) {
+        if (!ent->valid) {
+            if (ent->gexec) {
+                cudaGraphExecDestroy(ent->gexec);
+                ent->gexec = nullptr;
+            }
+            r = capture(ent->cap, [&](cudaStream_t s) { return enqueue_batch(ent, s); },
+                        &ent->gexec);
+            if (r != SHG_OK) return r;
+            ent->valid = true;
+        }
+        SHG_CK(cudaGraphLaunch(ent->gexec, st));
+    } else {
+        if ((r = enqueue_batch(ent, st)) != SHG_OK) return r;
+    }
+    // gather the powers
+    for (auto& g : ent->groups)
+        for (size_t k = 0; k < g.plans.size(); ++k)
+            SHG_CK(cudaMemcpyAsync(ent->pw_host + 2 * g.index[k], g.pw + 2 * k,
+                                   2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    SHG_CK(cudaStreamSynchronize(st));
+    bool finite = true;
+    for (int i = 0; i < n; ++i) {
+        shg_plan* p = key[i];
+        p->pw_host[0] = ent->pw_host[2 * i];
+        p->pw_host[1] = ent->pw_host[2 * i + 1];
+        const double e = p->b.p1 > 0 ? p->pw_host[1] / p->b.p1 : 0.0;
+        if (eta_host_out) eta_host_out[i] = e;
+        finite &= std::isfinite(e);
+        p->last_stream = st;
+        p->has_result = true;
+        p->batch_result = true;
+    }
+    return finite ? SHG_OK : SHG_ERR_NONFINITE;
+}

@@ -1,0 +1,214 @@
+// Initial pump, FP64 power reductions and temperature tables.
+#include "plan.h"
+
+namespace shg {
+
+cudaError_t row_f32(int, const void*, int, int, int, int, const void*, cudaStream_t);
+cudaError_t col_f32(int, const void*, int, int, const void*, cudaStream_t);
+cudaError_t attr_f32();
+cudaError_t row_f64(int, const void*, int, int, int, int, const void*, cudaStream_t);
+cudaError_t col_f64(int, const void*, int, int, const void*, cudaStream_t);
+cudaError_t attr_f64();
+
+cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
+                       const void* tw, cudaStream_t st) {
+    return fp64 ? row_f64(nx, descs, ninst, ny, nz, s, tw, st)
+                : row_f32(nx, descs, ninst, ny, nz, s, tw, st);
+}
+
+cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
+                       cudaStream_t st) {
+    return fp64 ? col_f64(ny, descs, ninst, nx, tw, st) : col_f32(ny, descs, ninst, nx, tw, st);
+}
+
+cudaError_t setup_pass_attributes() {
+    cudaError_t e = attr_f32();
+    if (e == cudaSuccess) e = attr_f64();
+    return e;
+}
+
+constexpr int kRedThreads = 256;
+
+// Block-wide sum of two doubles in a fixed order (deterministic).
+__device__ void block_sum2(double& a, double& b) {
+    __shared__ double sa[kRedThreads], sb[kRedThreads];
+    sa[threadIdx.x] = a;
+    sb[threadIdx.x] = b;
+    __syncthreads();
+    for (int w = kRedThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sa[threadIdx.x] += sa[threadIdx.x + w];
+            sb[threadIdx.x] += sb[threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    a = sa[0];
+    b = sb[0];
+    __syncthreads();
+}
+
+// Unnormalised Eq. (5) at z = 0: exp(-r^2 / (w0^2 (1 + i tau0))) / (1 + i tau0),
+// tau0 = -z_focus / z_R, z_R = w0^2 k_F / 2 (double precision).
+__device__ double2 gauss0(const InitDesc& d, int m, int n) {
+    const double x = d.x0 + d.dx * m, y = d.y0 + d.dy * n;
+    const double zr = d.w0 * d.w0 * d.kF * 0.5;
+    const double tau = -d.zf / zr;
+    // 1/(1 + i tau) = (1 - i tau) / (1 + tau^2)
+    const double den = 1.0 + tau * tau;
+    const double qr = 1.0 / den, qi = -tau / den;
+    const double a = -(x * x + y * y) / (d.w0 * d.w0);  // exponent = a * (qr + i qi)
+    const double mag = exp(a * qr);
+    double s, c;
+    sincos(a * qi, &s, &c);
+    const double er = mag * c, ei = mag * s;
+    return make_double2(er * qr - ei * qi, er * qi + ei * qr);
+}
+
+// Pass 1 of the init: partial sums of |g|^2 (or of the custom field power).
+__global__ void k_init_partial(const InitDesc* __restrict__ ids, int nx, int ny) {
+    const InitDesc& d = ids[blockIdx.y];
+    double acc = 0, unused = 0;
+    const int npts = nx * ny;
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < npts; i += gridDim.x * kRedThreads) {
+        double2 g = gauss0(d, i % nx, i / nx);
+        acc += g.x * g.x + g.y * g.y;
+    }
+    block_sum2(acc, unused);
+    if (threadIdx.x == 0) d.red[blockIdx.x * 2] = acc;
+}
+
+// Pass 2: every block sums the partials in the same order, scales and writes.
+template <class R>
+__global__ void k_init_write(const InitDesc* __restrict__ ids, const InstDesc<R>* __restrict__ ds,
+                             int nx, int ny) {
+    using C = cx<R>;
+    const InitDesc& d = ids[blockIdx.y];
+    C* f = ds[blockIdx.y].field;
+    const int npts = nx * ny;
+    __shared__ double a0s;
+    if (threadIdx.x == 0) {
+        double s = 0;
+        for (int b = 0; b < kRedBlocks; ++b) s += d.red[b * 2];
+        a0s = sqrt(d.p1 / (d.cFdxdy * s));
+    }
+    __syncthreads();
+    const double a0 = a0s;
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < npts; i += gridDim.x * kRedThreads) {
+        double2 g = gauss0(d, i % nx, i / nx);
+        f[i] = mk<C>(R(a0 * g.x), R(a0 * g.y));
+        f[npts + i] = mk<C>(R(0), R(0));
+    }
+}
+
+// Custom initial state: plain copy.
+template <class R>
+__global__ void k_copy_init(const InitDesc* __restrict__ ids, const InstDesc<R>* __restrict__ ds,
+                            int nx, int ny) {
+    using C = cx<R>;
+    const C* src = static_cast<const C*>(ids[blockIdx.y].f0);
+    C* f = ds[blockIdx.y].field;
+    const int n2 = 2 * nx * ny;
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < n2; i += gridDim.x * kRedThreads)
+        f[i] = src[i];
+}
+
+cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const*, int ninst,
+                        const void* descs, int nx, int ny, cudaStream_t st) {
+    // Instances of one batch either all use the Gaussian or carry f0; the
+    // host splits mixed batches.
+    dim3 grid(kRedBlocks, ninst);
+    k_init_partial<<<grid, kRedThreads, 0, st>>>(idescs, nx, ny);
+    if (fp64)
+        k_init_write<double><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<double>*>(descs), nx, ny);
+    else
+        k_init_write<float><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<float>*>(descs), nx, ny);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_init(bool fp64, const InitDesc* idescs, int ninst, const void* descs,
+                             int nx, int ny, cudaStream_t st) {
+    dim3 grid(kRedBlocks, ninst);
+    if (fp64)
+        k_copy_init<double><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<double>*>(descs), nx, ny);
+    else
+        k_copy_init<float><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<float>*>(descs), nx, ny);
+    return cudaGetLastError();
+}
+
+// P_j = (1/2) eps0 c n_j sum |A_j|^2 dx dy, summed in double in a fixed order.
+template <class R>
+__global__ void k_power_partial(const InitDesc* __restrict__ ids,
+                                const InstDesc<R>* __restrict__ ds, int nx, int ny) {
+    using C = cx<R>;
+    const InitDesc& d = ids[blockIdx.y];
+    const C* f = ds[blockIdx.y].field;
+    const int npts = nx * ny;
+    double aF = 0, aS = 0;
+    for (int i = blockIdx.x * kRedThreads + threadIdx.x; i < npts; i += gridDim.x * kRedThreads) {
+        C u = f[i], v = f[npts + i];
+        aF += double(u.x) * u.x + double(u.y) * u.y;
+        aS += double(v.x) * v.x + double(v.y) * v.y;
+    }
+    block_sum2(aF, aS);
+    if (threadIdx.x == 0) {
+        d.red[blockIdx.x * 2] = aF;
+        d.red[blockIdx.x * 2 + 1] = aS;
+    }
+}
+
+__global__ void k_power_final(const InitDesc* __restrict__ ids) {
+    const InitDesc& d = ids[blockIdx.x];
+    if (threadIdx.x == 0) {
+        double aF = 0, aS = 0;
+        for (int b = 0; b < kRedBlocks; ++b) {
+            aF += d.red[b * 2];
+            aS += d.red[b * 2 + 1];
+        }
+        d.pw[0] = d.cFdxdy * aF;
+        d.pw[1] = d.cSdxdy * aS;
+    }
+}
+
+cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
+                         int ny, cudaStream_t st) {
+    dim3 grid(kRedBlocks, ninst);
+    if (fp64)
+        k_power_partial<double><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<double>*>(descs), nx, ny);
+    else
+        k_power_partial<float><<<grid, kRedThreads, 0, st>>>(
+            idescs, static_cast<const InstDesc<float>*>(descs), nx, ny);
+    k_power_final<<<ninst, 32, 0, st>>>(idescs);
+    return cudaGetLastError();
+}
+
+// (dT, C) table: C[l] = C[l-1] + dZ/2 (dT[l-1] + dT[l]) accumulated in double
+// (Eq. 3 by the trapezoid rule on the map's z-nodes).
+__global__ void k_build_ttab(const float* __restrict__ dT, float2* __restrict__ tt, int tx,
+                             int ty, int tz, double dZ) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= tx * ty) return;
+    const size_t plane = size_t(tx) * ty;
+    double c = 0;
+    float prev = dT[col];
+    tt[col] = make_float2(prev, 0.f);
+    for (int l = 1; l < tz; ++l) {
+        const float cur = dT[l * plane + col];
+        c += 0.5 * dZ * (double(prev) + double(cur));
+        tt[l * plane + col] = make_float2(cur, float(c));
+        prev = cur;
+    }
+}
+
+cudaError_t launch_build_ttab(const float* dT, float2* ttab, int tx, int ty, int tz, double dZ,
+                              cudaStream_t st) {
+    const int cols = tx * ty;
+    k_build_ttab<<<(cols + 127) / 128, 128, 0, st>>>(dT, ttab, tx, ty, tz, dZ);
+    return cudaGetLastError();
+}
+
+}  // namespace shg

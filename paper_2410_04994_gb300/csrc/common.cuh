@@ -1,0 +1,81 @@
+// Shared device-side definitions of the SHG split-step kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define SHG_HD __host__ __device__ __forceinline__
+#define SHG_D __device__ __forceinline__
+
+// ----------------------------------------------------------- complex ----
+template <class R> struct Cx;
+template <> struct Cx<float> { using T = float2; };
+template <> struct Cx<double> { using T = double2; };
+template <class R> using cx = typename Cx<R>::T;
+
+// K-space factor entries: in single precision a (hi, lo) pair of float2 packed
+// in a float4, so that the multiply is exact to rounding (no per-step bias
+// from representing the factor in FP32); in double precision plain double2.
+template <class R> struct PropT;
+template <> struct PropT<float> { using T = float4; };
+template <> struct PropT<double> { using T = double2; };
+template <class R> using pt = typename PropT<R>::T;
+
+SHG_HD float2 pmul(float2 a, float4 p) {
+    float2 r;
+    r.x = fmaf(a.x, p.x, fmaf(-a.y, p.y, fmaf(a.x, p.z, -a.y * p.w)));
+    r.y = fmaf(a.x, p.y, fmaf(a.y, p.x, fmaf(a.x, p.w, a.y * p.z)));
+    return r;
+}
+SHG_HD double2 pmul(double2 a, double2 p) {
+    double2 r;
+    r.x = a.x * p.x - a.y * p.y;
+    r.y = a.x * p.y + a.y * p.x;
+    return r;
+}
+
+template <class C> SHG_HD C mk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
+template <class C> SHG_HD C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
+template <class C> SHG_HD C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+template <class C> SHG_HD C cmul(C a, C b) {
+    return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// a * conj(b)
+template <class C> SHG_HD C cmulc(C a, C b) {
+    return mk<C>(a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y);
+}
+template <class C> SHG_HD C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
+template <class C> SHG_HD C cconj(C a) { return mk<C>(a.x, -a.y); }
+
+// ------------------------------------------------------ per-instance ----
+// Everything one pass needs about one instance; built on the host by the plan.
+template <class R> struct InstDesc {
+    cx<R>* field;          // [2][ny][nx]: A_F then A_SH
+    const pt<R>* px;       // [2][nx] row factor exp(-i Kx^2 dz/2k_j) exp(-alpha_j dz/2) / nx
+    const pt<R>* py;       // [2][ny] column factor exp(-i Ky^2 dz/2k_j) / ny
+    const cx<R>* eph;      // [4 nz + 1] e^{i theta(q dz/4)}, theta = (dk0 + g T_off) z mod 2 pi
+    const float2* ttab;    // [tz][ty][tx] (dT, C) or nullptr for a uniform temperature
+    int tx, ty, tz;
+    float tx0, tdx_inv, ty0, tdy_inv, tdz_inv;  // node 0 position and 1/spacing of the map
+    R x0, dx, y0, dy;      // field sample positions x_m = x0 + m dx
+    R kF, kS;              // coupling constants (1/V)
+    R bF, bS;              // (1/2) beta_j (eps0 c n_j / 2): TPA factor per |A|^2
+    R lF, lS;              // (2 pi / lambda_j) dn/dT: lens phase per kelvin
+    R psi0F, psi0S;        // lens phase rate of the uniform offset T_off
+    R g;                   // dDk/dT
+    R dz;
+    int undepleted;
+    // heat deposits (THERMAL plans only)
+    double* Q;             // [hz][hy][hx] sum of q_dot dV
+    const int* hix;        // [nx] heat node of each column or -1
+    const int* hiy;        // [ny]
+    const int* hlz;        // [nz + 1] heat layer of each z_s or -1
+    int hx, hy, hz;
+    R qaF, qaS, qbF, qbS;  // alpha_j I-coefficient and beta_j I^2-coefficient per |A|^2, |A|^4
+    R dxdy;
+};
+
+// Error flag word shared by the kernels of one launch sequence.
+struct DevStatus {
+    int code;
+    int where;
+};

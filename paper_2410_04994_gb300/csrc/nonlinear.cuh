@@ -1,0 +1,141 @@
+// Pointwise nonlinear half-step N(dz/2) of the split-step method.
+//
+// Right-hand side (Eqs. (1)-(2) in the operator form of Eq. (11); diffraction
+// and linear absorption live in the K-space factor):
+//   f_F  = i kF A_SH conj(A_F) e^{-i phi} - bF |A_F|^2 A_F  + i psi_F A_F
+//   f_SH = i kS A_F^2 e^{+i phi}          - bS |A_SH|^2 A_SH + i psi_SH A_SH
+// with bj = (1/2) beta_j (eps0 c n_j / 2) so that bj |A|^2 = beta_j I_j / 2,
+// phi = theta(z) + g C(x,y,z) and psi_j = psi0_j + l_j dT(x,y,z).  theta is the
+// uniform part (dk0 + g T_off) z, reduced modulo 2 pi in double precision on
+// the host and tabulated as e^{i theta} at every quarter step.  One classical
+// RK4 step of size h = dz/2 advances each half step (stages at z0, z0+h/2,
+// z0+h/2, z0+h).
+#pragma once
+#include "common.cuh"
+
+namespace shg {
+
+template <class R> struct Coef {
+    R er, ei;  // e^{i phi}
+    R pF, pS;  // lens phase rates
+};
+
+// Clamped linear-interpolation cell along one axis of the temperature map.
+SHG_D void lin_cell(float u, int n, int& i, float& f) {
+    u = fminf(fmaxf(u, 0.f), float(n - 1));
+    i = min(int(floorf(u)), n - 2);
+    f = u - float(i);
+}
+
+// Bilinear sampling of the (dT, C) map at one field column/row pair, with the
+// z-layer chosen per stage; the two layers last used are kept.
+template <class R> struct TempSampler {
+    const float2* base;  // ttab + iy * tx + ix
+    int tx, plane;       // row stride and layer stride (floats2)
+    float fx, fy;
+    int la;              // layer held in va; vb holds la + 1
+    float2 va, vb;
+
+    SHG_D float2 bil(int l) const {
+        const float2* p = base + l * plane;
+        float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + tx), d = __ldg(p + tx + 1);
+        float2 r;
+        float ax = a.x + fx * (b.x - a.x), ay = a.y + fx * (b.y - a.y);
+        float cx = c.x + fx * (d.x - c.x), cy = c.y + fx * (d.y - c.y);
+        r.x = ax + fy * (cx - ax);
+        r.y = ay + fy * (cy - ay);
+        return r;
+    }
+    SHG_D float2 at(int l, float t) {
+        if (l != la) {
+            if (l == la + 1) {
+                va = vb;
+                vb = bil(l + 1);
+            } else {
+                va = bil(l);
+                vb = bil(l + 1);
+            }
+            la = l;
+        }
+        float2 r;
+        r.x = va.x + t * (vb.x - va.x);
+        r.y = va.y + t * (vb.y - va.y);
+        return r;
+    }
+};
+
+template <class R> SHG_D void sincos_r(R x, R* s, R* c);
+template <> SHG_D void sincos_r<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+template <> SHG_D void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+// Stage coefficients at quarter-step index q for the sampler's point.
+template <class R>
+SHG_D Coef<R> coef_at(const InstDesc<R>& d, int q, TempSampler<R>* ts) {
+    using C = cx<R>;
+    C e = d.eph[q];
+    Coef<R> k;
+    if (ts == nullptr) {
+        k.er = e.x; k.ei = e.y; k.pF = d.psi0F; k.pS = d.psi0S;
+        return k;
+    }
+    float u = float(q) * float(d.dz) * 0.25f * d.tdz_inv;
+    int l; float t;
+    lin_cell(u, d.tz, l, t);
+    float2 v = ts->at(l, t);  // (dT, C)
+    R s, c;
+    sincos_r<R>(d.g * R(v.y), &s, &c);
+    k.er = e.x * c - e.y * s;
+    k.ei = e.x * s + e.y * c;
+    k.pF = d.psi0F + d.lF * R(v.x);
+    k.pS = d.psi0S + d.lS * R(v.x);
+    return k;
+}
+
+template <class R>
+SHG_D void rhs(const InstDesc<R>& d, const Coef<R>& k, R afr, R afi, R asr, R asi,
+               R& fFr, R& fFi, R& fSr, R& fSi) {
+    const R aF2 = afr * afr + afi * afi;
+    const R aS2 = asr * asr + asi * asi;
+    const R gF = -d.bF * aF2;
+    fFr = gF * afr - k.pF * afi;
+    fFi = gF * afi + k.pF * afr;
+    if (!d.undepleted) {
+        const R tr = asr * afr + asi * afi;  // A_SH conj(A_F)
+        const R ti = asi * afr - asr * afi;
+        const R ur = tr * k.er + ti * k.ei;  // * e^{-i phi}
+        const R ui = ti * k.er - tr * k.ei;
+        fFr -= d.kF * ui;
+        fFi += d.kF * ur;
+    }
+    const R vr = afr * afr - afi * afi;  // A_F^2
+    const R vi = R(2) * afr * afi;
+    const R wr = vr * k.er - vi * k.ei;  // * e^{+i phi}
+    const R wi = vr * k.ei + vi * k.er;
+    const R gS = -d.bS * aS2;
+    fSr = -d.kS * wi + gS * asr - k.pS * asi;
+    fSi = d.kS * wr + gS * asi + k.pS * asr;
+}
+
+// One RK4 step of size h from the stage coefficients at z0, z0 + h/2, z0 + h.
+template <class R>
+SHG_D void rk4(const InstDesc<R>& d, cx<R>& aF, cx<R>& aS, const Coef<R>& c0,
+               const Coef<R>& cm, const Coef<R>& c1, R h) {
+    R k1Fr, k1Fi, k1Sr, k1Si, kFr, kFi, kSr, kSi;
+    rhs(d, c0, aF.x, aF.y, aS.x, aS.y, k1Fr, k1Fi, k1Sr, k1Si);
+    R accFr = k1Fr, accFi = k1Fi, accSr = k1Sr, accSi = k1Si;
+    const R hh = R(0.5) * h;
+    rhs(d, cm, aF.x + hh * k1Fr, aF.y + hh * k1Fi, aS.x + hh * k1Sr, aS.y + hh * k1Si,
+        kFr, kFi, kSr, kSi);
+    accFr += R(2) * kFr; accFi += R(2) * kFi; accSr += R(2) * kSr; accSi += R(2) * kSi;
+    rhs(d, cm, aF.x + hh * kFr, aF.y + hh * kFi, aS.x + hh * kSr, aS.y + hh * kSi,
+        kFr, kFi, kSr, kSi);
+    accFr += R(2) * kFr; accFi += R(2) * kFi; accSr += R(2) * kSr; accSi += R(2) * kSi;
+    rhs(d, c1, aF.x + h * kFr, aF.y + h * kFi, aS.x + h * kSr, aS.y + h * kSi,
+        kFr, kFi, kSr, kSi);
+    accFr += kFr; accFi += kFi; accSr += kSr; accSi += kSi;
+    const R h6 = h / R(6);
+    aF.x += h6 * accFr; aF.y += h6 * accFi;
+    aS.x += h6 * accSr; aS.y += h6 * accSi;
+}
+
+}  // namespace shg

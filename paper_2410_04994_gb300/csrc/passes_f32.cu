@@ -1,0 +1,39 @@
+// Single-precision instantiations of the row and column passes (n = 8..1024).
+#include "launch_passes.cuh"
+#include "plan.h"
+
+namespace shg {
+
+#define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+
+cudaError_t row_f32(int nx, const void* descs, int ninst, int ny, int nz, int s, const void* tw,
+                    cudaStream_t st) {
+    switch (nx) {
+#define X(n) case n: return row_launch<float, n>(descs, ninst, ny, nz, s, tw, st);
+        SHG_F32_SIZES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t col_f32(int ny, const void* descs, int ninst, int nx, const void* tw,
+                    cudaStream_t st) {
+    switch (ny) {
+#define X(n) case n: return col_launch<float, n>(descs, ninst, nx, tw, st);
+        SHG_F32_SIZES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t attr_f32() {
+    cudaError_t e = cudaSuccess;
+#define X(n)                                       \
+    if (e == cudaSuccess) e = row_attr<float, n>(); \
+    if (e == cudaSuccess) e = col_attr<float, n>();
+    SHG_F32_SIZES(X)
+#undef X
+    return e;
+}
+
+}  // namespace shg

@@ -1,0 +1,120 @@
+// Internal definitions shared by the host-side translation units of libshg.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/shg.h"
+#include "common.cuh"
+
+namespace shg {
+
+constexpr double kEps0 = 8.8541878128e-12;  // F/m
+constexpr double kCLight = 299792458.0;     // m/s
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kRedBlocks = 64;              // blocks per instance in the FP64 reductions
+
+// Extra per-instance inputs of the initial-field and reduction kernels.
+struct InitDesc {
+    double x0, dx, y0, dy;
+    double w0, zf, kF;      // Eq. (5) at z = 0
+    double p1;              // target discrete power
+    double cFdxdy;          // (1/2) eps0 c n_F dx dy
+    double cSdxdy;          // (1/2) eps0 c n_SH dx dy
+    double* red;            // [kRedBlocks][2] partial sums (plan-owned scratch)
+    double* pw;             // [2] P_F, P_SH results
+    const void* f0;         // custom initial fields [2][ny][nx] or nullptr
+};
+
+struct Adjoint;  // adjoint.cu
+struct Heat;     // heat.cu
+
+}  // namespace shg
+
+struct shg_plan {
+    shg_grid_t g;
+    shg_crystal_t c;
+    shg_beams_t b;
+    int flags = 0;
+    bool fp64 = false;
+    size_t csize = 8;         // bytes per complex element
+    int device = 0;
+
+    void* field = nullptr;    // [2][ny][nx] current state
+    void* field0 = nullptr;   // [2][ny][nx] custom initial state
+    bool custom_init = false;
+    void* px = nullptr;       // [2][nx]
+    void* py = nullptr;       // [2][ny]
+    void* pxc = nullptr;      // conjugate tables for the adjoint
+    void* pyc = nullptr;
+    void* eph = nullptr;      // [4 nz + 1]
+    void* tw = nullptr;       // [1024]
+    float2* ttab = nullptr;   // [tz][ty][tx] (dT, C)
+    float* tmap = nullptr;    // [tz][ty][tx] dT as set
+    int tx = 0, ty = 0, tz = 0;
+    double tlx = 0, tly = 0;
+    void* desc = nullptr;     // device InstDesc<R>[1]
+    shg::InitDesc* idesc = nullptr;  // device InitDesc[1]
+    double* red = nullptr;
+    double* pw = nullptr;
+    double pw_host[2] = {0, 0};
+    bool has_result = false;
+    bool batch_result = false;  // pw_host holds the last batch's powers
+    cudaStream_t last_stream = nullptr;
+
+    // heat grid
+    double* Q = nullptr;      // [hz][hy][hx]
+    int* hix = nullptr;
+    int* hiy = nullptr;
+    int* hlz = nullptr;
+    float* theat = nullptr;   // [hz][hy][hx] last solved dT
+    float* theat_prev = nullptr;
+    double* hred = nullptr;   // reduction scratch of the heat solve
+
+    // forward graph
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t cap = nullptr;
+    bool gvalid = false;
+
+    shg::Adjoint* adj = nullptr;
+};
+
+namespace shg {
+
+// status helpers
+shg_status_t cuda_fail(cudaError_t e, const char* what);
+#define SHG_CK(call)                                                 \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return ::shg::cuda_fail(e_, #call);   \
+    } while (0)
+
+// Fill host-side descriptors from the plan's current state.
+void fill_desc_f32(const shg_plan* p, InstDesc<float>* d);
+void fill_desc_f64(const shg_plan* p, InstDesc<double>* d);
+void fill_init(const shg_plan* p, InitDesc* d);
+
+// Kernel launchers (passes_f32.cu / passes_f64.cu / aux.cu).
+cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
+                       const void* tw, cudaStream_t st);
+cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
+                       cudaStream_t st);
+cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
+                        const void* descs, int nx, int ny, cudaStream_t st);
+cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
+                         int ny, cudaStream_t st);
+cudaError_t launch_build_ttab(const float* dT, float2* ttab, int tx, int ty, int tz, double dZ,
+                              cudaStream_t st);
+cudaError_t setup_pass_attributes();
+
+// Enqueue the whole forward propagation of instances sharing one grid.
+shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
+                             const InitDesc* idescs, int ninst, const void* tw,
+                             const std::vector<shg_plan*>& plans, cudaStream_t st);
+
+// Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
+void forget_plan_batches(shg_plan* p);
+void free_adjoint(shg_plan* p);
+
+}  // namespace shg

@@ -1,0 +1,76 @@
+"""Host-side checks of libshg.so that need no GPU: it loads, exports every
+entry point declared in include/shg.h, and rejects bad arguments before any
+device work."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2410_04994_gb300 import build
+    build.build()
+    import paper_2410_04994_gb300 as p
+    p.load()
+    return p
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "shg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(shg_[a-z_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(pkg):
+    names = declared()
+    assert len(names) >= 14
+    lib = ctypes.CDLL(pkg.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(pkg.EXPORTED)
+
+
+def test_status_strings(pkg):
+    for code in range(8):
+        assert pkg.shg_status_string(code) != "unknown status"
+    assert pkg.shg_status_string(99) == "unknown status"
+
+
+def _w(**kw):
+    import workloads as W
+    return W.plain_focused(n=32, nz=10, precision="f32").with_(**kw)
+
+
+@pytest.mark.parametrize("kw,flags,code", [
+    (dict(nx=12), 0, 2),
+    (dict(ny=2048), 0, 2),
+    (dict(nx=4), 0, 2),
+    (dict(nx=512), 1, 2),
+    (dict(nz=0), 0, 1),
+    (dict(lx=0.0), 0, 1),
+    (dict(w0=0.0), 0, 1),
+    (dict(p1=-1.0), 0, 1),
+    (dict(L=0.0), 0, 1),
+    (dict(hx=2, hy=8, hz=8), 2, 1),
+    (dict(hx=8, hy=8, hz=8, kappa_th=0.0), 2, 1),
+])
+def test_plan_create_rejects_bad_arguments(pkg, kw, flags, code):
+    w = _w(**kw)
+    with pytest.raises(pkg.ShgError) as ei:
+        pkg.shg_plan_create(*pkg.structs_from(w), flags)
+    assert ei.value.status == code
+
+
+def test_null_handles_are_rejected(pkg):
+    lib = pkg.load()
+    assert lib.shg_plan_create(None, None, None, 0, None) == 1
+    assert lib.shg_plan_destroy(None) == 0
+    assert lib.shg_propagate(None, None) == 1
+    assert lib.shg_efficiency(None, None, None, None) == 1
+    assert lib.shg_batch_submit(None, 0, None, None) == 1
+    assert lib.shg_propagate_adjoint(None, 1.0, None, None, None, None, None) == 1
+    assert lib.shg_heat_solve(None, 1, 1e-6, None, None, None) == 1
