@@ -177,6 +177,16 @@ shg_status_t shg_thermal_loop(shg_plan_t *plan, int n_outer, int max_sweeps, dou
 shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
                           shg_stream_t stream);
 
+/* Profiling aid.  Runs `nsteps` z-steps of the plans' row and column passes
+ * eagerly (not from a graph) on `stream`, grouped by grid as in
+ * shg_batch_submit, with a CUDA event pair around every launch.  For group g
+ * (g < *ngroups <= max_groups) it writes out[4g..4g+3] = {nx, ny, average
+ * row-pass ms, average column-pass ms} and inst_out[g] = instances in the
+ * group.  The plans' fields are advanced (use shg_propagate or
+ * shg_batch_submit afterwards for a clean result).  Synchronises `stream`. */
+shg_status_t shg_pass_times(shg_plan_t *const *plans, int n, int nsteps, double *out,
+                            int *inst_out, int max_groups, int *ngroups, shg_stream_t stream);
+
 /* Static description of a status code. */
 const char *shg_status_string(shg_status_t status);
 

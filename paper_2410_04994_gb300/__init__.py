@@ -78,6 +78,7 @@ _SIGS = {
     "shg_heat_solve": [_P, _I, _D, _DP, _IP, _P],
     "shg_thermal_loop": [_P, _I, _I, _D, _DP, _DP, _P],
     "shg_get_heat": [_P, _P, _P, _P],
+    "shg_pass_times": [ctypes.POINTER(_P), _I, _I, _DP, _IP, _I, _IP, _P],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
 
@@ -212,6 +213,19 @@ def shg_thermal_loop(plan: int, n_outer: int, max_sweeps: int = 100000, tol: flo
 
 def shg_get_heat(plan: int, q=None, dT=None, stream=None) -> None:
     _check(_lib().shg_get_heat(plan, _ptr(q), _ptr(dT), _stream(stream)), "shg_get_heat")
+
+
+def shg_pass_times(plans: Sequence[int], nsteps: int = 4, stream=None, max_groups: int = 16):
+    """Average row/column pass launch times per grid group (CUDA events)."""
+    n = len(plans)
+    arr = (_P * n)(*plans)
+    out = (_D * (4 * max_groups))()
+    inst = (_I * max_groups)()
+    ng = _I()
+    _check(_lib().shg_pass_times(arr, n, int(nsteps), out, inst, max_groups, ctypes.byref(ng),
+                                 _stream(stream)), "shg_pass_times")
+    return [dict(nx=int(out[4 * g]), ny=int(out[4 * g + 1]), row_ms=out[4 * g + 2],
+                 col_ms=out[4 * g + 3], instances=inst[g]) for g in range(ng.value)]
 
 
 def shg_status_string(status: int) -> str:

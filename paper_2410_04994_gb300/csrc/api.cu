@@ -1,6 +1,7 @@
 // C ABI of libshg: plan management, forward propagation and batched sweeps.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -173,16 +174,16 @@ template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void
     d->px = static_cast<const pt<R>*>(p->px);
     d->py = static_cast<const pt<R>*>(p->py);
     d->eph = static_cast<const cx<R>*>(p->eph);
-    d->ttab = p->ttab;
+    d->ttab = static_cast<const cx<R>*>(p->ttab);
     d->tx = p->tx;
     d->ty = p->ty;
     d->tz = p->tz;
     if (p->ttab) {
-        d->tx0 = float(-p->tlx / 2);
-        d->ty0 = float(-p->tly / 2);
-        d->tdx_inv = float((p->tx - 1) / p->tlx);
-        d->tdy_inv = float((p->ty - 1) / p->tly);
-        d->tdz_inv = float((p->tz - 1) / p->c.L);
+        d->tx0 = R(-p->tlx / 2);
+        d->ty0 = R(-p->tly / 2);
+        d->tdx_inv = R((p->tx - 1) / p->tlx);
+        d->tdy_inv = R((p->ty - 1) / p->tly);
+        d->tdz_inv = R((p->tz - 1) / p->c.L);
     }
     d->dx = R(p->g.lx / p->g.nx);
     d->dy = R(p->g.ly / p->g.ny);
@@ -274,8 +275,11 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
             if (e != cudaSuccess) return cuda_fail(e, "memset Q");
         }
     }
+    int hx = 0;
+    for (shg_plan* p : plans)
+        if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
     for (int s = 0; s <= nz; ++s) {
-        e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, st);
+        e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st);
         if (e != cudaSuccess) return cuda_fail(e, "row pass");
         if (s < nz) {
             e = launch_col(fp64, ny, descs, ninst, nx, tw, st);
@@ -371,7 +375,8 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
         if (grid->hx < 3 || grid->hy < 3 || grid->hz < 3 || !(crystal->wx > 0) ||
             !(crystal->wy > 0) || !(crystal->kappa_th > 0))
             return SHG_ERR_INVALID_ARG;
-        if (grid->hx > 2 * grid->nx + 64) return SHG_ERR_UNSUPPORTED_GRID;  // shared bins
+        // the row pass bins the heat deposit per CTA in shared memory
+        if (row_pass_smem(fp64, grid->nx, grid->hx) > 223 * 1024) return SHG_ERR_UNSUPPORTED_GRID;
     }
     shg_status_t st = ensure_attributes();
     if (st != SHG_OK) return st;
@@ -491,7 +496,7 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
         if (p->tmap) cudaFree(p->tmap);
         p->ttab = nullptr;
         p->tmap = nullptr;
-        SHG_CK(cudaMalloc((void**)&p->ttab, n * sizeof(float2)));
+        SHG_CK(cudaMalloc((void**)&p->ttab, n * p->csize));
         SHG_CK(cudaMalloc((void**)&p->tmap, n * sizeof(float)));
         p->gvalid = false;
     }
@@ -502,7 +507,7 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
     p->tly = t_ly > 0 ? t_ly : p->g.ly;
     if (dT_dev != p->tmap)
         SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    SHG_CK(launch_build_ttab(p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+    SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
     SHG_CK(cudaStreamSynchronize(s));
     return upload_desc(p);
 }
@@ -785,4 +790,72 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         p->batch_result = true;
     }
     return finite ? SHG_OK : SHG_ERR_NONFINITE;
+}
+
+extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nsteps, double* out,
+                                       int* inst_out, int max_groups, int* ngroups,
+                                       shg_stream_t stream) {
+    if (!plans || n <= 0 || nsteps <= 0 || !out || !ngroups || max_groups <= 0)
+        return SHG_ERR_INVALID_ARG;
+    std::vector<shg_plan*> key(plans, plans + n);
+    for (auto p : key)
+        if (!p) return SHG_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    BatchEntry* ent = nullptr;
+    shg_status_t r = build_entry(key, &ent);
+    if (r != SHG_OK) return r;
+    if ((r = refresh_entry(ent, st)) != SHG_OK) {
+        free_entry(ent);
+        return r;
+    }
+    const int ng = int(ent->groups.size());
+    if (ng > max_groups) {
+        free_entry(ent);
+        return SHG_ERR_INVALID_ARG;
+    }
+    std::vector<cudaEvent_t> ev(4 * nsteps * ng);
+    for (auto& e : ev) cudaEventCreate(&e);
+    cudaError_t e = cudaSuccess;
+    for (int s = 1; s <= nsteps && e == cudaSuccess; ++s) {
+        for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
+            BatchGroup& g = ent->groups[gi];
+            const int zs = std::min(s, g.nz - 1 > 0 ? g.nz - 1 : 0);
+            cudaEvent_t* E = &ev[4 * ((s - 1) * ng + gi)];
+            cudaEventRecord(E[0], st);
+            int hx = 0;
+            for (shg_plan* p : g.plans)
+                if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+            e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
+                           g.plans[0]->tw, hx, st);
+            cudaEventRecord(E[1], st);
+            if (e == cudaSuccess) {
+                cudaEventRecord(E[2], st);
+                e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st);
+                cudaEventRecord(E[3], st);
+            }
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) {
+        for (int gi = 0; gi < ng; ++gi) {
+            double tr = 0, tc = 0;
+            for (int s = 0; s < nsteps; ++s) {
+                cudaEvent_t* E = &ev[4 * (s * ng + gi)];
+                float a = 0, b = 0;
+                cudaEventElapsedTime(&a, E[0], E[1]);
+                cudaEventElapsedTime(&b, E[2], E[3]);
+                tr += a;
+                tc += b;
+            }
+            out[4 * gi] = ent->groups[gi].nx;
+            out[4 * gi + 1] = ent->groups[gi].ny;
+            out[4 * gi + 2] = tr / nsteps;
+            out[4 * gi + 3] = tc / nsteps;
+            if (inst_out) inst_out[gi] = int(ent->groups[gi].plans.size());
+        }
+        *ngroups = ng;
+    }
+    for (auto& x : ev) cudaEventDestroy(x);
+    free_entry(ent);
+    return e == cudaSuccess ? SHG_OK : cuda_fail(e, "shg_pass_times");
 }

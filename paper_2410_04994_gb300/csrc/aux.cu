@@ -3,17 +3,23 @@
 
 namespace shg {
 
-cudaError_t row_f32(int, const void*, int, int, int, int, const void*, cudaStream_t);
+cudaError_t row_f32(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+size_t row_smem_f32(int, int);
+size_t row_smem_f64(int, int);
 cudaError_t col_f32(int, const void*, int, int, const void*, cudaStream_t);
 cudaError_t attr_f32();
-cudaError_t row_f64(int, const void*, int, int, int, int, const void*, cudaStream_t);
+cudaError_t row_f64(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
 cudaError_t col_f64(int, const void*, int, int, const void*, cudaStream_t);
 cudaError_t attr_f64();
 
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
-                       const void* tw, cudaStream_t st) {
-    return fp64 ? row_f64(nx, descs, ninst, ny, nz, s, tw, st)
-                : row_f32(nx, descs, ninst, ny, nz, s, tw, st);
+                       const void* tw, int hx, cudaStream_t st) {
+    return fp64 ? row_f64(nx, descs, ninst, ny, nz, s, tw, hx, st)
+                : row_f32(nx, descs, ninst, ny, nz, s, tw, hx, st);
+}
+
+size_t row_pass_smem(bool fp64, int nx, int hx) {
+    return fp64 ? row_smem_f64(nx, hx) : row_smem_f32(nx, hx);
 }
 
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
@@ -187,27 +193,34 @@ cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, i
 }
 
 // (dT, C) table: C[l] = C[l-1] + dZ/2 (dT[l-1] + dT[l]) accumulated in double
-// (Eq. 3 by the trapezoid rule on the map's z-nodes).
-__global__ void k_build_ttab(const float* __restrict__ dT, float2* __restrict__ tt, int tx,
-                             int ty, int tz, double dZ) {
+// (Eq. 3 by the trapezoid rule on the map's z-nodes), stored in the plan's
+// precision.
+template <class V>
+__global__ void k_build_ttab(const float* __restrict__ dT, V* __restrict__ tt, int tx, int ty,
+                             int tz, double dZ) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= tx * ty) return;
     const size_t plane = size_t(tx) * ty;
     double c = 0;
     float prev = dT[col];
-    tt[col] = make_float2(prev, 0.f);
+    tt[col] = mk<V>(prev, 0);
     for (int l = 1; l < tz; ++l) {
         const float cur = dT[l * plane + col];
         c += 0.5 * dZ * (double(prev) + double(cur));
-        tt[l * plane + col] = make_float2(cur, float(c));
+        tt[l * plane + col] = mk<V>(cur, c);
         prev = cur;
     }
 }
 
-cudaError_t launch_build_ttab(const float* dT, float2* ttab, int tx, int ty, int tz, double dZ,
-                              cudaStream_t st) {
+cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
+                              double dZ, cudaStream_t st) {
     const int cols = tx * ty;
-    k_build_ttab<<<(cols + 127) / 128, 128, 0, st>>>(dT, ttab, tx, ty, tz, dZ);
+    if (fp64)
+        k_build_ttab<double2><<<(cols + 127) / 128, 128, 0, st>>>(dT, static_cast<double2*>(ttab),
+                                                                   tx, ty, tz, dZ);
+    else
+        k_build_ttab<float2><<<(cols + 127) / 128, 128, 0, st>>>(dT, static_cast<float2*>(ttab),
+                                                                  tx, ty, tz, dZ);
     return cudaGetLastError();
 }
 

@@ -53,9 +53,9 @@ template <class R> struct InstDesc {
     const pt<R>* px;       // [2][nx] row factor exp(-i Kx^2 dz/2k_j) exp(-alpha_j dz/2) / nx
     const pt<R>* py;       // [2][ny] column factor exp(-i Ky^2 dz/2k_j) / ny
     const cx<R>* eph;      // [4 nz + 1] e^{i theta(q dz/4)}, theta = (dk0 + g T_off) z mod 2 pi
-    const float2* ttab;    // [tz][ty][tx] (dT, C) or nullptr for a uniform temperature
+    const cx<R>* ttab;     // [tz][ty][tx] (dT, C) or nullptr for a uniform temperature
     int tx, ty, tz;
-    float tx0, tdx_inv, ty0, tdy_inv, tdz_inv;  // node 0 position and 1/spacing of the map
+    R tx0, tdx_inv, ty0, tdy_inv, tdz_inv;  // node 0 position and 1/spacing of the map
     R x0, dx, y0, dy;      // field sample positions x_m = x0 + m dx
     R kF, kS;              // coupling constants (1/V)
     R bF, bS;              // (1/2) beta_j (eps0 c n_j / 2): TPA factor per |A|^2
@@ -73,6 +73,20 @@ template <class R> struct InstDesc {
     R qaF, qaS, qbF, qbS;  // alpha_j I-coefficient and beta_j I^2-coefficient per |A|^2, |A|^4
     R dxdy;
 };
+
+// Asynchronous global -> shared copies (LDGSTS), so that a whole tile is in
+// flight at once without holding registers.
+template <class C> SHG_D void cp_async(C* smem_dst, const C* gsrc) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+SHG_D void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
 
 // Error flag word shared by the kernels of one launch sequence.
 struct DevStatus {

@@ -13,7 +13,9 @@
 // inverse transform.
 //
 // Stage twiddles come from one table W_1024^k = exp(-2 pi i k / 1024),
-// computed in double precision on the host and kept as (hi, lo) float pairs.
+// computed in double precision on the host and kept as (hi, lo) float pairs
+// (plainly rounded entries still left a measurable power drift over
+// thousands of steps).
 #pragma once
 #include "common.cuh"
 
@@ -183,55 +185,44 @@ template <int E, int T, class C> SHG_D void reload(C (&v)[E], const C* sm, int t
     for (int m = 0; m < E; ++m) v[m] = sm[pidx<RT>(t + T * m)];
 }
 
-// Forward (DIR = -1) or inverse (DIR = +1, unnormalised) transform of two
-// independent sequences (the two fields) that share the exchanges.  Every
-// thread of the block must call this (it contains __syncthreads).
+// Forward (DIR = -1) or inverse (DIR = +1, unnormalised) transform of one
+// sequence held as E registers per thread.  Every thread of the block must
+// call this (it contains __syncthreads).
 template <class RT, int N, int DIR, class C>
-SHG_D void fft2(C (&a)[FftCfg<RT, N>::E], C (&b)[FftCfg<RT, N>::E], C* sa, C* sb, int t,
-                const pt<RT>* __restrict__ tw) {
+SHG_D void fft1(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
     using F = FftCfg<RT, N>;
     constexpr int E = F::E, T = F::T;
     constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2;
     constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2);
     stage<N, E, T, R0, 1, L0, DIR>(a, sa, t, tw);
-    stage<N, E, T, R0, 1, L0, DIR>(b, sb, t, tw);
     if constexpr (F::NST >= 2) {
         __syncthreads();
         reload<E, T>(a, sa, t);
-        reload<E, T>(b, sb, t);
         __syncthreads();
         stage<N, E, T, (R1 > 1 ? R1 : 2), R0, L1, DIR>(a, sa, t, tw);
-        stage<N, E, T, (R1 > 1 ? R1 : 2), R0, L1, DIR>(b, sb, t, tw);
     }
     if constexpr (F::NST >= 3) {
         __syncthreads();
         reload<E, T>(a, sa, t);
-        reload<E, T>(b, sb, t);
         __syncthreads();
         stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, true, DIR>(a, sa, t, tw);
-        stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, true, DIR>(b, sb, t, tw);
     }
 }
 
-// FFT -> multiply by the per-bin factors pa[k], pb[k] -> inverse FFT, i.e.
-// the 1-D linear operator F^{-1} diag(p) F along the thread group's axis.
-// The 1/N of the inverse is folded into the factor tables.
+// FFT -> multiply by the per-bin factors p[k] -> inverse FFT, i.e. the 1-D
+// linear operator F^{-1} diag(p) F along the thread group's axis.  The 1/N of
+// the inverse is folded into the factor table.  No barrier is needed between
+// the two transforms: every thread has passed the barrier that follows the
+// forward transform's last reload before any inverse store happens.
 template <class RT, int N, class C>
-SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N>::E], C (&b)[FftCfg<RT, N>::E], C* sa, C* sb,
-                        int t, const pt<RT>* __restrict__ tw, const pt<RT>* __restrict__ pa,
-                        const pt<RT>* __restrict__ pb) {
+SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict__ tw,
+                        const pt<RT>* __restrict__ p) {
     using F = FftCfg<RT, N>;
     constexpr int E = F::E, T = F::T;
-    fft2<RT, N, -1>(a, b, sa, sb, t, tw);
+    fft1<RT, N, -1>(a, sa, t, tw);
 #pragma unroll
-    for (int m = 0; m < E; ++m) {
-        const int k = t + T * m;
-        a[m] = pmul(a[m], __ldg(&pa[k]));
-        b[m] = pmul(b[m], __ldg(&pb[k]));
-    }
-    // No barrier needed here: every thread passed the barrier that follows
-    // the forward transform's last reload before any inverse store happens.
-    fft2<RT, N, +1>(a, b, sa, sb, t, tw);
+    for (int m = 0; m < E; ++m) a[m] = pmul(a[m], __ldg(&p[t + T * m]));
+    fft1<RT, N, +1>(a, sa, t, tw);
 }
 
 }  // namespace shg

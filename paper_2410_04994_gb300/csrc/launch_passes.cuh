@@ -4,21 +4,35 @@
 
 namespace shg {
 
-template <class R, int N> cudaError_t row_attr() {
-    return cudaFuncSetAttribute(k_row_pass<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(RowGeom<R, N>::smem));
+// Largest dynamic shared memory a kernel may request: the device's opt-in
+// per-block limit minus the kernel's static shared memory.
+template <class K> cudaError_t allow_max_dyn_smem(K kernel) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes a;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&a, kernel);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 optin - int(a.sharedSizeBytes));
+    return e;
 }
-template <class R, int N> cudaError_t col_attr() {
-    return cudaFuncSetAttribute(k_col_pass<R, N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                int(ColGeom<R, N>::smem));
+
+template <class R, int N> cudaError_t row_attr() { return allow_max_dyn_smem(k_row_pass<R, N>); }
+
+// Dynamic shared memory of a row pass: transform buffers + deposit bins.
+template <class R, int N> size_t row_smem(int hx) {
+    return RowGeom<R, N>::smem + size_t(RowGeom<R, N>::ROWS) * hx * sizeof(float);
 }
+template <class R, int N> cudaError_t col_attr() { return allow_max_dyn_smem(k_col_pass<R, N>); }
 
 template <class R, int N>
 cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, const void* tw,
-                       cudaStream_t st) {
+                       int hx, cudaStream_t st) {
     using G = RowGeom<R, N>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    k_row_pass<R, N><<<grid, kPassThreads, G::smem, st>>>(
+    k_row_pass<R, N><<<grid, kPassThreads, row_smem<R, N>(hx), st>>>(
         static_cast<const InstDesc<R>*>(descs), ny, nz, s, static_cast<const pt<R>*>(tw));
     return cudaGetLastError();
 }

@@ -21,32 +21,34 @@ template <class R> struct Coef {
 };
 
 // Clamped linear-interpolation cell along one axis of the temperature map.
-SHG_D void lin_cell(float u, int n, int& i, float& f) {
-    u = fminf(fmaxf(u, 0.f), float(n - 1));
-    i = min(int(floorf(u)), n - 2);
-    f = u - float(i);
+template <class R> SHG_D void lin_cell(R u, int n, int& i, R& f) {
+    u = fmin(fmax(u, R(0)), R(n - 1));
+    i = min(int(floor(u)), n - 2);
+    f = u - R(i);
 }
 
 // Bilinear sampling of the (dT, C) map at one field column/row pair, with the
 // z-layer chosen per stage; the two layers last used are kept.
 template <class R> struct TempSampler {
-    const float2* base;  // ttab + iy * tx + ix
-    int tx, plane;       // row stride and layer stride (floats2)
-    float fx, fy;
+    using V = cx<R>;
+    const V* base;       // (dT, C) at (layer l0, row iy, column ix) of the global table
+    int tx, plane;       // row stride and layer stride of that storage
+    int l0;              // layer stored at `base`
+    R fx, fy;
     int la;              // layer held in va; vb holds la + 1
-    float2 va, vb;
+    V va, vb;
 
-    SHG_D float2 bil(int l) const {
-        const float2* p = base + l * plane;
-        float2 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + tx), d = __ldg(p + tx + 1);
-        float2 r;
-        float ax = a.x + fx * (b.x - a.x), ay = a.y + fx * (b.y - a.y);
-        float cx = c.x + fx * (d.x - c.x), cy = c.y + fx * (d.y - c.y);
+    SHG_D V bil(int l) const {
+        const V* p = base + (l - l0) * plane;
+        V a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + tx), d = __ldg(p + tx + 1);
+        V r;
+        R ax = a.x + fx * (b.x - a.x), ay = a.y + fx * (b.y - a.y);
+        R cx = c.x + fx * (d.x - c.x), cy = c.y + fx * (d.y - c.y);
         r.x = ax + fy * (cx - ax);
         r.y = ay + fy * (cy - ay);
         return r;
     }
-    SHG_D float2 at(int l, float t) {
+    SHG_D V at(int l, R t) {
         if (l != la) {
             if (l == la + 1) {
                 va = vb;
@@ -57,7 +59,7 @@ template <class R> struct TempSampler {
             }
             la = l;
         }
-        float2 r;
+        V r;
         r.x = va.x + t * (vb.x - va.x);
         r.y = va.y + t * (vb.y - va.y);
         return r;
@@ -65,23 +67,68 @@ template <class R> struct TempSampler {
 };
 
 template <class R> SHG_D void sincos_r(R x, R* s, R* c);
-template <> SHG_D void sincos_r<float>(float x, float* s, float* c) { sincosf(x, s, c); }
+// |g C| is a small phase in practice; the hardware approximation (absolute
+// error ~4e-7 on [-pi, pi]) is used there and the full-range routine outside.
+template <> SHG_D void sincos_r<float>(float x, float* s, float* c) {
+    if (fabsf(x) < 3.0f)
+        __sincosf(x, s, c);
+    else
+        sincosf(x, s, c);
+}
 template <> SHG_D void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
+
+// Per-CTA data of one stage point z_q = q dz/4: e^{i theta(z_q)} and the
+// temperature-map layer and fraction (the same for every point of the pass).
+template <class R> struct StageZ {
+    cx<R> e;
+    int l;
+    R t;
+};
+
+template <class R> SHG_D StageZ<R> stage_z(const InstDesc<R>& d, int q) {
+    StageZ<R> z;
+    z.e = d.eph[q];
+    z.l = 0;
+    z.t = R(0);
+    if (d.ttab != nullptr) lin_cell<R>(R(q) * d.dz * R(0.25) * d.tdz_inv, d.tz, z.l, z.t);
+    return z;
+}
+
+// Stage coefficients at a stage point for the sampler's point.
+template <class R>
+SHG_D Coef<R> coef_at(const InstDesc<R>& d, const StageZ<R>& z, bool thermal,
+                      TempSampler<R>& ts) {
+    using C = cx<R>;
+    Coef<R> k;
+    if (!thermal) {
+        k.er = z.e.x; k.ei = z.e.y; k.pF = d.psi0F; k.pS = d.psi0S;
+        return k;
+    }
+    const C v = ts.at(z.l, z.t);  // (dT, C)
+    R s, c;
+    sincos_r<R>(d.g * v.y, &s, &c);
+    k.er = z.e.x * c - z.e.y * s;
+    k.ei = z.e.x * s + z.e.y * c;
+    k.pF = d.psi0F + d.lF * v.x;
+    k.pS = d.psi0S + d.lS * v.x;
+    return k;
+}
 
 // Stage coefficients at quarter-step index q for the sampler's point.
 template <class R>
-SHG_D Coef<R> coef_at(const InstDesc<R>& d, int q, TempSampler<R>* ts) {
+SHG_D Coef<R> coef_at(const InstDesc<R>& d, int q, bool thermal, TempSampler<R>& ts) {
     using C = cx<R>;
     C e = d.eph[q];
     Coef<R> k;
-    if (ts == nullptr) {
+    if (!thermal) {
         k.er = e.x; k.ei = e.y; k.pF = d.psi0F; k.pS = d.psi0S;
         return k;
     }
-    float u = float(q) * float(d.dz) * 0.25f * d.tdz_inv;
-    int l; float t;
-    lin_cell(u, d.tz, l, t);
-    float2 v = ts->at(l, t);  // (dT, C)
+    const R u = R(q) * d.dz * R(0.25) * d.tdz_inv;
+    int l;
+    R t;
+    lin_cell<R>(u, d.tz, l, t);
+    const C v = ts.at(l, t);  // (dT, C)
     R s, c;
     sincos_r<R>(d.g * R(v.y), &s, &c);
     k.er = e.x * c - e.y * s;
@@ -133,7 +180,7 @@ SHG_D void rk4(const InstDesc<R>& d, cx<R>& aF, cx<R>& aS, const Coef<R>& c0,
     rhs(d, c1, aF.x + h * kFr, aF.y + h * kFi, aS.x + h * kSr, aS.y + h * kSi,
         kFr, kFi, kSr, kSi);
     accFr += kFr; accFi += kFi; accSr += kSr; accSi += kSi;
-    const R h6 = h / R(6);
+    const R h6 = h * (R(1) / R(6));
     aF.x += h6 * accFr; aF.y += h6 * accFi;
     aS.x += h6 * accSr; aS.y += h6 * accSi;
 }

@@ -37,153 +37,197 @@ template <class R, int N> struct ColGeom {
     static constexpr size_t smem = size_t(2) * TILE * S * sizeof(cx<R>);
 };
 
+// Where the row pass reads the temperature map from ([tz][ty][tx] storage with
+// the given strides, node (l0, iy0, ix0) at `base`).
+template <class R> struct MapView {
+    const cx<R>* base;
+    int stride, plane, l0, iy0, ix0;
+};
+
 // Temperature-map sampler for field point (xi, y).
 template <class R>
-SHG_D void make_sampler(const InstDesc<R>& d, int xi, int y, TempSampler<R>& ts) {
+SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, int y,
+                        TempSampler<R>& ts) {
     int ix, iy;
-    float fx, fy;
-    lin_cell((float(d.x0 + d.dx * R(xi)) - d.tx0) * d.tdx_inv, d.tx, ix, fx);
-    lin_cell((float(d.y0 + d.dy * R(y)) - d.ty0) * d.tdy_inv, d.ty, iy, fy);
-    ts.base = d.ttab + iy * d.tx + ix;
-    ts.tx = d.tx;
-    ts.plane = d.tx * d.ty;
+    R fx, fy;
+    lin_cell<R>((d.x0 + d.dx * R(xi) - d.tx0) * d.tdx_inv, d.tx, ix, fx);
+    lin_cell<R>((d.y0 + d.dy * R(y) - d.ty0) * d.tdy_inv, d.ty, iy, fy);
+    ts.base = mv.base + (iy - mv.iy0) * mv.stride + (ix - mv.ix0);
+    ts.tx = mv.stride;
+    ts.plane = mv.plane;
+    ts.l0 = mv.l0;
     ts.fx = fx;
     ts.fy = fy;
     ts.la = -2;
 }
 
-// Per-row heat deposit at z_s: q_dot dV of each point, summed per heat node in
-// shared memory, then added to the heat grid in double precision.
-template <class R, int N>
-SHG_D void deposit_row(const InstDesc<R>& d, const cx<R> (&vF)[FftCfg<R, N>::E],
-                       const cx<R> (&vS)[FftCfg<R, N>::E], float* bins, int lr, int t,
-                       int y, bool active, int s, int nz) {
-    using G = RowGeom<R, N>;
-    constexpr int E = FftCfg<R, N>::E, T = G::T, ROWS = G::ROWS;
-    const int nb = ROWS * d.hx;
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) bins[i] = 0.f;
-    __syncthreads();
-    const int l = d.hlz[s];
-    const int j = active ? d.hiy[y] : -1;
-    if (l >= 0 && j >= 0) {
-        const R w = d.dxdy * d.dz * ((s == 0 || s == nz) ? R(0.5) : R(1));
-#pragma unroll
-        for (int m = 0; m < E; ++m) {
-            const int i = __ldg(&d.hix[t + T * m]);
-            if (i < 0) continue;
-            const R aF2 = vF[m].x * vF[m].x + vF[m].y * vF[m].y;
-            const R aS2 = vS[m].x * vS[m].x + vS[m].y * vS[m].y;
-            const R q = aF2 * (d.qaF + d.qbF * aF2) + aS2 * (d.qaS + d.qbS * aS2);
-            atomicAdd(&bins[lr * d.hx + i], float(q * w));
-        }
-    }
-    __syncthreads();
-    const int y0 = blockIdx.x * ROWS;
-    for (int k = threadIdx.x; k < nb; k += blockDim.x) {
-        const float v = bins[k];
-        const int r = k / d.hx, i = k - r * d.hx;
-        const int yy = y0 + r;
-        if (v != 0.f && l >= 0) {
-            const int jj = d.hiy[yy];
-            atomicAdd(&d.Q[(size_t(l) * d.hy + jj) * d.hx + i], double(v));
-        }
-    }
-    __syncthreads();
-}
-
 // Row pass R(s).  grid = (ceil(ny / ROWS), instances); block = 256.
+//
+// The CTA's rows of both fields are copied into padded shared buffers with
+// cp.async (all copies in flight at once).  Each thread owns the points
+// x = t + T*m of its row; the nonlinear part runs point by point in a rolled
+// loop on the shared copy, so no register array is indexed dynamically, and
+// the transforms then run field by field from the same buffers.  The heat
+// deposit at z_s (THERMAL plans) is binned per CTA in shared memory and added
+// to the heat grid with one double-precision atomic per touched node.
 template <class R, int NX>
-__global__ void __launch_bounds__(kPassThreads)
+__global__ void __launch_bounds__(kPassThreads, 2)
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
     using C = cx<R>;
     using G = RowGeom<R, NX>;
     constexpr int E = FftCfg<R, NX>::E, T = G::T, ROWS = G::ROWS, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ InstDesc<R> dsh;
+    __shared__ StageZ<R> zsh[5];
     C* smem = reinterpret_cast<C*>(smem_raw);
-    const InstDesc<R>& d = descs[blockIdx.y];
     const int lr = threadIdx.x / T, t = threadIdx.x - (threadIdx.x / T) * T;
     const int y = blockIdx.x * ROWS + lr;
     const bool active = y < ny;
-    C* rowF = d.field + size_t(y) * NX;
-    C* rowS = d.field + (size_t(ny) + y) * NX;
-    C vF[E], vS[E];
-    if (active) {
+    C* sF = smem + lr * S;
+    C* sS = smem + (ROWS + lr) * S;
+    {
+        const InstDesc<R>& dg = descs[blockIdx.y];
+        C* rowF = dg.field + size_t(y) * NX;
+        C* rowS = dg.field + (size_t(ny) + y) * NX;
+        if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            vF[m] = rowF[t + T * m];
-            vS[m] = rowS[t + T * m];
+            for (int m = 0; m < E; ++m) {
+                cp_async(&sF[pidx<R>(t + T * m)], &rowF[t + T * m]);
+                cp_async(&sS[pidx<R>(t + T * m)], &rowS[t + T * m]);
+            }
+        }
+        if (threadIdx.x == 0) dsh = dg;
+        if (threadIdx.x < 5) {
+            const int q = 4 * s - 2 + threadIdx.x;
+            zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
     }
+    const bool dep = descs[blockIdx.y].Q != nullptr;
+    float* bins = reinterpret_cast<float*>(smem + 2 * ROWS * S);
+    const int nb = dep ? ROWS * descs[blockIdx.y].hx : 0;
+    for (int i = threadIdx.x; i < nb; i += kPassThreads) bins[i] = 0.f;
+    __syncthreads();
+    const InstDesc<R>& d = dsh;
     const bool thermal = d.ttab != nullptr;
+    const MapView<R> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
+    cp_async_wait_all();
+    __syncthreads();
     const R h = R(0.5) * d.dz;
-    // heat deposit needs the state at z_s, i.e. after N_b(s-1)
-    if (s > 0 && active) {
-#pragma unroll 1
-        for (int m = 0; m < E; ++m) {
-            TempSampler<R> ts;
-            TempSampler<R>* tsp = thermal ? (make_sampler(d, t + T * m, y, ts), &ts) : nullptr;
-            const Coef<R> c0 = coef_at(d, 4 * s - 2, tsp);
-            const Coef<R> cm = coef_at(d, 4 * s - 1, tsp);
-            const Coef<R> c1 = coef_at(d, 4 * s, tsp);
-            rk4(d, vF[m], vS[m], c0, cm, c1, h);
+    const int l_dep = dep ? d.hlz[s] : -1;
+    const int j_dep = (dep && active) ? d.hiy[y] : -1;
+    const R w_dep = dep ? d.dxdy * d.dz * ((s == 0 || s == nz) ? R(0.5) : R(1)) : R(0);
+    // One point: N_b(s-1) [z_s - dz/2 -> z_s], deposit at z_s, N_a(s).
+    auto point = [&](int xi, C& aF, C& aS) {
+        TempSampler<R> ts;
+        if (thermal) make_sampler(d, mv, xi, y, ts);
+        const Coef<R> cz = coef_at(d, zsh[2], thermal, ts);  // z_s, shared by both halves
+        if (s > 0) {
+            const Coef<R> c0 = coef_at(d, zsh[0], thermal, ts);
+            const Coef<R> cm = coef_at(d, zsh[1], thermal, ts);
+            rk4(d, aF, aS, c0, cm, cz, h);
         }
-    }
-    if (d.Q != nullptr) deposit_row<R, NX>(d, vF, vS, reinterpret_cast<float*>(smem), lr, t, y,
-                                           active, s, nz);
-    if (s < nz && active) {
-#pragma unroll 1
-        for (int m = 0; m < E; ++m) {
-            TempSampler<R> ts;
-            TempSampler<R>* tsp = thermal ? (make_sampler(d, t + T * m, y, ts), &ts) : nullptr;
-            const Coef<R> c0 = coef_at(d, 4 * s, tsp);
-            const Coef<R> cm = coef_at(d, 4 * s + 1, tsp);
-            const Coef<R> c1 = coef_at(d, 4 * s + 2, tsp);
-            rk4(d, vF[m], vS[m], c0, cm, c1, h);
+        if (l_dep >= 0 && j_dep >= 0) {
+            const int i = __ldg(&d.hix[xi]);
+            if (i >= 0) {
+                const R aF2 = aF.x * aF.x + aF.y * aF.y;
+                const R aS2 = aS.x * aS.x + aS.y * aS.y;
+                const R q = aF2 * (d.qaF + d.qbF * aF2) + aS2 * (d.qaS + d.qbS * aS2);
+                atomicAdd(&bins[lr * d.hx + i], float(q * w_dep));
+            }
         }
-    }
-    if (s < nz) {
-        fft_mul_ifft<R, NX>(vF, vS, smem + lr * S, smem + (ROWS + lr) * S, t, tw, d.px,
-                            d.px + NX);
-    }
+        if (s < nz) {
+            const Coef<R> cm = coef_at(d, zsh[3], thermal, ts);
+            const Coef<R> c1 = coef_at(d, zsh[4], thermal, ts);
+            rk4(d, aF, aS, cz, cm, c1, h);
+        }
+    };
     if (active) {
+        // two independent points per iteration give the scheduler two RK4
+        // dependency chains to interleave
+#pragma unroll 1
+        for (int m = 0; m < E; m += 2) {
+            const int x0 = t + T * m, x1 = x0 + T;
+            C aF0 = sF[pidx<R>(x0)], aS0 = sS[pidx<R>(x0)];
+            C aF1 = sF[pidx<R>(x1)], aS1 = sS[pidx<R>(x1)];
+            point(x0, aF0, aS0);
+            point(x1, aF1, aS1);
+            sF[pidx<R>(x0)] = aF0;
+            sS[pidx<R>(x0)] = aS0;
+            sF[pidx<R>(x1)] = aF1;
+            sS[pidx<R>(x1)] = aS1;
+        }
+    }
+    if (dep) {
+        __syncthreads();
+        const int y0 = blockIdx.x * ROWS;
+        for (int k = threadIdx.x; k < nb; k += kPassThreads) {
+            const float v = bins[k];
+            if (v != 0.f && l_dep >= 0) {
+                const int r = k / d.hx, i = k - r * d.hx;
+                const int jj = d.hiy[y0 + r];
+                atomicAdd(&d.Q[(size_t(l_dep) * d.hy + jj) * d.hx + i], double(v));
+            }
+        }
+    }
+    // Lx on each field in turn (none in the last pass); results to global.
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        C* sb = f == 0 ? sF : sS;
+        C* row = d.field + (size_t(f) * ny + y) * NX;
+        C v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            rowF[t + T * m] = vF[m];
-            rowS[t + T * m] = vS[m];
+        for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
+        if (s < nz) {
+            __syncthreads();  // the transform's first stores reuse the staging buffer
+            fft_mul_ifft<R, NX>(v, sb, t, tw, d.px + f * NX);
+        }
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) row[t + T * m] = v[m];
         }
     }
 }
 
 // Column pass C(s).  grid = (ceil(nx / TILE), instances); block = 256.
+// The TILE columns of both fields are staged into padded shared buffers with
+// cp.async, transformed field by field, and written back from registers.
 template <class R, int NY>
-__global__ void __launch_bounds__(kPassThreads)
+__global__ void __launch_bounds__(kPassThreads, 2)
     k_col_pass(const InstDesc<R>* __restrict__ descs, int nx, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
     using G = ColGeom<R, NY>;
     constexpr int E = FftCfg<R, NY>::E, T = G::T, TILE = G::TILE, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
-    const InstDesc<R>& d = descs[blockIdx.y];
+    C* field = descs[blockIdx.y].field;
+    const pt<R>* py = descs[blockIdx.y].py;
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = blockIdx.x * TILE + c;
     const bool active = x < nx;
-    C* colF = d.field + x;
-    C* colS = d.field + size_t(NY) * nx + x;
-    C vF[E], vS[E];
     if (active) {
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            vF[m] = colF[size_t(t + T * m) * nx];
-            vS[m] = colS[size_t(t + T * m) * nx];
+        for (int f = 0; f < 2; ++f) {
+            const C* col = field + size_t(f) * NY * nx + x;
+            C* sb = smem + (f * TILE + c) * S;
+#pragma unroll
+            for (int m = 0; m < E; ++m)
+                cp_async(&sb[pidx<R>(t + T * m)], col + size_t(t + T * m) * nx);
         }
     }
-    fft_mul_ifft<R, NY>(vF, vS, smem + c * S, smem + (TILE + c) * S, t, tw, d.py, d.py + NY);
-    if (active) {
+    cp_async_wait_all();
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        C* sb = smem + (f * TILE + c) * S;
+        C v[E];
 #pragma unroll
-        for (int m = 0; m < E; ++m) {
-            colF[size_t(t + T * m) * nx] = vF[m];
-            colS[size_t(t + T * m) * nx] = vS[m];
+        for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
+        __syncthreads();  // all staged values read before the transform's stores
+        fft_mul_ifft<R, NY>(v, sb, t, tw, py + f * NY);
+        if (active) {
+            C* col = field + size_t(f) * NY * nx + x;
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
         }
     }
 }

@@ -7,9 +7,9 @@ namespace shg {
 #define SHG_F64_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256)
 
 cudaError_t row_f64(int nx, const void* descs, int ninst, int ny, int nz, int s, const void* tw,
-                    cudaStream_t st) {
+                    int hx, cudaStream_t st) {
     switch (nx) {
-#define X(n) case n: return row_launch<double, n>(descs, ninst, ny, nz, s, tw, st);
+#define X(n) case n: return row_launch<double, n>(descs, ninst, ny, nz, s, tw, hx, st);
         SHG_F64_SIZES(X)
 #undef X
     }
@@ -34,6 +34,15 @@ cudaError_t attr_f64() {
     SHG_F64_SIZES(X)
 #undef X
     return e;
+}
+
+size_t row_smem_f64(int nx, int hx) {
+    switch (nx) {
+#define X(n) case n: return row_smem<double, n>(hx);
+        SHG_F64_SIZES(X)
+#undef X
+    }
+    return 0;
 }
 
 }  // namespace shg

@@ -50,7 +50,7 @@ struct shg_plan {
     void* pyc = nullptr;
     void* eph = nullptr;      // [4 nz + 1]
     void* tw = nullptr;       // [1024]
-    float2* ttab = nullptr;   // [tz][ty][tx] (dT, C)
+    void* ttab = nullptr;     // [tz][ty][tx] (dT, C) in the plan's precision
     float* tmap = nullptr;    // [tz][ty][tx] dT as set
     int tx = 0, ty = 0, tz = 0;
     double tlx = 0, tly = 0;
@@ -97,15 +97,16 @@ void fill_init(const shg_plan* p, InitDesc* d);
 
 // Kernel launchers (passes_f32.cu / passes_f64.cu / aux.cu).
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
-                       const void* tw, cudaStream_t st);
+                       const void* tw, int hx, cudaStream_t st);
+size_t row_pass_smem(bool fp64, int nx, int hx);
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
                        cudaStream_t st);
 cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
                         const void* descs, int nx, int ny, cudaStream_t st);
 cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
                          int ny, cudaStream_t st);
-cudaError_t launch_build_ttab(const float* dT, float2* ttab, int tx, int ty, int tz, double dZ,
-                              cudaStream_t st);
+cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
+                              double dZ, cudaStream_t st);
 cudaError_t setup_pass_attributes();
 
 // Enqueue the whole forward propagation of instances sharing one grid.
