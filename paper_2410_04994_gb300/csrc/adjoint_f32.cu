@@ -1,0 +1,34 @@
+// Single-precision instantiations of the transposed row pass.
+#include "adjoint_pass.cuh"
+#include "launch_passes.cuh"
+
+namespace shg {
+
+template <class R, int N>
+static cudaError_t row_adj_launch(const void* dl, const void* Y, AdjAcc acc, int ny, int nz,
+                                  int s, const void* tw, cudaStream_t st) {
+    using G = RowGeom<R, N>;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = allow_max_dyn_smem(k_row_adj<R, N>);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    dim3 grid((ny + G::ROWS - 1) / G::ROWS, 1);
+    k_row_adj<R, N><<<grid, kPassThreads, G::smem, st>>>(
+        static_cast<const InstDesc<R>*>(dl), static_cast<const cx<R>*>(Y), acc, ny, nz, s,
+        static_cast<const pt<R>*>(tw));
+    return cudaGetLastError();
+}
+
+cudaError_t row_adj_f32(int nx, const void* dl, const void* Y, AdjAcc acc, int ny, int nz, int s,
+                        const void* tw, cudaStream_t st) {
+    switch (nx) {
+#define X(n) case n: return row_adj_launch<float, n>(dl, Y, acc, ny, nz, s, tw, st);
+        X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace shg

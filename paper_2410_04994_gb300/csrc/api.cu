@@ -279,6 +279,10 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
     for (int s = 0; s <= nz; ++s) {
+        for (shg_plan* p : plans) {
+            shg_status_t r = adjoint_checkpoint(p, s, st);
+            if (r != SHG_OK) return r;
+        }
         e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st);
         if (e != cudaSuccess) return cuda_fail(e, "row pass");
         if (s < nz) {
@@ -429,7 +433,8 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     if ((st = build_prop_tables(p)) != SHG_OK || (st = build_phase_table(p)) != SHG_OK ||
         (st = build_twiddles(p)) != SHG_OK ||
         ((flags & SHG_FLAG_THERMAL) && (st = build_heat_index(p)) != SHG_OK) ||
-        (st = upload_desc(p)) != SHG_OK) {
+        (st = upload_desc(p)) != SHG_OK ||
+        ((flags & SHG_FLAG_ADJOINT) && (st = adjoint_alloc(p)) != SHG_OK)) {
         plan_free(p);
         return st;
     }

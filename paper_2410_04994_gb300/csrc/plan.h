@@ -117,5 +117,8 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);
 void free_adjoint(shg_plan* p);
+shg_status_t adjoint_alloc(shg_plan* p);
+// Enqueue the checkpoint copy of the state entering row pass R(s) (adjoint plans).
+shg_status_t adjoint_checkpoint(shg_plan* p, int s, cudaStream_t st);
 
 }  // namespace shg
