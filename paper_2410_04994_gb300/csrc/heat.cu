@@ -1,16 +1,192 @@
-// Heat solve (red-black SOR) and the self-consistent loop.
+// Steady heat solve (Eq. 7 discretised as Eq. 16, Dirichlet T = T_oven on all
+// faces, Eq. 9) by red-black successive over-relaxation, and the
+// self-consistent loop of Fig. 2.
+//
+// Unknown: dT = T - T_oven on the node grid [hz][hy][hx] spanning the crystal
+// [-wx/2, wx/2] x [-wy/2, wy/2] x [0, L], zero on the faces.  Source: the heat
+// deposited by the last THERMAL propagation, q_dot = Q / (dx dy dz) at each
+// node (Q = sum of q_dot dV of the field samples binned to the node).
+// SOR factor omega = 2 / (1 + sqrt(1 - rho_J^2)) with rho_J the Jacobi
+// spectral radius of the anisotropic stencil.  Convergence: the largest Jacobi
+// correction over the interior, checked after every full (red + black) sweep.
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "plan.h"
 
-extern "C" shg_status_t shg_heat_solve(shg_plan_t* p, int, double, double*, int*, shg_stream_t) {
-    if (!p) return SHG_ERR_INVALID_ARG;
-    return SHG_ERR_STATE;
+namespace shg {
+
+struct HeatGeom {
+    int hx, hy, hz;
+    float ax, ay, az;  // 1/dx^2, 1/dy^2, 1/dz^2
+    float invD;        // 1 / (2 (ax + ay + az))
+    float qs;          // 1 / (kappa dx dy dz): Q -> q_dot / kappa
+    float omega;
+};
+
+static HeatGeom heat_geom(const shg_plan* p) {
+    HeatGeom g;
+    g.hx = p->g.hx;
+    g.hy = p->g.hy;
+    g.hz = p->g.hz;
+    const double dx = p->c.wx / (g.hx - 1), dy = p->c.wy / (g.hy - 1), dz = p->c.L / (g.hz - 1);
+    const double ax = 1 / (dx * dx), ay = 1 / (dy * dy), az = 1 / (dz * dz);
+    g.ax = float(ax);
+    g.ay = float(ay);
+    g.az = float(az);
+    g.invD = float(1.0 / (2.0 * (ax + ay + az)));
+    g.qs = float(1.0 / (p->c.kappa_th * dx * dy * dz));
+    const double rho = (ax * std::cos(kPi / (g.hx - 1)) + ay * std::cos(kPi / (g.hy - 1)) +
+                        az * std::cos(kPi / (g.hz - 1))) / (ax + ay + az);
+    g.omega = float(2.0 / (1.0 + std::sqrt(1.0 - rho * rho)));
+    return g;
 }
-extern "C" shg_status_t shg_thermal_loop(shg_plan_t* p, int, int, double, double*, double*,
-                                         shg_stream_t) {
-    if (!p) return SHG_ERR_INVALID_ARG;
-    return SHG_ERR_STATE;
+
+__device__ __forceinline__ float jacobi_target(const float* T, const double* Q, const HeatGeom& g,
+                                               size_t c) {
+    const size_t plane = size_t(g.hx) * g.hy;
+    const float s = g.ax * (T[c - 1] + T[c + 1]) + g.ay * (T[c - g.hx] + T[c + g.hx]) +
+                    g.az * (T[c - plane] + T[c + plane]) + float(Q[c]) * g.qs;
+    return s * g.invD;
 }
-extern "C" shg_status_t shg_get_heat(shg_plan_t* p, double*, float*, shg_stream_t) {
+
+// One colour of a red-black sweep: nodes with (i + j + l) % 2 == colour.
+// grid = (ceil((hx - 2 + 1) / 2 / 128), hy - 2, hz - 2), block = 128.
+__global__ void k_sor_colour(float* __restrict__ T, const double* __restrict__ Q, HeatGeom g,
+                             int colour) {
+    const int j = blockIdx.y + 1, l = blockIdx.z + 1;
+    const int i0 = 1 + ((colour + 1 + j + l) & 1);  // first interior i of this colour
+    const int i = i0 + 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    if (i > g.hx - 2) return;
+    const size_t c = (size_t(l) * g.hy + j) * g.hx + i;
+    const float t = T[c];
+    T[c] = t + g.omega * (jacobi_target(T, Q, g, c) - t);
+}
+
+// Largest |Jacobi correction| over the interior (non-negative floats compare
+// as their bit patterns).  grid = (ceil((hx-2)/128), hy - 2, hz - 2).
+__global__ void k_max_correction(const float* __restrict__ T, const double* __restrict__ Q,
+                                 HeatGeom g, unsigned* __restrict__ out) {
+    const int j = blockIdx.y + 1, l = blockIdx.z + 1;
+    const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
+    float v = 0.f;
+    if (i <= g.hx - 2) {
+        const size_t c = (size_t(l) * g.hy + j) * g.hx + i;
+        v = fabsf(jacobi_target(T, Q, g, c) - T[c]);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+}
+
+__global__ void k_max_abs_diff(const float* __restrict__ a, const float* __restrict__ b, size_t n,
+                               unsigned* __restrict__ out) {
+    float v = 0.f;
+    for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n;
+         k += size_t(gridDim.x) * blockDim.x)
+        v = fmaxf(v, fabsf(a[k] - b[k]));
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+}
+
+static shg_status_t max_correction(shg_plan* p, const HeatGeom& g, cudaStream_t st, float* out) {
+    unsigned* d = reinterpret_cast<unsigned*>(p->hred);
+    SHG_CK(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+    dim3 grid((g.hx - 2 + 127) / 128, g.hy - 2, g.hz - 2);
+    k_max_correction<<<grid, 128, 0, st>>>(p->theat, p->Q, g, d);
+    SHG_CK(cudaGetLastError());
+    unsigned h = 0;
+    SHG_CK(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    SHG_CK(cudaStreamSynchronize(st));
+    memcpy(out, &h, sizeof(float));
+    return SHG_OK;
+}
+
+static shg_status_t sor(shg_plan* p, int max_sweeps, double tol, double* resid, int* sweeps,
+                        cudaStream_t st) {
+    const HeatGeom g = heat_geom(p);
+    float corr = 0;
+    shg_status_t r = max_correction(p, g, st, &corr);
+    if (r != SHG_OK) return r;
+    int n = 0;
+    const int half = (g.hx - 2 + 1) / 2;
+    dim3 grid((half + 127) / 128, g.hy - 2, g.hz - 2);
+    while (double(corr) >= tol && n < max_sweeps) {
+        k_sor_colour<<<grid, 128, 0, st>>>(p->theat, p->Q, g, 0);
+        k_sor_colour<<<grid, 128, 0, st>>>(p->theat, p->Q, g, 1);
+        SHG_CK(cudaGetLastError());
+        ++n;
+        if ((r = max_correction(p, g, st, &corr)) != SHG_OK) return r;
+        if (!std::isfinite(corr)) return SHG_ERR_NONFINITE;
+    }
+    if (resid) *resid = corr;
+    if (sweeps) *sweeps = n;
+    return SHG_OK;
+}
+
+static shg_status_t install_map(shg_plan* p, cudaStream_t st) {
+    return shg_set_temperature(p, p->theat, p->g.hx, p->g.hy, p->g.hz, p->c.wx, p->c.wy,
+                               reinterpret_cast<shg_stream_t>(st));
+}
+
+}  // namespace shg
+
+using namespace shg;
+
+extern "C" shg_status_t shg_heat_solve(shg_plan_t* p, int max_sweeps, double tol, double* resid,
+                                       int* sweeps, shg_stream_t stream) {
+    if (!p || max_sweeps < 0 || !(tol > 0)) return SHG_ERR_INVALID_ARG;
+    if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    shg_status_t r = sor(p, max_sweeps, tol, resid, sweeps, st);
+    if (r != SHG_OK) return r;
+    return install_map(p, st);
+}
+
+extern "C" shg_status_t shg_get_heat(shg_plan_t* p, double* q_dev, float* dT_dev,
+                                     shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;
-    return SHG_ERR_STATE;
+    if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->has_result && p->last_stream != st) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
+    if (q_dev) SHG_CK(cudaMemcpyAsync(q_dev, p->Q, nh * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (dT_dev)
+        SHG_CK(cudaMemcpyAsync(dT_dev, p->theat, nh * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    return SHG_OK;
+}
+
+extern "C" shg_status_t shg_thermal_loop(shg_plan_t* p, int n_outer, int max_sweeps, double tol,
+                                         double* eta_out, double* change_out,
+                                         shg_stream_t stream) {
+    if (!p || n_outer < 1 || max_sweeps < 0 || !(tol > 0)) return SHG_ERR_INVALID_ARG;
+    if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
+    // q_dot = 0 before the first pass: dT = 0
+    SHG_CK(cudaMemsetAsync(p->theat, 0, nh * sizeof(float), st));
+    SHG_CK(cudaMemsetAsync(p->Q, 0, nh * sizeof(double), st));
+    for (int it = 0; it < n_outer; ++it) {
+        SHG_CK(cudaMemcpyAsync(p->theat_prev, p->theat, nh * sizeof(float),
+                               cudaMemcpyDeviceToDevice, st));
+        shg_status_t r = sor(p, max_sweeps, tol, nullptr, nullptr, st);
+        if (r != SHG_OK) return r;
+        unsigned* d = reinterpret_cast<unsigned*>(p->hred);
+        SHG_CK(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+        k_max_abs_diff<<<256, 256, 0, st>>>(p->theat, p->theat_prev, nh, d);
+        SHG_CK(cudaGetLastError());
+        unsigned h = 0;
+        SHG_CK(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        if ((r = install_map(p, st)) != SHG_OK) return r;  // synchronises st
+        float change;
+        memcpy(&change, &h, sizeof(float));
+        if ((r = shg_propagate(p, stream)) != SHG_OK) return r;
+        double eta = 0;
+        if ((r = shg_efficiency(p, &eta, nullptr, nullptr)) != SHG_OK) return r;
+        if (eta_out) eta_out[it] = eta;
+        if (change_out) change_out[it] = change;
+    }
+    return SHG_OK;
 }

@@ -1,0 +1,84 @@
+"""GPU heat deposits, red-black SOR and the self-consistent loop vs the oracle.
+
+Each side runs the whole chain from the same workload (its own deposits, its
+own SOR): heat deposits to a relative L2 error of 1e-4, dT to 1e-3 of its
+maximum (both solvers stop at a Jacobi correction below 1e-6 K, so each is
+within a few 1e-6 K of the exact discrete solution), eta to 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _loop_case(n=64, nz=100, heat=(16, 16, 32), p1=100.0, n_outer=3):
+    """Reduced self-consistent loop with the absorbing-workload losses
+    (dT reaches ~7 K and eta drops from 0.140 to 0.120 over the loop)."""
+    return W.thermal_loop(n=n, nz=nz, heat=heat, p1=p1, n_outer=n_outer)
+
+
+def _gpu_loop(w, tol=1e-6):
+    import paper_2410_04994_gb300 as pkg
+    plan = pkg.Plan(w, thermal=True)
+    etas, changes = pkg.shg_thermal_loop(plan.handle, w.n_outer, 200000, tol)
+    q = torch.empty((w.hz, w.hy, w.hx), dtype=torch.float64, device="cuda")
+    dT = torch.empty((w.hz, w.hy, w.hx), dtype=torch.float32, device="cuda")
+    pkg.shg_get_heat(plan.handle, q, dT)
+    torch.cuda.synchronize()
+    return etas, changes, q.cpu().numpy(), dT.cpu().numpy()
+
+
+def test_deposit_and_loop_match_oracle():
+    from oracle import heat
+    w = _loop_case()
+    etas, changes, Q, dT = _gpu_loop(w)
+    hist = heat.thermal_loop(w, w.n_outer, tol=1e-6)
+    for k, h in enumerate(hist):
+        assert abs(etas[k] / h["eta"] - 1) < 1e-4, (k, etas[k], h["eta"])
+        assert abs(changes[k] - h["change"]) <= 1e-3 * max(h["change"], 1e-6) + 2e-5
+    Qo = hist[-1]["Q"].numpy()
+    assert np.linalg.norm(Q - Qo) <= 1e-4 * np.linalg.norm(Qo)
+    dTo = hist[-1]["dT"].numpy()
+    assert np.abs(dTo).max() > 1e-3
+    assert np.abs(dT - dTo).max() <= 1e-3 * np.abs(dTo).max() + 1e-5
+    # the loop changes eta: the temperature feedback is active
+    assert abs(etas[-1] / etas[0] - 1) > 1e-4
+
+
+def test_first_pass_deposit_conserves_absorbed_power():
+    """After one pass (dT = 0) the deposited heat equals the power lost by the
+    two waves, to the trapezoid rule's accuracy in z and the FP32 power
+    conservation of the fields (1e-4 of the input power)."""
+    w = _loop_case(n_outer=1).with_(nz=400)
+    import paper_2410_04994_gb300 as pkg
+    plan = pkg.Plan(w, thermal=True)
+    etas, _ = pkg.shg_thermal_loop(plan.handle, 1, 1000, 1e-6)
+    eta, p_f, p_sh = plan.efficiency()
+    q = torch.empty((w.hz, w.hy, w.hx), dtype=torch.float64, device="cuda")
+    pkg.shg_get_heat(plan.handle, q, None)
+    lost = w.p1 - p_f - p_sh
+    assert lost > 0.002 * w.p1
+    assert abs(float(q.sum()) - lost) < 1e-4 * w.p1
+
+
+@pytest.mark.slow
+def test_full_size_thermal_loop_properties():
+    """1024 x 1024, nz = 8000, 128 x 128 x 256 heat grid, 6 outer iterations:
+    finite results, energy balance of the last pass, and a converging loop."""
+    import paper_2410_04994_gb300 as pkg
+    w = W.thermal_loop()
+    plan = pkg.Plan(w, thermal=True)
+    etas, changes = pkg.shg_thermal_loop(plan.handle, w.n_outer, 200000, 1e-6)
+    eta, p_f, p_sh = plan.efficiency()
+    q = torch.empty((w.hz, w.hy, w.hx), dtype=torch.float64, device="cuda")
+    pkg.shg_get_heat(plan.handle, q, None)
+    assert all(math.isfinite(e) and 0 < e < 1 for e in etas)
+    lost = w.p1 - p_f - p_sh
+    assert abs(float(q.sum()) - lost) < 1e-4 * w.p1
+    assert changes[0] == 0.0 and changes[1] > 0
+    assert changes[-1] < 0.5 * changes[1]
