@@ -187,6 +187,29 @@ shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
 shg_status_t shg_pass_times(shg_plan_t *const *plans, int n, int nsteps, double *out,
                             int *inst_out, int max_groups, int *ngroups, shg_stream_t stream);
 
+/* Powers P_F, P_SH = (1/2) eps0 c n_j sum |A_j|^2 dx dy of fields the caller
+ * already holds, written to memory the caller already holds, with no device
+ * allocation.  This is a library convenience with no counterpart in the
+ * paper: it serves callers that may not call cudaMalloc (a host framework
+ * with a fixed device-memory budget, or a latency-critical loop where an
+ * allocation could wait on the device or fail).
+ *   fields_dev: n_inst instances, each [2][ny][nx] (A_F then A_SH), float2, or
+ *               double2 if fp64 != 0, contiguous, device.
+ *   powers_dev: n_inst x {P_F, P_SH} doubles (W), device.
+ *   lx, ly: window (dx = lx/nx, dy = ly/ny); n_f, n_sh: refractive indices.
+ * The partial sums live in one static device array of the library
+ * (1024 instances x 32 blocks x 2 doubles = 512 KiB), which every GPU that
+ * loads the library holds until the process exits; n_inst > 1024 is rejected
+ * with SHG_ERR_INVALID_ARG.  Each call overwrites every partial it reads, so
+ * nothing carries over between calls, but calls that overlap on the GPU
+ * (other streams, other threads) race on the array and must be serialised.
+ * The first call on a device looks up the array's device address (and loads
+ * the library's device code if that has not happened yet): make that first
+ * call before any stream capture.  Asynchronous on `stream`. */
+shg_status_t shg_field_powers_noalloc(const void *fields_dev, int nx, int ny, int n_inst,
+                                      int fp64, double lx, double ly, double n_f,
+                                      double n_sh, double *powers_dev, shg_stream_t stream);
+
 /* Static description of a status code. */
 const char *shg_status_string(shg_status_t status);
 

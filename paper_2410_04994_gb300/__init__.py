@@ -79,6 +79,7 @@ _SIGS = {
     "shg_thermal_loop": [_P, _I, _I, _D, _DP, _DP, _P],
     "shg_get_heat": [_P, _P, _P, _P],
     "shg_pass_times": [ctypes.POINTER(_P), _I, _I, _DP, _IP, _I, _IP, _P],
+    "shg_field_powers_noalloc": [_P, _I, _I, _I, _I, _D, _D, _D, _D, _P, _P],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
 
@@ -226,6 +227,17 @@ def shg_pass_times(plans: Sequence[int], nsteps: int = 4, stream=None, max_group
                                  _stream(stream)), "shg_pass_times")
     return [dict(nx=int(out[4 * g]), ny=int(out[4 * g + 1]), row_ms=out[4 * g + 2],
                  col_ms=out[4 * g + 3], instances=inst[g]) for g in range(ng.value)]
+
+
+def shg_field_powers_noalloc(fields, nx: int, ny: int, n_inst: int, lx: float, ly: float,
+                             n_f: float, n_sh: float, powers, stream=None) -> None:
+    """P_F, P_SH of caller-held fields into a caller-held float64 CUDA tensor
+    [n_inst, 2]; the library allocates nothing (see include/shg.h)."""
+    import torch
+    fp64 = 1 if fields.dtype in (torch.complex128, torch.float64) else 0
+    _check(_lib().shg_field_powers_noalloc(_ptr(fields), nx, ny, n_inst, fp64, float(lx),
+                                           float(ly), float(n_f), float(n_sh), _ptr(powers),
+                                           _stream(stream)), "shg_field_powers_noalloc")
 
 
 def shg_status_string(status: int) -> str:
