@@ -157,9 +157,10 @@ shg_status_t shg_batch_submit(shg_plan_t *const *plans, int n, double *eta_host_
                               shg_stream_t stream);
 
 /* Solve kappa lap dT = -q_dot (Eq. 7/16, Dirichlet dT = 0 on all faces) on
- * the heat grid by red-black SOR from the q_dot deposited by the last
- * THERMAL propagation, until the largest Jacobi correction is below tol (K)
- * or max_sweeps sweeps.  Installs dT as the plan's temperature map.
+ * the heat grid by red-black SOR (double precision, warm-started from the
+ * previous solution) from the q_dot deposited by the last THERMAL
+ * propagation, until the largest Jacobi correction is below tol (K) or
+ * max_sweeps sweeps.  Installs dT as the plan's temperature map.
  * Returns the final correction and sweep count.  Synchronises `stream`. */
 shg_status_t shg_heat_solve(shg_plan_t *plan, int max_sweeps, double tol, double *resid,
                             int *sweeps, shg_stream_t stream);
@@ -172,8 +173,8 @@ shg_status_t shg_thermal_loop(shg_plan_t *plan, int n_outer, int max_sweeps, dou
                               double *eta_out, double *change_out, shg_stream_t stream);
 
 /* Heat-grid state for inspection: the deposited heat per node q_dev (W, the
- * sum of q_dot dV, double [hz][hy][hx]) and the last solved dT (float).
- * Either pointer may be NULL. */
+ * sum of q_dot dV, double [hz][hy][hx]) and the last solved dT (solved in
+ * double, returned rounded to float).  Either pointer may be NULL. */
 shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
                           shg_stream_t stream);
 

@@ -415,15 +415,16 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     if (flags & SHG_FLAG_THERMAL) {
         const size_t nh = size_t(grid->hx) * grid->hy * grid->hz;
         ALLOC(p->Q, nh * sizeof(double));
-        ALLOC(p->theat, nh * sizeof(float));
-        ALLOC(p->theat_prev, nh * sizeof(float));
+        ALLOC(p->theat, nh * sizeof(double));
+        ALLOC(p->theat_prev, nh * sizeof(double));
+        ALLOC(p->theat_f, nh * sizeof(float));
         ALLOC(p->hix, grid->nx * sizeof(int));
         ALLOC(p->hiy, grid->ny * sizeof(int));
         ALLOC(p->hlz, (grid->nz + 1) * sizeof(int));
         ALLOC(p->hred, 2 * 1024 * sizeof(double));
         if ((e = cudaMemset(p->Q, 0, nh * sizeof(double))) != cudaSuccess) return fail(e, "memset");
-        if ((e = cudaMemset(p->theat, 0, nh * sizeof(float))) != cudaSuccess) return fail(e, "memset");
-        if ((e = cudaMemset(p->theat_prev, 0, nh * sizeof(float))) != cudaSuccess)
+        if ((e = cudaMemset(p->theat, 0, nh * sizeof(double))) != cudaSuccess) return fail(e, "memset");
+        if ((e = cudaMemset(p->theat_prev, 0, nh * sizeof(double))) != cudaSuccess)
             return fail(e, "memset");
     }
 #undef ALLOC
@@ -451,7 +452,8 @@ static void plan_free(shg_plan* p) {
     if (p->cap) cudaStreamDestroy(p->cap);
     void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
                     p->tw,    p->ttab,   p->tmap, p->desc, p->idesc, p->red, p->pw,
-                    p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->hred};
+                    p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->theat_f,
+                    p->hred};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;

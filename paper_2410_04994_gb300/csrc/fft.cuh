@@ -23,25 +23,26 @@ namespace shg {
 
 // Sizes handled per thread and the radix sequence of each transform length.
 template <class R, int N> struct FftCfg;
-#define SHG_FFT_CFG(RT, NN, EE, R0_, R1_, R2_)                                   \
-    template <> struct FftCfg<RT, NN> {                                          \
-        static constexpr int E = EE, T = NN / EE, R0 = R0_, R1 = R1_, R2 = R2_;  \
-        static constexpr int NST = (R1_ > 1 ? 1 : 0) + (R2_ > 1 ? 1 : 0) + 1;    \
+#define SHG_FFT_CFG(RT, NN, EE, R0_, R1_, R2_, R3_)                                    \
+    template <> struct FftCfg<RT, NN> {                                                \
+        static constexpr int E = EE, T = NN / EE, R0 = R0_, R1 = R1_, R2 = R2_, R3 = R3_; \
+        static constexpr int NST = 1 + (R1_ > 1) + (R2_ > 1) + (R3_ > 1);              \
+        static_assert(R0_ * R1_ * R2_ * R3_ == NN, "radices must multiply to N");      \
     };
-SHG_FFT_CFG(float, 8, 8, 8, 1, 1)
-SHG_FFT_CFG(float, 16, 16, 16, 1, 1)
-SHG_FFT_CFG(float, 32, 16, 16, 2, 1)
-SHG_FFT_CFG(float, 64, 16, 16, 4, 1)
-SHG_FFT_CFG(float, 128, 16, 16, 8, 1)
-SHG_FFT_CFG(float, 256, 16, 16, 16, 1)
-SHG_FFT_CFG(float, 512, 16, 16, 16, 2)
-SHG_FFT_CFG(float, 1024, 16, 16, 16, 4)
-SHG_FFT_CFG(double, 8, 8, 8, 1, 1)
-SHG_FFT_CFG(double, 16, 8, 8, 2, 1)
-SHG_FFT_CFG(double, 32, 8, 8, 4, 1)
-SHG_FFT_CFG(double, 64, 8, 8, 8, 1)
-SHG_FFT_CFG(double, 128, 8, 8, 8, 2)
-SHG_FFT_CFG(double, 256, 8, 8, 8, 4)
+SHG_FFT_CFG(float, 8, 8, 8, 1, 1, 1)
+SHG_FFT_CFG(float, 16, 16, 16, 1, 1, 1)
+SHG_FFT_CFG(float, 32, 16, 16, 2, 1, 1)
+SHG_FFT_CFG(float, 64, 16, 16, 4, 1, 1)
+SHG_FFT_CFG(float, 128, 16, 16, 8, 1, 1)
+SHG_FFT_CFG(float, 256, 16, 16, 16, 1, 1)
+SHG_FFT_CFG(float, 512, 8, 8, 8, 8, 1)
+SHG_FFT_CFG(float, 1024, 8, 8, 8, 8, 2)
+SHG_FFT_CFG(double, 8, 8, 8, 1, 1, 1)
+SHG_FFT_CFG(double, 16, 8, 8, 2, 1, 1)
+SHG_FFT_CFG(double, 32, 8, 8, 4, 1, 1)
+SHG_FFT_CFG(double, 64, 8, 8, 8, 1, 1)
+SHG_FFT_CFG(double, 128, 8, 8, 8, 2, 1)
+SHG_FFT_CFG(double, 256, 8, 8, 8, 4, 1)
 #undef SHG_FFT_CFG
 
 // Shared-memory padding: one spare element per bank row so that the strided
@@ -165,6 +166,9 @@ SHG_D void stage(C (&v)[E], C* sm, int t, const pt<decltype(C::x)>* __restrict__
             for (int r = 1; r < R; ++r) {
                 const auto w = __ldg(&tw[jm * r * (1024 / (NS * R))]);
                 u[r] = DIR < 0 ? pmul(u[r], w) : pmulc(u[r], w);
+                // bound the number of (hi, lo) twiddles the compiler keeps in
+                // flight: without this it hoists them all and spills
+                if ((r & 3) == 3) asm volatile("" ::: "memory");
             }
         }
         dft_reg<R, DIR>(u);
@@ -192,8 +196,8 @@ template <class RT, int N, int DIR, class C>
 SHG_D void fft1(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
     using F = FftCfg<RT, N>;
     constexpr int E = F::E, T = F::T;
-    constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2;
-    constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2);
+    constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2, R3 = F::R3;
+    constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2), L2 = (F::NST == 3);
     stage<N, E, T, R0, 1, L0, DIR>(a, sa, t, tw);
     if constexpr (F::NST >= 2) {
         __syncthreads();
@@ -205,7 +209,13 @@ SHG_D void fft1(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict
         __syncthreads();
         reload<E, T>(a, sa, t);
         __syncthreads();
-        stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, true, DIR>(a, sa, t, tw);
+        stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, L2, DIR>(a, sa, t, tw);
+    }
+    if constexpr (F::NST >= 4) {
+        __syncthreads();
+        reload<E, T>(a, sa, t);
+        __syncthreads();
+        stage<N, E, T, (R3 > 1 ? R3 : 2), R0 * R1 * R2, true, DIR>(a, sa, t, tw);
     }
 }
 

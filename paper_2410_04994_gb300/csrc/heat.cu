@@ -2,6 +2,10 @@
 // faces, Eq. 9) by red-black successive over-relaxation, and the
 // self-consistent loop of Fig. 2.
 //
+// The iteration runs in double precision: in FP32 the Jacobi correction of a
+// solution of a few kelvin bottoms out near 1e-6 K (rounding of the stencil
+// sums), which would make a 1e-6 K stopping test unreachable.
+//
 // Unknown: dT = T - T_oven on the node grid [hz][hy][hx] spanning the crystal
 // [-wx/2, wx/2] x [-wy/2, wy/2] x [0, L], zero on the faces.  Source: the heat
 // deposited by the last THERMAL propagation, q_dot = Q / (dx dy dz) at each
@@ -19,10 +23,10 @@ namespace shg {
 
 struct HeatGeom {
     int hx, hy, hz;
-    float ax, ay, az;  // 1/dx^2, 1/dy^2, 1/dz^2
-    float invD;        // 1 / (2 (ax + ay + az))
-    float qs;          // 1 / (kappa dx dy dz): Q -> q_dot / kappa
-    float omega;
+    double ax, ay, az;  // 1/dx^2, 1/dy^2, 1/dz^2
+    double invD;        // 1 / (2 (ax + ay + az))
+    double qs;          // 1 / (kappa dx dy dz): Q -> q_dot / kappa
+    double omega;
 };
 
 static HeatGeom heat_geom(const shg_plan* p) {
@@ -32,86 +36,94 @@ static HeatGeom heat_geom(const shg_plan* p) {
     g.hz = p->g.hz;
     const double dx = p->c.wx / (g.hx - 1), dy = p->c.wy / (g.hy - 1), dz = p->c.L / (g.hz - 1);
     const double ax = 1 / (dx * dx), ay = 1 / (dy * dy), az = 1 / (dz * dz);
-    g.ax = float(ax);
-    g.ay = float(ay);
-    g.az = float(az);
-    g.invD = float(1.0 / (2.0 * (ax + ay + az)));
-    g.qs = float(1.0 / (p->c.kappa_th * dx * dy * dz));
+    g.ax = ax;
+    g.ay = ay;
+    g.az = az;
+    g.invD = 1.0 / (2.0 * (ax + ay + az));
+    g.qs = 1.0 / (p->c.kappa_th * dx * dy * dz);
     const double rho = (ax * std::cos(kPi / (g.hx - 1)) + ay * std::cos(kPi / (g.hy - 1)) +
                         az * std::cos(kPi / (g.hz - 1))) / (ax + ay + az);
-    g.omega = float(2.0 / (1.0 + std::sqrt(1.0 - rho * rho)));
+    g.omega = 2.0 / (1.0 + std::sqrt(1.0 - rho * rho));
     return g;
 }
 
-__device__ __forceinline__ float jacobi_target(const float* T, const double* Q, const HeatGeom& g,
-                                               size_t c) {
+__device__ __forceinline__ double jacobi_target(const double* T, const double* Q,
+                                                const HeatGeom& g, size_t c) {
     const size_t plane = size_t(g.hx) * g.hy;
-    const float s = g.ax * (T[c - 1] + T[c + 1]) + g.ay * (T[c - g.hx] + T[c + g.hx]) +
-                    g.az * (T[c - plane] + T[c + plane]) + float(Q[c]) * g.qs;
+    const double s = g.ax * (T[c - 1] + T[c + 1]) + g.ay * (T[c - g.hx] + T[c + g.hx]) +
+                     g.az * (T[c - plane] + T[c + plane]) + Q[c] * g.qs;
     return s * g.invD;
 }
 
 // One colour of a red-black sweep: nodes with (i + j + l) % 2 == colour.
 // grid = (ceil((hx - 2 + 1) / 2 / 128), hy - 2, hz - 2), block = 128.
-__global__ void k_sor_colour(float* __restrict__ T, const double* __restrict__ Q, HeatGeom g,
+__global__ void k_sor_colour(double* __restrict__ T, const double* __restrict__ Q, HeatGeom g,
                              int colour) {
     const int j = blockIdx.y + 1, l = blockIdx.z + 1;
     const int i0 = 1 + ((colour + 1 + j + l) & 1);  // first interior i of this colour
     const int i = i0 + 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     if (i > g.hx - 2) return;
     const size_t c = (size_t(l) * g.hy + j) * g.hx + i;
-    const float t = T[c];
+    const double t = T[c];
     T[c] = t + g.omega * (jacobi_target(T, Q, g, c) - t);
 }
 
-// Largest |Jacobi correction| over the interior (non-negative floats compare
+// Largest |Jacobi correction| over the interior (non-negative doubles compare
 // as their bit patterns).  grid = (ceil((hx-2)/128), hy - 2, hz - 2).
-__global__ void k_max_correction(const float* __restrict__ T, const double* __restrict__ Q,
-                                 HeatGeom g, unsigned* __restrict__ out) {
+__global__ void k_max_correction(const double* __restrict__ T, const double* __restrict__ Q,
+                                 HeatGeom g, unsigned long long* __restrict__ out) {
     const int j = blockIdx.y + 1, l = blockIdx.z + 1;
     const int i = 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    float v = 0.f;
+    double v = 0.0;
     if (i <= g.hx - 2) {
         const size_t c = (size_t(l) * g.hy + j) * g.hx + i;
-        v = fabsf(jacobi_target(T, Q, g, c) - T[c]);
+        v = fabs(jacobi_target(T, Q, g, c) - T[c]);
     }
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-__global__ void k_max_abs_diff(const float* __restrict__ a, const float* __restrict__ b, size_t n,
-                               unsigned* __restrict__ out) {
-    float v = 0.f;
+__global__ void k_max_abs_diff(const double* __restrict__ a, const double* __restrict__ b,
+                               size_t n, unsigned long long* __restrict__ out) {
+    double v = 0.0;
     for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n;
          k += size_t(gridDim.x) * blockDim.x)
-        v = fmaxf(v, fabsf(a[k] - b[k]));
-    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(v));
+        v = fmax(v, fabs(a[k] - b[k]));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0)
+        atomicMax(out, static_cast<unsigned long long>(__double_as_longlong(v)));
 }
 
-static shg_status_t max_correction(shg_plan* p, const HeatGeom& g, cudaStream_t st, float* out) {
-    unsigned* d = reinterpret_cast<unsigned*>(p->hred);
-    SHG_CK(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, size_t n) {
+    for (size_t k = blockIdx.x * size_t(blockDim.x) + threadIdx.x; k < n;
+         k += size_t(gridDim.x) * blockDim.x)
+        b[k] = float(a[k]);
+}
+
+static shg_status_t max_correction(shg_plan* p, const HeatGeom& g, cudaStream_t st, double* out) {
+    auto* d = reinterpret_cast<unsigned long long*>(p->hred);
+    SHG_CK(cudaMemsetAsync(d, 0, sizeof(*d), st));
     dim3 grid((g.hx - 2 + 127) / 128, g.hy - 2, g.hz - 2);
     k_max_correction<<<grid, 128, 0, st>>>(p->theat, p->Q, g, d);
     SHG_CK(cudaGetLastError());
-    unsigned h = 0;
-    SHG_CK(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    unsigned long long h = 0;
+    SHG_CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
     SHG_CK(cudaStreamSynchronize(st));
-    memcpy(out, &h, sizeof(float));
+    memcpy(out, &h, sizeof(double));
     return SHG_OK;
 }
 
 static shg_status_t sor(shg_plan* p, int max_sweeps, double tol, double* resid, int* sweeps,
                         cudaStream_t st) {
     const HeatGeom g = heat_geom(p);
-    float corr = 0;
+    double corr = 0;
     shg_status_t r = max_correction(p, g, st, &corr);
     if (r != SHG_OK) return r;
     int n = 0;
     const int half = (g.hx - 2 + 1) / 2;
     dim3 grid((half + 127) / 128, g.hy - 2, g.hz - 2);
-    while (double(corr) >= tol && n < max_sweeps) {
+    while (corr >= tol && n < max_sweeps) {
         k_sor_colour<<<grid, 128, 0, st>>>(p->theat, p->Q, g, 0);
         k_sor_colour<<<grid, 128, 0, st>>>(p->theat, p->Q, g, 1);
         SHG_CK(cudaGetLastError());
@@ -125,7 +137,10 @@ static shg_status_t sor(shg_plan* p, int max_sweeps, double tol, double* resid, 
 }
 
 static shg_status_t install_map(shg_plan* p, cudaStream_t st) {
-    return shg_set_temperature(p, p->theat, p->g.hx, p->g.hy, p->g.hz, p->c.wx, p->c.wy,
+    const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
+    k_to_float<<<256, 256, 0, st>>>(p->theat, p->theat_f, nh);
+    SHG_CK(cudaGetLastError());
+    return shg_set_temperature(p, p->theat_f, p->g.hx, p->g.hy, p->g.hz, p->c.wx, p->c.wy,
                                reinterpret_cast<shg_stream_t>(st));
 }
 
@@ -152,8 +167,10 @@ extern "C" shg_status_t shg_get_heat(shg_plan_t* p, double* q_dev, float* dT_dev
     if (p->has_result && p->last_stream != st) SHG_CK(cudaStreamSynchronize(p->last_stream));
     const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
     if (q_dev) SHG_CK(cudaMemcpyAsync(q_dev, p->Q, nh * sizeof(double), cudaMemcpyDeviceToDevice, st));
-    if (dT_dev)
-        SHG_CK(cudaMemcpyAsync(dT_dev, p->theat, nh * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    if (dT_dev) {
+        k_to_float<<<256, 256, 0, st>>>(p->theat, dT_dev, nh);
+        SHG_CK(cudaGetLastError());
+    }
     return SHG_OK;
 }
 
@@ -166,22 +183,22 @@ extern "C" shg_status_t shg_thermal_loop(shg_plan_t* p, int n_outer, int max_swe
     if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
     const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
     // q_dot = 0 before the first pass: dT = 0
-    SHG_CK(cudaMemsetAsync(p->theat, 0, nh * sizeof(float), st));
+    SHG_CK(cudaMemsetAsync(p->theat, 0, nh * sizeof(double), st));
     SHG_CK(cudaMemsetAsync(p->Q, 0, nh * sizeof(double), st));
     for (int it = 0; it < n_outer; ++it) {
-        SHG_CK(cudaMemcpyAsync(p->theat_prev, p->theat, nh * sizeof(float),
+        SHG_CK(cudaMemcpyAsync(p->theat_prev, p->theat, nh * sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
         shg_status_t r = sor(p, max_sweeps, tol, nullptr, nullptr, st);
         if (r != SHG_OK) return r;
-        unsigned* d = reinterpret_cast<unsigned*>(p->hred);
-        SHG_CK(cudaMemsetAsync(d, 0, sizeof(unsigned), st));
+        auto* d = reinterpret_cast<unsigned long long*>(p->hred);
+        SHG_CK(cudaMemsetAsync(d, 0, sizeof(*d), st));
         k_max_abs_diff<<<256, 256, 0, st>>>(p->theat, p->theat_prev, nh, d);
         SHG_CK(cudaGetLastError());
-        unsigned h = 0;
-        SHG_CK(cudaMemcpyAsync(&h, d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        unsigned long long h = 0;
+        SHG_CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
         if ((r = install_map(p, st)) != SHG_OK) return r;  // synchronises st
-        float change;
-        memcpy(&change, &h, sizeof(float));
+        double change;
+        memcpy(&change, &h, sizeof(double));
         if ((r = shg_propagate(p, stream)) != SHG_OK) return r;
         double eta = 0;
         if ((r = shg_efficiency(p, &eta, nullptr, nullptr)) != SHG_OK) return r;

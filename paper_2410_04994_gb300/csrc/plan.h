@@ -68,8 +68,9 @@ struct shg_plan {
     int* hix = nullptr;
     int* hiy = nullptr;
     int* hlz = nullptr;
-    float* theat = nullptr;   // [hz][hy][hx] last solved dT
-    float* theat_prev = nullptr;
+    double* theat = nullptr;  // [hz][hy][hx] last solved dT
+    double* theat_prev = nullptr;
+    float* theat_f = nullptr; // dT rounded to float, as installed as the map
     double* hred = nullptr;   // reduction scratch of the heat solve
 
     // forward graph
