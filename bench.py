@@ -245,6 +245,27 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+# -------------------------------------------------------------- multi-rank ----
+
+def rank_instances(rank: int, nz: int = 2000, groups=W.SWEEP_GROUPS):
+    """Instances of one rank: an independent seeded sweep (seed 1 + rank), so
+    per-rank work is fixed as ranks are added (weak scaling) and no data moves
+    between ranks."""
+    return W.sweep_instances(seed=1 + rank, nz=nz, groups=groups)
+
+
+def aggregate_rate(point_steps_local: float, seconds_local: float, world: int, device=None):
+    """Whole-job throughput: point-steps summed over ranks / the slowest
+    rank's time (the only collective of the benchmark; not on the data path)."""
+    if world == 1:
+        return point_steps_local / seconds_local, seconds_local
+    t = torch.tensor([seconds_local], dtype=torch.float64, device=device)
+    n = torch.tensor([point_steps_local], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
+    return float(n) / float(t), float(t)
+
+
 # --------------------------------------------------------------- our path ----
 
 def run_ours(args, rank, world):
@@ -259,7 +280,7 @@ def run_ours(args, rank, world):
     dev = torch.cuda.current_device()
     groups_arg = tuple((int(a), int(b)) for a, b in
                        (g.split(":") for g in args.groups.split(","))) if args.groups else W.SWEEP_GROUPS
-    insts = W.sweep_instances(seed=1 + rank, nz=args.nz, groups=groups_arg)
+    insts = rank_instances(rank, nz=args.nz, groups=groups_arg)
     npoint_steps = sum(w.nx * w.ny * w.nz for w in insts)
     plans = [pkg.Plan(w) for w in insts]
     maps = [torch.as_tensor(w.dT).to("cuda") for w in insts]
@@ -298,12 +319,7 @@ def run_ours(args, rank, world):
         torch.distributed.barrier()
     clk = clocks.stop()
     ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(ms) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], device="cuda", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t)
-    value = npoint_steps * world * args.steps / t_total
+    value, t_total = aggregate_rate(npoint_steps * args.steps, sum(ms) / 1e3, world, "cuda")
     if not all(math.isfinite(e) for e in etas):
         raise RuntimeError("non-finite efficiency")
 
@@ -322,7 +338,7 @@ def run_ours(args, rank, world):
             p.set_temperature(dm, w.t_lx, w.t_ly)
         step()
         e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = npoint_steps * world / (statistics.median(e2e_ms) / 1e3)
+    e2e_value, _ = aggregate_rate(npoint_steps, statistics.median(e2e_ms) / 1e3, world, "cuda")
 
     result = None
     if rank == 0:
