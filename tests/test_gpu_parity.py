@@ -59,11 +59,9 @@ def test_rectangular_grids_fp32(nx, ny):
 
 @pytest.mark.parametrize("n", [8, 16, 64, 256])
 def test_fp64_transform_lengths(n):
-    """FP64 fields with a temperature map.  The map and its cumulative integral
-    are stored and sampled in FP32 in every plan, so phi and psi carry ~1e-7
-    relative error: the bar is 1e-6 here (1e-9 for FP64 without a map)."""
+    """FP64 fields with a temperature map (stored and sampled in double)."""
     w = W.depleted_absorbing(n=n, nz=6, tgrid=(5, 5, 5), p1=300.0).with_(precision="f64")
-    _compare(w, 1e-6, 1e-6)
+    _compare(w, 1e-9, 1e-9)
 
 
 @pytest.mark.parametrize("n", [8, 64, 256])
