@@ -65,13 +65,14 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     C* lamF = d.field + size_t(y) * NX;
     C* lamS = d.field + (size_t(ny) + y) * NX;
     const size_t plane = size_t(ny) * NX;
+    const RowCell<R> rc = thermal ? row_cell(d, y) : RowCell<R>{0, R(0)};
 #pragma unroll 1
     for (int m = 0; m < E; ++m) {
         const int xi = t + T * m;
         C lF = sF[pidx<R>(xi)], lS = sS[pidx<R>(xi)];
         const C yF = YF[xi], yS = YS[xi];
         TempSampler<R> ts;
-        if (thermal) make_sampler(d, mv, xi, y, ts);
+        if (thermal) make_sampler(d, mv, xi, rc, ts);
         Coef<R> c[5];
         StageBar<R> b[5];
 #pragma unroll

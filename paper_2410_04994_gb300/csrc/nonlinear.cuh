@@ -67,13 +67,12 @@ template <class R> struct TempSampler {
 };
 
 template <class R> SHG_D void sincos_r(R x, R* s, R* c);
-// |g C| is a small phase in practice; the hardware approximation (absolute
-// error ~4e-7 on [-pi, pi]) is used there and the full-range routine outside.
+// The argument is reduced to [-pi, pi] first; there the hardware
+// approximation has an absolute error of ~4e-7 (|g C| is a small phase in
+// practice, so the reduction is exact for it).
 template <> SHG_D void sincos_r<float>(float x, float* s, float* c) {
-    if (fabsf(x) < 3.0f)
-        __sincosf(x, s, c);
-    else
-        sincosf(x, s, c);
+    const float k = rintf(x * 0.159154943091895336f);  // x / (2 pi)
+    __sincosf(fmaf(-k, 6.28318530717958648f, x), s, c);
 }
 template <> SHG_D void sincos_r<double>(double x, double* s, double* c) { sincos(x, s, c); }
 

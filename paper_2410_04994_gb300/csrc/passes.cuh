@@ -44,14 +44,26 @@ template <class R> struct MapView {
     int stride, plane, l0, iy0, ix0;
 };
 
+// Map row cell of field row y (the same for every point of the row).
+template <class R> struct RowCell {
+    int iy;
+    R fy;
+};
+template <class R> SHG_D RowCell<R> row_cell(const InstDesc<R>& d, int y) {
+    RowCell<R> rc;
+    lin_cell<R>((d.y0 + d.dy * R(y) - d.ty0) * d.tdy_inv, d.ty, rc.iy, rc.fy);
+    return rc;
+}
+
 // Temperature-map sampler for field point (xi, y).
 template <class R>
-SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, int y,
+SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, const RowCell<R>& rc,
                         TempSampler<R>& ts) {
-    int ix, iy;
-    R fx, fy;
+    int ix;
+    R fx;
     lin_cell<R>((d.x0 + d.dx * R(xi) - d.tx0) * d.tdx_inv, d.tx, ix, fx);
-    lin_cell<R>((d.y0 + d.dy * R(y) - d.ty0) * d.tdy_inv, d.ty, iy, fy);
+    const int iy = rc.iy;
+    const R fy = rc.fy;
     ts.base = mv.base + (iy - mv.iy0) * mv.stride + (ix - mv.ix0);
     ts.tx = mv.stride;
     ts.plane = mv.plane;
@@ -117,10 +129,11 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     const int l_dep = dep ? d.hlz[s] : -1;
     const int j_dep = (dep && active) ? d.hiy[y] : -1;
     const R w_dep = dep ? d.dxdy * d.dz * ((s == 0 || s == nz) ? R(0.5) : R(1)) : R(0);
+    const RowCell<R> rc = thermal ? row_cell(d, y) : RowCell<R>{0, R(0)};
     // One point: N_b(s-1) [z_s - dz/2 -> z_s], deposit at z_s, N_a(s).
     auto point = [&](int xi, C& aF, C& aS) {
         TempSampler<R> ts;
-        if (thermal) make_sampler(d, mv, xi, y, ts);
+        if (thermal) make_sampler(d, mv, xi, rc, ts);
         const Coef<R> cz = coef_at(d, zsh[2], thermal, ts);  // z_s, shared by both halves
         if (s > 0) {
             const Coef<R> c0 = coef_at(d, zsh[0], thermal, ts);
