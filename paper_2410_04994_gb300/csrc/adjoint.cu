@@ -302,8 +302,12 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
             SHG_CK(cudaMemcpyAsync(static_cast<char*>(a->seg) + size_t(s - sb) * a->sbytes,
                                    a->work, a->sbytes, cudaMemcpyDeviceToDevice, st));
             if (s + 1 < se) {
-                SHG_CK(launch_row(p->fp64, nx, a->descW, 1, ny, nz, s, p->tw, 0, st));
-                if (s < nz) SHG_CK(launch_col(p->fp64, ny, a->descW, 1, nx, p->tw, st));
+                // the same FFT shapes as the forward sweep, to replay its states
+                SHG_CK(launch_row(p->fp64, nx, a->descW, 1, ny, nz, s, p->tw, 0, st,
+                                  fft_variant(p->fp64, nx, 0)));
+                if (s < nz)
+                    SHG_CK(launch_col(p->fp64, ny, a->descW, 1, nx, p->tw, st,
+                                      fft_variant(p->fp64, ny, 1)));
             }
         }
         for (int s = se - 1; s >= sb; --s) {

@@ -7,6 +7,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <tuple>
 #include <vector>
 
 #include "plan.h"
@@ -262,6 +263,64 @@ static shg_status_t quiesce(shg_plan* p) {
 
 // ----------------------------------------------------------- forward ----
 
+// ---------------------------------------------------------- autotuner ----
+
+static std::mutex g_tune_mu;
+static std::map<std::tuple<bool, int, int>, int> g_tuned;
+
+static int forced_variant() {
+    const char* f = getenv("SHG_FFT_VARIANT");
+    return (f && (f[0] == '0' || f[0] == '1') && f[1] == 0) ? f[0] - '0' : -1;
+}
+
+int fft_variant(bool fp64, int n, int pass) {
+    if (!has_fft_variant(fp64, n)) return 0;
+    const int f = forced_variant();
+    if (f >= 0) return f;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(std::make_tuple(fp64, n, pass));
+    return it == g_tuned.end() ? 0 : it->second;
+}
+
+// Time both FFT shapes of each pass of this group on its own data (one
+// warm-up and three timed launches each, CUDA events on `st`) and keep the
+// faster one for the rest of the process.  The group's fields are modified;
+// every propagation re-initialises them first.
+shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
+                        const void* tw, int hx, cudaStream_t st) {
+    if (forced_variant() >= 0) return SHG_OK;
+    for (int pass = 0; pass < 2; ++pass) {
+        const int n = pass == 0 ? nx : ny;
+        if (!has_fft_variant(fp64, n)) continue;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            if (g_tuned.count(std::make_tuple(fp64, n, pass))) continue;
+        }
+        float best[2] = {0, 0};
+        cudaEvent_t e0, e1;
+        SHG_CK(cudaEventCreate(&e0));
+        SHG_CK(cudaEventCreate(&e1));
+        const int s = nz > 1 ? 1 : 0;
+        for (int v = 0; v < 2; ++v) {
+            for (int rep = 0; rep < 4; ++rep) {
+                if (rep == 1) SHG_CK(cudaEventRecord(e0, st));
+                const cudaError_t e = pass == 0
+                    ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v)
+                    : launch_col(fp64, ny, descs, ninst, nx, tw, st, v);
+                if (e != cudaSuccess) return cuda_fail(e, "tune_group");
+            }
+            SHG_CK(cudaEventRecord(e1, st));
+            SHG_CK(cudaEventSynchronize(e1));
+            SHG_CK(cudaEventElapsedTime(&best[v], e0, e1));
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[std::make_tuple(fp64, n, pass)] = best[1] < best[0] ? 1 : 0;
+    }
+    return SHG_OK;
+}
+
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
                              const InitDesc* idescs, int ninst, const void* tw,
                              const std::vector<shg_plan*>& plans, cudaStream_t st) {
@@ -278,15 +337,16 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     int hx = 0;
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+    const int vr = fft_variant(fp64, nx, 0), vc = fft_variant(fp64, ny, 1);
     for (int s = 0; s <= nz; ++s) {
         for (shg_plan* p : plans) {
             shg_status_t r = adjoint_checkpoint(p, s, st);
             if (r != SHG_OK) return r;
         }
-        e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st);
+        e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, vr);
         if (e != cudaSuccess) return cuda_fail(e, "row pass");
         if (s < nz) {
-            e = launch_col(fp64, ny, descs, ninst, nx, tw, st);
+            e = launch_col(fp64, ny, descs, ninst, nx, tw, st, vc);
             if (e != cudaSuccess) return cuda_fail(e, "column pass");
         }
     }
@@ -324,6 +384,11 @@ static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
         return enqueue_forward(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, p->idesc, 1, p->tw,
                                one, s);
     };
+    {
+        int hx = ((p->flags & SHG_FLAG_THERMAL) && p->Q) ? p->g.hx : 0;
+        shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st);
+        if (r != SHG_OK) return r;
+    }
     if (!use_graphs()) return body(st);
     if (!p->gvalid) {
         if (p->gexec) {
@@ -380,7 +445,9 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
             !(crystal->wy > 0) || !(crystal->kappa_th > 0))
             return SHG_ERR_INVALID_ARG;
         // the row pass bins the heat deposit per CTA in shared memory
-        if (row_pass_smem(fp64, grid->nx, grid->hx) > 223 * 1024) return SHG_ERR_UNSUPPORTED_GRID;
+        for (int v = 0; v < 2; ++v)
+            if (row_pass_smem(fp64, grid->nx, grid->hx, v) > 223 * 1024)
+                return SHG_ERR_UNSUPPORTED_GRID;
     }
     shg_status_t st = ensure_attributes();
     if (st != SHG_OK) return st;
@@ -763,6 +830,14 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
     for (auto p : key)
         if (p->has_result) cudaStreamSynchronize(p->last_stream);
     if ((r = refresh_entry(ent, st)) != SHG_OK) return r;
+    for (auto& g : ent->groups) {
+        int hx = 0;
+        for (shg_plan* p : g.plans)
+            if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+        if ((r = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs, int(g.plans.size()),
+                            g.plans[0]->tw, hx, st)) != SHG_OK)
+            return r;
+    }
     if (use_graphs()) {
         if (!ent->valid) {
             if (ent->gexec) {
@@ -832,12 +907,22 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             int hx = 0;
             for (shg_plan* p : g.plans)
                 if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+            if (s == 1) {
+                shg_status_t r2 = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs,
+                                             int(g.plans.size()), g.plans[0]->tw, hx, st);
+                if (r2 != SHG_OK) {
+                    free_entry(ent);
+                    return r2;
+                }
+                cudaEventRecord(E[0], st);
+            }
             e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
-                           g.plans[0]->tw, hx, st);
+                           g.plans[0]->tw, hx, st, fft_variant(g.fp64, g.nx, 0));
             cudaEventRecord(E[1], st);
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);
-                e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st);
+                e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st,
+                               fft_variant(g.fp64, g.ny, 1));
                 cudaEventRecord(E[3], st);
             }
         }

@@ -3,28 +3,32 @@
 
 namespace shg {
 
-cudaError_t row_f32(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
-size_t row_smem_f32(int, int);
-size_t row_smem_f64(int, int);
-cudaError_t col_f32(int, const void*, int, int, const void*, cudaStream_t);
+cudaError_t row_f32(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+cudaError_t row_f64(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+size_t row_smem_f32(int, int, int);
+size_t row_smem_f64(int, int, int);
+cudaError_t col_f32(int, int, const void*, int, int, const void*, cudaStream_t);
+cudaError_t col_f64(int, int, const void*, int, int, const void*, cudaStream_t);
+bool has_variant_f32(int);
 cudaError_t attr_f32();
-cudaError_t row_f64(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
-cudaError_t col_f64(int, const void*, int, int, const void*, cudaStream_t);
 cudaError_t attr_f64();
 
+bool has_fft_variant(bool fp64, int n) { return !fp64 && has_variant_f32(n); }
+
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
-                       const void* tw, int hx, cudaStream_t st) {
-    return fp64 ? row_f64(nx, descs, ninst, ny, nz, s, tw, hx, st)
-                : row_f32(nx, descs, ninst, ny, nz, s, tw, hx, st);
+                       const void* tw, int hx, cudaStream_t st, int variant) {
+    return fp64 ? row_f64(nx, variant, descs, ninst, ny, nz, s, tw, hx, st)
+                : row_f32(nx, variant, descs, ninst, ny, nz, s, tw, hx, st);
 }
 
-size_t row_pass_smem(bool fp64, int nx, int hx) {
-    return fp64 ? row_smem_f64(nx, hx) : row_smem_f32(nx, hx);
+size_t row_pass_smem(bool fp64, int nx, int hx, int variant) {
+    return fp64 ? row_smem_f64(nx, variant, hx) : row_smem_f32(nx, variant, hx);
 }
 
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
-                       cudaStream_t st) {
-    return fp64 ? col_f64(ny, descs, ninst, nx, tw, st) : col_f32(ny, descs, ninst, nx, tw, st);
+                       cudaStream_t st, int variant) {
+    return fp64 ? col_f64(ny, variant, descs, ninst, nx, tw, st)
+                : col_f32(ny, variant, descs, ninst, nx, tw, st);
 }
 
 cudaError_t setup_pass_attributes() {

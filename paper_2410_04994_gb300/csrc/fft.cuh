@@ -22,13 +22,17 @@
 namespace shg {
 
 // Sizes handled per thread and the radix sequence of each transform length.
-template <class R, int N> struct FftCfg;
-#define SHG_FFT_CFG(RT, NN, EE, R0_, R1_, R2_, R3_)                                    \
-    template <> struct FftCfg<RT, NN> {                                                \
+// Variant V = 0 is the default shape; V = 1 is an alternative with 8 elements
+// per thread (fewer registers, more resident CTAs) that the launcher's
+// autotuner may pick per size and pass.
+template <class R, int N, int V = 0> struct FftCfg;
+#define SHG_FFT_CFG_V(RT, NN, VV, EE, R0_, R1_, R2_, R3_)                              \
+    template <> struct FftCfg<RT, NN, VV> {                                            \
         static constexpr int E = EE, T = NN / EE, R0 = R0_, R1 = R1_, R2 = R2_, R3 = R3_; \
         static constexpr int NST = 1 + (R1_ > 1) + (R2_ > 1) + (R3_ > 1);              \
         static_assert(R0_ * R1_ * R2_ * R3_ == NN, "radices must multiply to N");      \
     };
+#define SHG_FFT_CFG(RT, NN, EE, R0_, R1_, R2_, R3_) SHG_FFT_CFG_V(RT, NN, 0, EE, R0_, R1_, R2_, R3_)
 SHG_FFT_CFG(float, 8, 8, 8, 1, 1, 1)
 SHG_FFT_CFG(float, 16, 16, 16, 1, 1, 1)
 SHG_FFT_CFG(float, 32, 16, 16, 2, 1, 1)
@@ -43,7 +47,11 @@ SHG_FFT_CFG(double, 32, 8, 8, 4, 1, 1)
 SHG_FFT_CFG(double, 64, 8, 8, 8, 1, 1)
 SHG_FFT_CFG(double, 128, 8, 8, 8, 2, 1)
 SHG_FFT_CFG(double, 256, 8, 8, 8, 4, 1)
+SHG_FFT_CFG_V(float, 64, 1, 8, 8, 8, 1, 1)
+SHG_FFT_CFG_V(float, 128, 1, 8, 8, 8, 2, 1)
+SHG_FFT_CFG_V(float, 256, 1, 8, 8, 8, 4, 1)
 #undef SHG_FFT_CFG
+#undef SHG_FFT_CFG_V
 
 // Shared-memory padding: one spare element per bank row so that the strided
 // Stockham stores spread over all banks (16 float2 or 8 double2 per 128 B).
@@ -192,9 +200,9 @@ template <int E, int T, class C> SHG_D void reload(C (&v)[E], const C* sm, int t
 // Forward (DIR = -1) or inverse (DIR = +1, unnormalised) transform of one
 // sequence held as E registers per thread.  Every thread of the block must
 // call this (it contains __syncthreads).
-template <class RT, int N, int DIR, class C>
-SHG_D void fft1(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
-    using F = FftCfg<RT, N>;
+template <class RT, int N, int V, int DIR, class C>
+SHG_D void fft1(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
+    using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
     constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2, R3 = F::R3;
     constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2), L2 = (F::NST == 3);
@@ -224,15 +232,15 @@ SHG_D void fft1(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict
 // the inverse is folded into the factor table.  No barrier is needed between
 // the two transforms: every thread has passed the barrier that follows the
 // forward transform's last reload before any inverse store happens.
-template <class RT, int N, class C>
-SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N>::E], C* sa, int t, const pt<RT>* __restrict__ tw,
+template <class RT, int N, int V = 0, class C>
+SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw,
                         const pt<RT>* __restrict__ p) {
-    using F = FftCfg<RT, N>;
+    using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
-    fft1<RT, N, -1>(a, sa, t, tw);
+    fft1<RT, N, V, -1>(a, sa, t, tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) a[m] = pmul(a[m], __ldg(&p[t + T * m]));
-    fft1<RT, N, +1>(a, sa, t, tw);
+    fft1<RT, N, V, +1>(a, sa, t, tw);
 }
 
 }  // namespace shg

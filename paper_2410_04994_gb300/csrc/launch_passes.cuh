@@ -19,29 +19,33 @@ template <class K> cudaError_t allow_max_dyn_smem(K kernel) {
     return e;
 }
 
-template <class R, int N> cudaError_t row_attr() { return allow_max_dyn_smem(k_row_pass<R, N>); }
+template <class R, int N, int V = 0> cudaError_t row_attr() {
+    return allow_max_dyn_smem(k_row_pass<R, N, V>);
+}
 
 // Dynamic shared memory of a row pass: transform buffers + deposit bins.
-template <class R, int N> size_t row_smem(int hx) {
-    return RowGeom<R, N>::smem + size_t(RowGeom<R, N>::ROWS) * hx * sizeof(float);
+template <class R, int N, int V = 0> size_t row_smem(int hx) {
+    return RowGeom<R, N, V>::smem + size_t(RowGeom<R, N, V>::ROWS) * hx * sizeof(float);
 }
-template <class R, int N> cudaError_t col_attr() { return allow_max_dyn_smem(k_col_pass<R, N>); }
+template <class R, int N, int V = 0> cudaError_t col_attr() {
+    return allow_max_dyn_smem(k_col_pass<R, N, V>);
+}
 
-template <class R, int N>
+template <class R, int N, int V = 0>
 cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, const void* tw,
                        int hx, cudaStream_t st) {
-    using G = RowGeom<R, N>;
+    using G = RowGeom<R, N, V>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    k_row_pass<R, N><<<grid, kPassThreads, row_smem<R, N>(hx), st>>>(
+    k_row_pass<R, N, V><<<grid, kPassThreads, row_smem<R, N, V>(hx), st>>>(
         static_cast<const InstDesc<R>*>(descs), ny, nz, s, static_cast<const pt<R>*>(tw));
     return cudaGetLastError();
 }
 
-template <class R, int N>
+template <class R, int N, int V = 0>
 cudaError_t col_launch(const void* descs, int ninst, int nx, const void* tw, cudaStream_t st) {
-    using G = ColGeom<R, N>;
+    using G = ColGeom<R, N, V>;
     dim3 grid((nx + G::TILE - 1) / G::TILE, ninst);
-    k_col_pass<R, N><<<grid, kPassThreads, G::smem, st>>>(static_cast<const InstDesc<R>*>(descs),
+    k_col_pass<R, N, V><<<grid, kPassThreads, G::smem, st>>>(static_cast<const InstDesc<R>*>(descs),
                                                           nx, static_cast<const pt<R>*>(tw));
     return cudaGetLastError();
 }

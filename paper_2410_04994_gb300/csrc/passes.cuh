@@ -21,16 +21,19 @@ namespace shg {
 
 constexpr int kPassThreads = 256;
 
-template <class R, int N> struct RowGeom {
-    using F = FftCfg<R, N>;
+// Resident CTAs per SM the launch is compiled for (register budget).
+template <int V> struct MinBlocks { static constexpr int value = V == 0 ? 2 : 3; };
+
+template <class R, int N, int V = 0> struct RowGeom {
+    using F = FftCfg<R, N, V>;
     static constexpr int T = F::T;
     static constexpr int ROWS = kPassThreads / T;
     static constexpr int S = padded_len<R>(N, T < Bank<R>::W ? T : 1);
     static constexpr size_t smem = size_t(2) * ROWS * S * sizeof(cx<R>);
 };
 
-template <class R, int N> struct ColGeom {
-    using F = FftCfg<R, N>;
+template <class R, int N, int V = 0> struct ColGeom {
+    using F = FftCfg<R, N, V>;
     static constexpr int T = F::T;
     static constexpr int TILE = kPassThreads / T;
     static constexpr int S = padded_len<R>(N, TILE < Bank<R>::W ? Bank<R>::W / TILE : 1);
@@ -82,13 +85,13 @@ SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, cons
 // the transforms then run field by field from the same buffers.  The heat
 // deposit at z_s (THERMAL plans) is binned per CTA in shared memory and added
 // to the heat grid with one double-precision atomic per touched node.
-template <class R, int NX>
-__global__ void __launch_bounds__(kPassThreads, 2)
+template <class R, int NX, int V = 0>
+__global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = RowGeom<R, NX>;
-    constexpr int E = FftCfg<R, NX>::E, T = G::T, ROWS = G::ROWS, S = G::S;
+    using G = RowGeom<R, NX, V>;
+    constexpr int E = FftCfg<R, NX, V>::E, T = G::T, ROWS = G::ROWS, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<R> dsh;
     __shared__ StageZ<R> zsh[5];
@@ -193,7 +196,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         if (s < nz) {
             __syncthreads();  // the transform's first stores reuse the staging buffer
-            fft_mul_ifft<R, NX>(v, sb, t, tw, d.px + f * NX);
+            fft_mul_ifft<R, NX, V>(v, sb, t, tw, d.px + f * NX);
         }
         if (active) {
 #pragma unroll
@@ -205,12 +208,12 @@ __global__ void __launch_bounds__(kPassThreads, 2)
 // Column pass C(s).  grid = (ceil(nx / TILE), instances); block = 256.
 // The TILE columns of both fields are staged into padded shared buffers with
 // cp.async, transformed field by field, and written back from registers.
-template <class R, int NY>
-__global__ void __launch_bounds__(kPassThreads, 2)
+template <class R, int NY, int V = 0>
+__global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     k_col_pass(const InstDesc<R>* __restrict__ descs, int nx, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = ColGeom<R, NY>;
-    constexpr int E = FftCfg<R, NY>::E, T = G::T, TILE = G::TILE, S = G::S;
+    using G = ColGeom<R, NY, V>;
+    constexpr int E = FftCfg<R, NY, V>::E, T = G::T, TILE = G::TILE, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
     C* field = descs[blockIdx.y].field;
@@ -236,7 +239,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         __syncthreads();  // all staged values read before the transform's stores
-        fft_mul_ifft<R, NY>(v, sb, t, tw, py + f * NY);
+        fft_mul_ifft<R, NY, V>(v, sb, t, tw, py + f * NY);
         if (active) {
             C* col = field + size_t(f) * NY * nx + x;
 #pragma unroll

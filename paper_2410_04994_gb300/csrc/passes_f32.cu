@@ -1,13 +1,24 @@
-// Single-precision instantiations of the row and column passes (n = 8..1024).
+// Single-precision instantiations of the row and column passes (n = 8..1024),
+// with the alternative FFT shape (variant 1) for n = 64, 128, 256.
 #include "launch_passes.cuh"
 #include "plan.h"
 
 namespace shg {
 
 #define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+#define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
 
-cudaError_t row_f32(int nx, const void* descs, int ninst, int ny, int nz, int s, const void* tw,
-                    int hx, cudaStream_t st) {
+bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
+
+cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
+                    const void* tw, int hx, cudaStream_t st) {
+    if (v == 1) {
+        switch (nx) {
+#define X(n) case n: return row_launch<float, n, 1>(descs, ninst, ny, nz, s, tw, hx, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     switch (nx) {
 #define X(n) case n: return row_launch<float, n>(descs, ninst, ny, nz, s, tw, hx, st);
         SHG_F32_SIZES(X)
@@ -16,8 +27,15 @@ cudaError_t row_f32(int nx, const void* descs, int ninst, int ny, int nz, int s,
     return cudaErrorInvalidValue;
 }
 
-cudaError_t col_f32(int ny, const void* descs, int ninst, int nx, const void* tw,
+cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const void* tw,
                     cudaStream_t st) {
+    if (v == 1) {
+        switch (ny) {
+#define X(n) case n: return col_launch<float, n, 1>(descs, ninst, nx, tw, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     switch (ny) {
 #define X(n) case n: return col_launch<float, n>(descs, ninst, nx, tw, st);
         SHG_F32_SIZES(X)
@@ -28,15 +46,27 @@ cudaError_t col_f32(int ny, const void* descs, int ninst, int nx, const void* tw
 
 cudaError_t attr_f32() {
     cudaError_t e = cudaSuccess;
-#define X(n)                                       \
+#define X(n)                                        \
     if (e == cudaSuccess) e = row_attr<float, n>(); \
     if (e == cudaSuccess) e = col_attr<float, n>();
     SHG_F32_SIZES(X)
 #undef X
+#define X(n)                                           \
+    if (e == cudaSuccess) e = row_attr<float, n, 1>(); \
+    if (e == cudaSuccess) e = col_attr<float, n, 1>();
+    SHG_F32_VARIANT_SIZES(X)
+#undef X
     return e;
 }
 
-size_t row_smem_f32(int nx, int hx) {
+size_t row_smem_f32(int nx, int v, int hx) {
+    if (v == 1) {
+        switch (nx) {
+#define X(n) case n: return row_smem<float, n, 1>(hx);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     switch (nx) {
 #define X(n) case n: return row_smem<float, n>(hx);
         SHG_F32_SIZES(X)

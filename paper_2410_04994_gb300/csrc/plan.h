@@ -97,11 +97,19 @@ void fill_desc_f64(const shg_plan* p, InstDesc<double>* d);
 void fill_init(const shg_plan* p, InitDesc* d);
 
 // Kernel launchers (passes_f32.cu / passes_f64.cu / aux.cu).
+// `variant` selects the FFT shape (0 default, 1 alternative where it exists).
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
-                       const void* tw, int hx, cudaStream_t st);
-size_t row_pass_smem(bool fp64, int nx, int hx);
+                       const void* tw, int hx, cudaStream_t st, int variant = 0);
+size_t row_pass_smem(bool fp64, int nx, int hx, int variant = 0);
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
-                       cudaStream_t st);
+                       cudaStream_t st, int variant = 0);
+bool has_fft_variant(bool fp64, int n);
+// FFT shape picked for (precision, length, pass) by the autotuner: measured
+// once per process on the first group that uses it, unless SHG_FFT_VARIANT
+// forces one.  tune_group() must run outside stream capture.
+int fft_variant(bool fp64, int n, int pass);
+shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
+                        const void* tw, int hx, cudaStream_t st);
 cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
                         const void* descs, int nx, int ny, cudaStream_t st);
 cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,

@@ -106,3 +106,13 @@ def test_single_step():
 def test_undepleted_fp32_matches_oracle():
     w = W.plain_focused(n=64, nz=50, undepleted=True, precision="f32")
     _compare(w, ETA_TOL, FIELD_TOL)
+
+
+@pytest.mark.parametrize("variant", ["0", "1"])
+@pytest.mark.parametrize("n", [64, 128, 256])
+def test_both_fft_shapes_of_the_autotuner(n, variant, monkeypatch):
+    """Each FFT shape the autotuner can pick (forced through SHG_FFT_VARIANT)
+    matches the oracle on its own."""
+    monkeypatch.setenv("SHG_FFT_VARIANT", variant)
+    w = W.depleted_absorbing(n=n, nz=6, tgrid=(9, 7, 5), p1=400.0)
+    _compare(w, ETA_TOL, FIELD_TOL)
