@@ -106,6 +106,13 @@ shg_status_t shg_plan_create(const shg_grid_t *grid, const shg_crystal_t *crysta
 /* Release every device buffer of the plan.  NULL is accepted. */
 shg_status_t shg_plan_destroy(shg_plan_t *plan);
 
+/* Bound on the polls of each device-side wait of this plan's kernels (the
+ * mbarrier waits of the TMA-staged column pass; default 2^20, about a
+ * second).  A wait that runs out makes its CTA skip its tile and the next
+ * shg_efficiency / shg_batch_submit return SHG_ERR_TIMEOUT; the context stays
+ * usable.  0 makes every such wait give up at once (a test of that path). */
+shg_status_t shg_set_wait_limit(shg_plan_t *plan, unsigned polls);
+
 /* Replace the beam parameters (Eq. 5/6 inputs, T_off, undepleted switch) and
  * drop any fields set by shg_set_fields.  Grid and crystal are unchanged. */
 shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);

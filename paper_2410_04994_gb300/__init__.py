@@ -67,6 +67,7 @@ _SIGS = {
     "shg_plan_create": [ctypes.POINTER(shg_grid_t), ctypes.POINTER(shg_crystal_t),
                         ctypes.POINTER(shg_beams_t), _I, ctypes.POINTER(_P)],
     "shg_plan_destroy": [_P],
+    "shg_set_wait_limit": [_P, ctypes.c_uint],
     "shg_set_beams": [_P, ctypes.POINTER(shg_beams_t)],
     "shg_set_temperature": [_P, _P, _I, _I, _I, _D, _D, _P],
     "shg_set_fields": [_P, _P, _P, _P],
@@ -144,6 +145,10 @@ def shg_plan_create(grid: shg_grid_t, crystal: shg_crystal_t, beams: shg_beams_t
 
 def shg_plan_destroy(plan: int) -> None:
     _check(_lib().shg_plan_destroy(plan), "shg_plan_destroy")
+
+
+def shg_set_wait_limit(plan: int, polls: int) -> None:
+    _check(_lib().shg_set_wait_limit(plan, int(polls)), "shg_set_wait_limit")
 
 
 def shg_set_beams(plan: int, beams: shg_beams_t) -> None:

@@ -164,6 +164,48 @@ static shg_status_t build_heat_index(shg_plan* p) {
     return SHG_OK;
 }
 
+// ---------------------------------------------------------- tensor maps ----
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(f);
+    });
+    return fn;
+}
+
+// Tensor map of the plan's field buffer seen as 8-byte elements
+// [2 fields][ny][nx], with boxes of (column tile) x (up to 256 rows) x 1.
+static shg_status_t build_tensor_map(shg_plan* p) {
+    const int tile = col_tma_tile(p->fp64, p->g.ny);
+    if (tile <= 0) return SHG_OK;
+    EncodeTiledFn enc = encode_tiled();
+    if (!enc) return SHG_OK;  // no driver entry point: the cp.async column pass is used
+    const cuuint64_t dims[3] = {cuuint64_t(p->g.nx), cuuint64_t(p->g.ny), 2};
+    const cuuint64_t strides[2] = {cuuint64_t(p->g.nx) * 8, cuuint64_t(p->g.nx) * p->g.ny * 8};
+    const cuuint32_t box[3] = {cuuint32_t(tile), cuuint32_t(std::min(p->g.ny, 256)), 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = enc(&p->cmap, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, p->field, dims, strides,
+                           box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return SHG_OK;  // not encodable: cp.async column pass
+    SHG_CK(cudaMalloc(&p->cmap_dev, sizeof(CUtensorMap)));
+    SHG_CK(cudaMemcpy(p->cmap_dev, &p->cmap, sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    p->has_cmap = true;
+    return SHG_OK;
+}
+
 // ------------------------------------------------------ descriptors ----
 
 template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void* field) {
@@ -201,6 +243,8 @@ template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void
     d->g = R(p->c.ddk_dT);
     d->dz = R(p->c.L / p->g.nz);
     d->undepleted = p->b.undepleted ? 1 : 0;
+    d->status = p->status;
+    d->wait_polls = p->wait_polls;
     if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
         d->Q = p->Q;
         d->hix = p->hix;
@@ -270,61 +314,85 @@ static std::map<std::tuple<bool, int, int>, int> g_tuned;
 
 static int forced_variant() {
     const char* f = getenv("SHG_FFT_VARIANT");
-    return (f && (f[0] == '0' || f[0] == '1') && f[1] == 0) ? f[0] - '0' : -1;
+    return (f && f[0] >= '0' && f[0] <= '2' && f[1] == 0) ? f[0] - '0' : -1;
+}
+
+// Candidate flavours of a pass for a length: the default shape, the
+// alternative shape, and (column pass) the TMA-staged kernel.
+static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
+    std::vector<int> c{0};
+    if (has_fft_variant(fp64, n)) c.push_back(1);
+    if (pass == 1 && tmaps && col_tma_tile(fp64, n) > 0) c.push_back(2);
+    return c;
 }
 
 int fft_variant(bool fp64, int n, int pass) {
-    if (!has_fft_variant(fp64, n)) return 0;
     const int f = forced_variant();
-    if (f >= 0) return f;
+    if (f >= 0) {
+        if (f == 1 && !has_fft_variant(fp64, n)) return 0;
+        if (f == 2 && pass == 0) return 0;
+        return f;
+    }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tuned.find(std::make_tuple(fp64, n, pass));
     return it == g_tuned.end() ? 0 : it->second;
 }
 
-// Time both FFT shapes of each pass of this group on its own data (one
-// warm-up and three timed launches each, CUDA events on `st`) and keep the
-// faster one for the rest of the process.  The group's fields are modified;
+// Time every candidate flavour of each pass of this group on its own data
+// (one warm-up and three launches each, CUDA events on `st`) and keep the
+// fastest for the rest of the process.  The group's fields are modified;
 // every propagation re-initialises them first.
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st) {
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps) {
     if (forced_variant() >= 0) return SHG_OK;
     for (int pass = 0; pass < 2; ++pass) {
         const int n = pass == 0 ? nx : ny;
-        if (!has_fft_variant(fp64, n)) continue;
+        const std::vector<int> cand = candidates(fp64, n, pass, tmaps != nullptr);
+        if (cand.size() < 2) continue;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             if (g_tuned.count(std::make_tuple(fp64, n, pass))) continue;
         }
-        float best[2] = {0, 0};
         cudaEvent_t e0, e1;
         SHG_CK(cudaEventCreate(&e0));
         SHG_CK(cudaEventCreate(&e1));
         const int s = nz > 1 ? 1 : 0;
-        for (int v = 0; v < 2; ++v) {
+        int best_v = 0;
+        float best_t = 1e30f;
+        for (int v : cand) {
             for (int rep = 0; rep < 4; ++rep) {
                 if (rep == 1) SHG_CK(cudaEventRecord(e0, st));
                 const cudaError_t e = pass == 0
                     ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v)
-                    : launch_col(fp64, ny, descs, ninst, nx, tw, st, v);
+                    : launch_col(fp64, ny, descs, ninst, nx, tw, st, v, tmaps);
                 if (e != cudaSuccess) return cuda_fail(e, "tune_group");
             }
             SHG_CK(cudaEventRecord(e1, st));
             SHG_CK(cudaEventSynchronize(e1));
-            SHG_CK(cudaEventElapsedTime(&best[v], e0, e1));
+            float t = 0;
+            SHG_CK(cudaEventElapsedTime(&t, e0, e1));
+            if (t < best_t) {
+                best_t = t;
+                best_v = v;
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[std::make_tuple(fp64, n, pass)] = best[1] < best[0] ? 1 : 0;
+        g_tuned[std::make_tuple(fp64, n, pass)] = best_v;
     }
     return SHG_OK;
 }
 
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
                              const InitDesc* idescs, int ninst, const void* tw,
-                             const std::vector<shg_plan*>& plans, cudaStream_t st) {
+                             const std::vector<shg_plan*>& plans, cudaStream_t st,
+                             const void* tmaps) {
     const bool custom = plans[0]->custom_init;
+    for (shg_plan* p : plans) {
+        const cudaError_t e0 = cudaMemsetAsync(p->status, 0, sizeof(int), st);
+        if (e0 != cudaSuccess) return cuda_fail(e0, "memset status");
+    }
     cudaError_t e = custom ? launch_copy_init(fp64, idescs, ninst, descs, nx, ny, st)
                            : launch_init(fp64, idescs, nullptr, ninst, descs, nx, ny, st);
     if (e != cudaSuccess) return cuda_fail(e, "init");
@@ -346,7 +414,7 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
         e = launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, vr);
         if (e != cudaSuccess) return cuda_fail(e, "row pass");
         if (s < nz) {
-            e = launch_col(fp64, ny, descs, ninst, nx, tw, st, vc);
+            e = launch_col(fp64, ny, descs, ninst, nx, tw, st, vc, tmaps);
             if (e != cudaSuccess) return cuda_fail(e, "column pass");
         }
     }
@@ -380,13 +448,15 @@ static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
 
 static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
     std::vector<shg_plan*> one{p};
+    const void* tmaps = p->has_cmap ? p->cmap_dev : nullptr;
     auto body = [&](cudaStream_t s) {
         return enqueue_forward(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, p->idesc, 1, p->tw,
-                               one, s);
+                               one, s, tmaps);
     };
     {
         int hx = ((p->flags & SHG_FLAG_THERMAL) && p->Q) ? p->g.hx : 0;
-        shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st);
+        shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st,
+                                    p->has_cmap ? p->cmap_dev : nullptr);
         if (r != SHG_OK) return r;
     }
     if (!use_graphs()) return body(st);
@@ -479,6 +549,7 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     ALLOC(p->idesc, sizeof(InitDesc));
     ALLOC(p->red, 2 * kRedBlocks * sizeof(double));
     ALLOC(p->pw, 2 * sizeof(double));
+    ALLOC(p->status, sizeof(int));
     if (flags & SHG_FLAG_THERMAL) {
         const size_t nh = size_t(grid->hx) * grid->hy * grid->hz;
         ALLOC(p->Q, nh * sizeof(double));
@@ -496,9 +567,11 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     }
 #undef ALLOC
     if ((e = cudaMemset(p->field, 0, 2 * npts * p->csize)) != cudaSuccess) return fail(e, "memset");
+    if ((e = cudaMemset(p->status, 0, sizeof(int))) != cudaSuccess) return fail(e, "memset");
     if ((e = cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking)) != cudaSuccess)
         return fail(e, "cudaStreamCreate");
     if ((st = build_prop_tables(p)) != SHG_OK || (st = build_phase_table(p)) != SHG_OK ||
+        (st = build_tensor_map(p)) != SHG_OK ||
         (st = build_twiddles(p)) != SHG_OK ||
         ((flags & SHG_FLAG_THERMAL) && (st = build_heat_index(p)) != SHG_OK) ||
         (st = upload_desc(p)) != SHG_OK ||
@@ -520,7 +593,7 @@ static void plan_free(shg_plan* p) {
     void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
                     p->tw,    p->ttab,   p->tmap, p->desc, p->idesc, p->red, p->pw,
                     p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->theat_f,
-                    p->hred};
+                    p->hred,  p->status, p->cmap_dev};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -531,6 +604,14 @@ shg_status_t shg_plan_destroy(shg_plan_t* p) {
     if (p->has_result || p->last_stream) cudaStreamSynchronize(p->last_stream);
     plan_free(p);
     return SHG_OK;
+}
+
+shg_status_t shg_set_wait_limit(shg_plan_t* p, unsigned polls) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    p->wait_polls = polls;
+    return upload_desc(p);
 }
 
 shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
@@ -624,6 +705,9 @@ shg_status_t shg_efficiency(shg_plan_t* p, double* eta, double* p_f, double* p_s
     if (!p) return SHG_ERR_INVALID_ARG;
     if (!p->has_result) return SHG_ERR_STATE;
     SHG_CK(cudaStreamSynchronize(p->last_stream));
+    int kst = 0;
+    SHG_CK(cudaMemcpy(&kst, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (kst != 0) return shg_status_t(kst);
     if (!p->batch_result)
         SHG_CK(cudaMemcpy(p->pw_host, p->pw, 2 * sizeof(double), cudaMemcpyDeviceToHost));
     const double e = p->b.p1 > 0 ? p->pw_host[1] / p->b.p1 : 0.0;
@@ -660,6 +744,7 @@ struct BatchGroup {
     void* descs = nullptr;      // device InstDesc[n]
     InitDesc* idescs = nullptr; // device InitDesc[n]
     double* pw = nullptr;       // device [n][2]
+    void* tmaps = nullptr;      // device CUtensorMap[n], or nullptr (cp.async column pass)
 };
 
 struct BatchEntry {
@@ -681,6 +766,7 @@ static void free_entry(BatchEntry* b) {
         if (g.descs) cudaFree(g.descs);
         if (g.idescs) cudaFree(g.idescs);
         if (g.pw) cudaFree(g.pw);
+        if (g.tmaps) cudaFree(g.tmaps);
     }
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap) cudaStreamDestroy(b->cap);
@@ -715,6 +801,18 @@ static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry*
             (e = cudaMalloc((void**)&g.pw, n * 2 * sizeof(double))) != cudaSuccess) {
             free_entry(b);
             return cuda_fail(e, "batch alloc");
+        }
+        bool all_tmaps = true;
+        for (shg_plan* p : g.plans) all_tmaps &= p->has_cmap;
+        if (all_tmaps) {
+            std::vector<CUtensorMap> hm(n);
+            for (int k = 0; k < n; ++k) hm[k] = g.plans[k]->cmap;
+            if ((e = cudaMalloc(&g.tmaps, n * sizeof(CUtensorMap))) != cudaSuccess ||
+                (e = cudaMemcpy(g.tmaps, hm.data(), n * sizeof(CUtensorMap),
+                                cudaMemcpyHostToDevice)) != cudaSuccess) {
+                free_entry(b);
+                return cuda_fail(e, "batch tensor maps");
+            }
         }
     }
     if ((e = cudaMallocHost((void**)&b->pw_host, b->n * 2 * sizeof(double))) != cudaSuccess ||
@@ -775,7 +873,7 @@ static shg_status_t enqueue_batch(BatchEntry* b, cudaStream_t st) {
         cudaStream_t s = b->side[i];
         SHG_CK(cudaStreamWaitEvent(s, fork, 0));
         shg_status_t r = enqueue_forward(g.fp64, g.nx, g.ny, g.nz, g.descs, g.idescs,
-                                         int(g.plans.size()), g.plans[0]->tw, g.plans, s);
+                                         int(g.plans.size()), g.plans[0]->tw, g.plans, s, g.tmaps);
         if (r != SHG_OK) return r;
         SHG_CK(cudaEventRecord(b->ev[i], s));
         SHG_CK(cudaStreamWaitEvent(st, b->ev[i], 0));
@@ -835,7 +933,7 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         for (shg_plan* p : g.plans)
             if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
         if ((r = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs, int(g.plans.size()),
-                            g.plans[0]->tw, hx, st)) != SHG_OK)
+                            g.plans[0]->tw, hx, st, g.tmaps)) != SHG_OK)
             return r;
     }
     if (use_graphs()) {
@@ -859,6 +957,11 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
             SHG_CK(cudaMemcpyAsync(ent->pw_host + 2 * g.index[k], g.pw + 2 * k,
                                    2 * sizeof(double), cudaMemcpyDeviceToHost, st));
     SHG_CK(cudaStreamSynchronize(st));
+    for (auto p : key) {
+        int kst = 0;
+        SHG_CK(cudaMemcpy(&kst, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (kst != 0) return shg_status_t(kst);
+    }
     bool finite = true;
     for (int i = 0; i < n; ++i) {
         shg_plan* p = key[i];
@@ -909,7 +1012,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
             if (s == 1) {
                 shg_status_t r2 = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs,
-                                             int(g.plans.size()), g.plans[0]->tw, hx, st);
+                                             int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps);
                 if (r2 != SHG_OK) {
                     free_entry(ent);
                     return r2;
@@ -922,7 +1025,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);
                 e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st,
-                               fft_variant(g.fp64, g.ny, 1));
+                               fft_variant(g.fp64, g.ny, 1), g.tmaps);
                 cudaEventRecord(E[3], st);
             }
         }

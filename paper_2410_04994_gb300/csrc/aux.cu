@@ -7,8 +7,9 @@ cudaError_t row_f32(int, int, const void*, int, int, int, int, const void*, int,
 cudaError_t row_f64(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
 size_t row_smem_f32(int, int, int);
 size_t row_smem_f64(int, int, int);
-cudaError_t col_f32(int, int, const void*, int, int, const void*, cudaStream_t);
-cudaError_t col_f64(int, int, const void*, int, int, const void*, cudaStream_t);
+cudaError_t col_f32(int, int, const void*, int, int, const void*, cudaStream_t, const void*);
+cudaError_t col_f64(int, int, const void*, int, int, const void*, cudaStream_t, const void*);
+int col_tma_tile_f32(int);
 bool has_variant_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
@@ -26,10 +27,12 @@ size_t row_pass_smem(bool fp64, int nx, int hx, int variant) {
 }
 
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
-                       cudaStream_t st, int variant) {
-    return fp64 ? col_f64(ny, variant, descs, ninst, nx, tw, st)
-                : col_f32(ny, variant, descs, ninst, nx, tw, st);
+                       cudaStream_t st, int variant, const void* tmaps) {
+    return fp64 ? col_f64(ny, variant, descs, ninst, nx, tw, st, tmaps)
+                : col_f32(ny, variant, descs, ninst, nx, tw, st, tmaps);
 }
+
+int col_tma_tile(bool fp64, int ny) { return fp64 ? 0 : col_tma_tile_f32(ny); }
 
 cudaError_t setup_pass_attributes() {
     cudaError_t e = attr_f32();

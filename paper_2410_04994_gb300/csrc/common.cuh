@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "../../include/shg.h"
+
 #define SHG_HD __host__ __device__ __forceinline__
 #define SHG_D __device__ __forceinline__
 
@@ -72,6 +74,8 @@ template <class R> struct InstDesc {
     int hx, hy, hz;
     R qaF, qaS, qbF, qbS;  // alpha_j I-coefficient and beta_j I^2-coefficient per |A|^2, |A|^4
     R dxdy;
+    int* status;           // set to a non-zero shg_status_t by a kernel that gave up
+    unsigned wait_polls;   // bound on the polls of a device-side wait (0: give up at once)
 };
 
 // Asynchronous global -> shared copies (LDGSTS), so that a whole tile is in

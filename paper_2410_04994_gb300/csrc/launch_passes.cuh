@@ -50,4 +50,17 @@ cudaError_t col_launch(const void* descs, int ninst, int nx, const void* tw, cud
     return cudaGetLastError();
 }
 
+template <int N> cudaError_t col_tma_attr() { return allow_max_dyn_smem(k_col_tma<N>); }
+
+template <int N>
+cudaError_t col_tma_launch(const void* tmaps, const void* descs, int ninst, int nx, const void* tw,
+                           cudaStream_t st) {
+    using K = ColTma<N>;
+    dim3 grid((nx + K::TILE - 1) / K::TILE, ninst);
+    k_col_tma<N><<<grid, kPassThreads, K::smem, st>>>(static_cast<const CUtensorMap*>(tmaps),
+                                                      static_cast<const InstDesc<float>*>(descs),
+                                                      nx, static_cast<const pt<float>*>(tw));
+    return cudaGetLastError();
+}
+
 }  // namespace shg

@@ -16,6 +16,7 @@
 #include "common.cuh"
 #include "fft.cuh"
 #include "nonlinear.cuh"
+#include "tma.cuh"
 
 namespace shg {
 
@@ -242,6 +243,77 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
         fft_mul_ifft<R, NY, V>(v, sb, t, tw, py + f * NY);
         if (active) {
             C* col = field + size_t(f) * NY * nx + x;
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
+        }
+    }
+}
+
+// Column pass staged by TMA (FP32).  One elected thread issues 3-D box copies
+// of the CTA's TILE columns of both fields ([field][row][column] boxes of up
+// to 256 rows) from the instance's tensor map into a dense shared buffer;
+// the block waits on an mbarrier with a bounded number of polls (on expiry it
+// records SHG_ERR_TIMEOUT in the instance status and returns).  Each field is
+// then transformed from that buffer through one padded exchange buffer and
+// written back from registers.  grid = (ceil(nx / TILE), instances).
+template <int NY> struct ColTma {
+    using G = ColGeom<float, NY, 0>;
+    static constexpr int TILE = G::TILE, S = G::S, BY = NY < 256 ? NY : 256;
+    static constexpr size_t stage_bytes = size_t(2) * NY * TILE * sizeof(float2);
+    static constexpr size_t smem = 128 + stage_bytes + size_t(TILE) * S * sizeof(float2) + 16;
+};
+
+constexpr unsigned kTmaMaxPolls = 1u << 20;
+
+template <int NY>
+__global__ void __launch_bounds__(kPassThreads, 2)
+    k_col_tma(const CUtensorMap* __restrict__ tmaps, const InstDesc<float>* __restrict__ descs,
+              int nx, const pt<float>* __restrict__ tw) {
+    using K = ColTma<NY>;
+    using G = typename K::G;
+    constexpr int E = FftCfg<float, NY, 0>::E, T = G::T, TILE = K::TILE, S = K::S, BY = K::BY;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float2* stage = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
+                                              ~uintptr_t(127));
+    float2* exch = stage + 2 * NY * TILE;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(exch + TILE * S);
+    const InstDesc<float>& d = descs[blockIdx.y];
+    const int x0 = blockIdx.x * TILE;
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, unsigned(K::stage_bytes));
+        const CUtensorMap* tm = tmaps + blockIdx.y;
+#pragma unroll
+        for (int f = 0; f < 2; ++f)
+#pragma unroll
+            for (int yb = 0; yb < NY; yb += BY)
+                tma_load_3d(stage + (size_t(f) * NY + yb) * TILE, tm, x0, yb, f, bar);
+    }
+    const bool ok = mbar_wait_bounded(bar, 0, d.wait_polls);
+    if (__syncthreads_or(!ok)) {
+        // Give up on this tile: report, then let the copies already issued
+        // land (bounded again) before the CTA's shared memory is released.
+        if (threadIdx.x == 0) {
+            if (d.status) atomicExch(d.status, int(SHG_ERR_TIMEOUT));
+            mbar_wait_bounded(bar, 0, kTmaMaxPolls);
+        }
+        return;
+    }
+    const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
+    const int x = x0 + c;
+    const bool active = x < nx;
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = stage[(size_t(f) * NY + t + T * m) * TILE + c];
+        fft_mul_ifft<float, NY, 0>(v, exch + c * S, t, tw, d.py + f * NY);
+        if (active) {
+            float2* col = d.field + size_t(f) * NY * nx + x;
 #pragma unroll
             for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
         }

@@ -7,6 +7,7 @@ namespace shg {
 
 #define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 #define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
+#define SHG_F32_TMA_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
@@ -27,8 +28,25 @@ cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz,
     return cudaErrorInvalidValue;
 }
 
+// Column tile width of the TMA-staged column pass for length ny (0: none).
+int col_tma_tile_f32(int ny) {
+    switch (ny) {
+#define X(n) case n: return ColTma<n>::TILE;
+        SHG_F32_TMA_SIZES(X)
+#undef X
+    }
+    return 0;
+}
+
 cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const void* tw,
-                    cudaStream_t st) {
+                    cudaStream_t st, const void* tmaps) {
+    if (v == 2 && tmaps != nullptr) {
+        switch (ny) {
+#define X(n) case n: return col_tma_launch<n>(tmaps, descs, ninst, nx, tw, st);
+            SHG_F32_TMA_SIZES(X)
+#undef X
+        }
+    }
     if (v == 1) {
         switch (ny) {
 #define X(n) case n: return col_launch<float, n, 1>(descs, ninst, nx, tw, st);
@@ -55,6 +73,10 @@ cudaError_t attr_f32() {
     if (e == cudaSuccess) e = row_attr<float, n, 1>(); \
     if (e == cudaSuccess) e = col_attr<float, n, 1>();
     SHG_F32_VARIANT_SIZES(X)
+#undef X
+#define X(n) \
+    if (e == cudaSuccess) e = col_tma_attr<n>();
+    SHG_F32_TMA_SIZES(X)
 #undef X
     return e;
 }

@@ -17,7 +17,7 @@ cudaError_t row_f64(int nx, int, const void* descs, int ninst, int ny, int nz, i
 }
 
 cudaError_t col_f64(int ny, int, const void* descs, int ninst, int nx, const void* tw,
-                    cudaStream_t st) {
+                    cudaStream_t st, const void*) {
     switch (ny) {
 #define X(n) case n: return col_launch<double, n>(descs, ninst, nx, tw, st);
         SHG_F64_SIZES(X)

@@ -1,5 +1,6 @@
 // Internal definitions shared by the host-side translation units of libshg.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <string>
@@ -73,6 +74,13 @@ struct shg_plan {
     float* theat_f = nullptr; // dT rounded to float, as installed as the map
     double* hred = nullptr;   // reduction scratch of the heat solve
 
+    // tensor map of `field` for the TMA column pass (FP32, supported lengths)
+    CUtensorMap cmap;
+    void* cmap_dev = nullptr;
+    bool has_cmap = false;
+    int* status = nullptr;     // device status word written by kernels that give up
+    unsigned wait_polls = 1u << 20;  // bound on each device-side wait (shg_set_wait_limit)
+
     // forward graph
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t cap = nullptr;
@@ -97,19 +105,24 @@ void fill_desc_f64(const shg_plan* p, InstDesc<double>* d);
 void fill_init(const shg_plan* p, InitDesc* d);
 
 // Kernel launchers (passes_f32.cu / passes_f64.cu / aux.cu).
-// `variant` selects the FFT shape (0 default, 1 alternative where it exists).
+// `variant` selects the kernel flavour: 0 the default FFT shape, 1 the
+// alternative shape where it exists; for the column pass 2 is the TMA-staged
+// kernel (needs `tmaps`).  Unavailable choices fall back to 0.
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
                        const void* tw, int hx, cudaStream_t st, int variant = 0);
 size_t row_pass_smem(bool fp64, int nx, int hx, int variant = 0);
+// `tmaps`: per-instance tensor maps of the fields (CUtensorMap[ninst]) for
+// the TMA-staged column pass, or nullptr for the cp.async-staged one.
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
-                       cudaStream_t st, int variant = 0);
+                       cudaStream_t st, int variant = 0, const void* tmaps = nullptr);
+int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
-// FFT shape picked for (precision, length, pass) by the autotuner: measured
-// once per process on the first group that uses it, unless SHG_FFT_VARIANT
-// forces one.  tune_group() must run outside stream capture.
+// Kernel flavour picked for (precision, length, pass) by the autotuner:
+// measured once per process on the first group that uses it, unless
+// SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.
 int fft_variant(bool fp64, int n, int pass);
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st);
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps);
 cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
                         const void* descs, int nx, int ny, cudaStream_t st);
 cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
@@ -121,7 +134,8 @@ cudaError_t setup_pass_attributes();
 // Enqueue the whole forward propagation of instances sharing one grid.
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
                              const InitDesc* idescs, int ninst, const void* tw,
-                             const std::vector<shg_plan*>& plans, cudaStream_t st);
+                             const std::vector<shg_plan*>& plans, cudaStream_t st,
+                             const void* tmaps = nullptr);
 
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);

@@ -79,3 +79,20 @@ def test_sweep_instances_full_length(n):
     a_f, a_sh = plans[k].fields()
     assert rel_l2(a_sh.cpu(), AS) < FIELD_TOL
     assert rel_l2(a_f.cpu(), AF) < FIELD_TOL
+
+
+@pytest.mark.parametrize("variant", ["1", "2"])
+def test_batch_with_each_forced_kernel_flavour(variant, monkeypatch):
+    """The batch path with the alternative FFT shape (1) or the TMA-staged
+    column pass over the group's tensor-map array (2) forced, against the
+    oracle per instance."""
+    import paper_2410_04994_gb300 as pkg
+    monkeypatch.setenv("SHG_FFT_VARIANT", variant)
+    insts = W.sweep_instances(nz=12, groups=((64, 2), (128, 2), (256, 1)), tgrid=(9, 9, 12))
+    plans = _plans(insts)
+    etas = pkg.shg_batch_submit([p.handle for p in plans])
+    for p, w, e in zip(plans, insts, etas):
+        eta_ref, AF, AS = oracle_run(w)
+        assert abs(e / eta_ref - 1) < ETA_TOL, (w.name, e, eta_ref)
+        a_f, a_sh = p.fields()
+        assert rel_l2(a_sh.cpu(), AS) < FIELD_TOL

@@ -108,11 +108,36 @@ def test_undepleted_fp32_matches_oracle():
     _compare(w, ETA_TOL, FIELD_TOL)
 
 
-@pytest.mark.parametrize("variant", ["0", "1"])
-@pytest.mark.parametrize("n", [64, 128, 256])
-def test_both_fft_shapes_of_the_autotuner(n, variant, monkeypatch):
-    """Each FFT shape the autotuner can pick (forced through SHG_FFT_VARIANT)
-    matches the oracle on its own."""
+@pytest.mark.parametrize("variant", ["0", "1", "2"])
+@pytest.mark.parametrize("n", [32, 64, 128, 256, 1024])
+def test_every_kernel_flavour_of_the_autotuner(n, variant, monkeypatch):
+    """Each kernel flavour the autotuner can pick, forced through
+    SHG_FFT_VARIANT (0/1: the two FFT shapes with cp.async staging, 2: the
+    TMA-staged column pass), matches the oracle on its own."""
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
-    w = W.depleted_absorbing(n=n, nz=6, tgrid=(9, 7, 5), p1=400.0)
+    w = W.depleted_absorbing(n=n, nz=6 if n < 1024 else 1, tgrid=(9, 7, 5), p1=400.0)
     _compare(w, ETA_TOL, FIELD_TOL)
+
+
+def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
+    """A device-side wait that runs out (the TMA column pass with a poll
+    limit of 0, so every mbarrier wait gives up at once) is reported as
+    SHG_ERR_TIMEOUT by the next efficiency call; the CTAs drain their copies
+    before returning, and the same plan with the default limit afterwards
+    matches the oracle."""
+    import paper_2410_04994_gb300 as pkg
+    monkeypatch.setenv("SHG_FFT_VARIANT", "2")
+    w = W.plain_focused(n=64, nz=4, precision="f32")
+    plan = pkg.Plan(w)
+    pkg.shg_set_wait_limit(plan.handle, 0)
+    plan.propagate()
+    with pytest.raises(pkg.ShgError) as ei:
+        plan.efficiency()
+    assert ei.value.status == pkg.SHG_ERR_TIMEOUT
+    pkg.shg_set_wait_limit(plan.handle, 1 << 20)
+    plan.propagate()
+    eta, _, _ = plan.efficiency()
+    eta_ref, _, _ = oracle_run(w)
+    assert abs(eta / eta_ref - 1) < ETA_TOL
+    with pytest.raises(pkg.ShgError):
+        pkg.shg_set_wait_limit(None, 0)
