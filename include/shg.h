@@ -91,7 +91,9 @@ typedef struct {
 enum {
     SHG_FLAG_FP64 = 1,    /* fields and arithmetic in double precision */
     SHG_FLAG_THERMAL = 2, /* deposit q_dot (Eq. 8) on the heat grid while propagating */
-    SHG_FLAG_ADJOINT = 4  /* keep sqrt(nz)-spaced checkpoints for shg_propagate_adjoint */
+    SHG_FLAG_ADJOINT = 4, /* keep sqrt(nz)-spaced checkpoints for shg_propagate_adjoint */
+    SHG_FLAG_NODE_SAMPLER = 8 /* FP32: sample the temperature map at its nodes in every pass
+                                 instead of keeping a per-point table (less memory, slower) */
 };
 
 typedef struct shg_plan shg_plan_t;
@@ -122,7 +124,10 @@ shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
  * [-t_ly/2, t_ly/2] x [0, L]; t_lx or t_ly <= 0 means the field window.
  * Copied into the plan together with its cumulative z-integral (Eq. 3,
  * trapezoid on the nodes).  tx, ty, tz >= 2.  dT_dev == NULL clears the map
- * (uniform temperature T_off). */
+ * (uniform temperature T_off).  FP32 plans without SHG_FLAG_NODE_SAMPLER also
+ * keep every map layer bilinearly sampled at every field point (tz*ny*nx*8
+ * bytes of device memory; the nodes are sampled in the passes instead when
+ * that table would exceed 4 GiB). */
 shg_status_t shg_set_temperature(shg_plan_t *plan, const float *dT_dev, int tx, int ty,
                                  int tz, double t_lx, double t_ly, shg_stream_t stream);
 

@@ -29,6 +29,7 @@ SHG_ERR_STATE = 7
 SHG_FLAG_FP64 = 1
 SHG_FLAG_THERMAL = 2
 SHG_FLAG_ADJOINT = 4
+SHG_FLAG_NODE_SAMPLER = 8
 
 
 class shg_grid_t(ctypes.Structure):
@@ -266,13 +267,15 @@ class Plan:
     """Owning handle around an shg plan (destroyed with the object)."""
 
     def __init__(self, w, flags: Optional[int] = None, thermal: bool = False,
-                 adjoint: bool = False):
+                 adjoint: bool = False, node_sampler: bool = False):
         if flags is None:
             flags = SHG_FLAG_FP64 if getattr(w, "precision", "f32") == "f64" else 0
             if thermal:
                 flags |= SHG_FLAG_THERMAL
             if adjoint:
                 flags |= SHG_FLAG_ADJOINT
+            if node_sampler:
+                flags |= SHG_FLAG_NODE_SAMPLER
         self.w = w
         self.flags = flags
         self.fp64 = bool(flags & SHG_FLAG_FP64)

@@ -27,6 +27,10 @@ shg_status_t cuda_fail(cudaError_t e, const char* what) {
 cudaError_t launch_copy_init(bool fp64, const InitDesc* idescs, int ninst, const void* descs,
                              int nx, int ny, cudaStream_t st);
 
+// Largest per-point temperature table a plan keeps (beyond it the passes
+// sample the node table).
+constexpr size_t kUmapMaxBytes = size_t(4) << 30;
+
 static bool pow2_in(int n, int lo, int hi) { return n >= lo && n <= hi && (n & (n - 1)) == 0; }
 
 static std::once_flag g_attr_once;
@@ -218,6 +222,7 @@ template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void
     d->py = static_cast<const pt<R>*>(p->py);
     d->eph = static_cast<const cx<R>*>(p->eph);
     d->ttab = static_cast<const cx<R>*>(p->ttab);
+    d->umap = (!p->fp64 && p->ttab) ? static_cast<const cx<R>*>(p->umap) : nullptr;
     d->tx = p->tx;
     d->ty = p->ty;
     d->tz = p->tz;
@@ -317,6 +322,16 @@ static int forced_variant() {
     return (f && f[0] >= '0' && f[0] <= '2' && f[1] == 0) ? f[0] - '0' : -1;
 }
 
+int row_umap_bit(const std::vector<shg_plan*>& plans) {
+    bool any = false;
+    for (const shg_plan* p : plans) {
+        if (!p->ttab) continue;
+        if (!p->umap || !(double(p->tz - 1) < 0.99 * p->g.nz)) return 0;
+        any = true;
+    }
+    return any ? kRowUmap : 0;
+}
+
 // Candidate flavours of a pass for a length: the default shape, the
 // alternative shape, and (column pass) the TMA-staged kernel.
 static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
@@ -343,7 +358,7 @@ int fft_variant(bool fp64, int n, int pass) {
 // fastest for the rest of the process.  The group's fields are modified;
 // every propagation re-initialises them first.
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st, const void* tmaps) {
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits) {
     if (forced_variant() >= 0) return SHG_OK;
     for (int pass = 0; pass < 2; ++pass) {
         const int n = pass == 0 ? nx : ny;
@@ -363,7 +378,7 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
             for (int rep = 0; rep < 4; ++rep) {
                 if (rep == 1) SHG_CK(cudaEventRecord(e0, st));
                 const cudaError_t e = pass == 0
-                    ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v)
+                    ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v | row_bits)
                     : launch_col(fp64, ny, descs, ninst, nx, tw, st, v, tmaps);
                 if (e != cudaSuccess) return cuda_fail(e, "tune_group");
             }
@@ -405,7 +420,7 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     int hx = 0;
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
-    const int vr = fft_variant(fp64, nx, 0), vc = fft_variant(fp64, ny, 1);
+    const int vr = fft_variant(fp64, nx, 0) | row_umap_bit(plans), vc = fft_variant(fp64, ny, 1);
     for (int s = 0; s <= nz; ++s) {
         for (shg_plan* p : plans) {
             shg_status_t r = adjoint_checkpoint(p, s, st);
@@ -456,7 +471,7 @@ static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
     {
         int hx = ((p->flags & SHG_FLAG_THERMAL) && p->Q) ? p->g.hx : 0;
         shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st,
-                                    p->has_cmap ? p->cmap_dev : nullptr);
+                                    p->has_cmap ? p->cmap_dev : nullptr, row_umap_bit(one));
         if (r != SHG_OK) return r;
     }
     if (!use_graphs()) return body(st);
@@ -515,7 +530,7 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
             !(crystal->wy > 0) || !(crystal->kappa_th > 0))
             return SHG_ERR_INVALID_ARG;
         // the row pass bins the heat deposit per CTA in shared memory
-        for (int v = 0; v < 2; ++v)
+        for (int v : {0, 1, kRowUmap, 1 | kRowUmap})
             if (row_pass_smem(fp64, grid->nx, grid->hx, v) > 223 * 1024)
                 return SHG_ERR_UNSUPPORTED_GRID;
     }
@@ -591,7 +606,7 @@ static void plan_free(shg_plan* p) {
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
     void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
-                    p->tw,    p->ttab,   p->tmap, p->desc, p->idesc, p->red, p->pw,
+                    p->tw,    p->ttab,   p->umap, p->tmap, p->desc, p->idesc, p->red, p->pw,
                     p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->theat_f,
                     p->hred,  p->status, p->cmap_dev};
     for (void* b : bufs)
@@ -642,6 +657,11 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
             p->tx = p->ty = p->tz = 0;
             p->gvalid = false;
         }
+        if (p->umap) {
+            cudaFree(p->umap);
+            p->umap = nullptr;
+            p->umap_bytes = 0;
+        }
         return upload_desc(p);
     }
     if (tx < 2 || ty < 2 || tz < 2) return SHG_ERR_INVALID_ARG;
@@ -663,8 +683,25 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
     if (dT_dev != p->tmap)
         SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
     SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+    // per-point table (FP32): tz layers of the field grid
+    const size_t ub = size_t(tz) * p->g.nx * p->g.ny * sizeof(float2);
+    const bool want = !p->fp64 && !(p->flags & SHG_FLAG_NODE_SAMPLER) && ub <= kUmapMaxBytes &&
+                      tz <= 65535;
+    if (p->umap && (!want || p->umap_bytes != ub)) {
+        cudaFree(p->umap);
+        p->umap = nullptr;
+        p->umap_bytes = 0;
+    }
+    if (want && !p->umap) {
+        SHG_CK(cudaMalloc(&p->umap, ub));
+        p->umap_bytes = ub;
+    }
     SHG_CK(cudaStreamSynchronize(s));
-    return upload_desc(p);
+    shg_status_t r = upload_desc(p);
+    if (r != SHG_OK || !p->umap) return r;
+    SHG_CK(launch_upsample_map(p->desc, p->umap, p->g.nx, p->g.ny, tz, s));
+    SHG_CK(cudaStreamSynchronize(s));
+    return SHG_OK;
 }
 
 shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh_dev,
@@ -739,6 +776,7 @@ struct BatchGroup {
     bool fp64;
     int nx, ny, nz;
     bool custom;
+    int row_bits = 0;           // row_umap_bit() of the plans when the graph was captured
     std::vector<shg_plan*> plans;
     std::vector<int> index;     // position of each plan in the caller's list
     void* descs = nullptr;      // device InstDesc[n]
@@ -793,6 +831,7 @@ static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry*
         g->plans.push_back(p);
         g->index.push_back(i);
     }
+    for (auto& g : b->groups) g.row_bits = row_umap_bit(g.plans);
     cudaError_t e;
     for (auto& g : b->groups) {
         const int n = int(g.plans.size());
@@ -912,8 +951,10 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
     if (ent) {
         // the captured graph depends on each plan's init kind; rebuild if changed
         bool stale = false;
-        for (auto& g : ent->groups)
+        for (auto& g : ent->groups) {
             for (auto p : g.plans) stale |= (p->custom_init != g.custom);
+            stale |= row_umap_bit(g.plans) != g.row_bits;
+        }
         if (stale) {
             free_entry(ent);
             ent = nullptr;
@@ -933,7 +974,7 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         for (shg_plan* p : g.plans)
             if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
         if ((r = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs, int(g.plans.size()),
-                            g.plans[0]->tw, hx, st, g.tmaps)) != SHG_OK)
+                            g.plans[0]->tw, hx, st, g.tmaps, row_umap_bit(g.plans))) != SHG_OK)
             return r;
     }
     if (use_graphs()) {
@@ -1012,7 +1053,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
             if (s == 1) {
                 shg_status_t r2 = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs,
-                                             int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps);
+                                             int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps,
+                                             row_umap_bit(g.plans));
                 if (r2 != SHG_OK) {
                     free_entry(ent);
                     return r2;
@@ -1020,7 +1062,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 cudaEventRecord(E[0], st);
             }
             e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
-                           g.plans[0]->tw, hx, st, fft_variant(g.fp64, g.nx, 0));
+                           g.plans[0]->tw, hx, st,
+                           fft_variant(g.fp64, g.nx, 0) | row_umap_bit(g.plans));
             cudaEventRecord(E[1], st);
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);

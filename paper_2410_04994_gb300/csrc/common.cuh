@@ -50,12 +50,17 @@ template <class C> SHG_HD C cconj(C a) { return mk<C>(a.x, -a.y); }
 
 // ------------------------------------------------------ per-instance ----
 // Everything one pass needs about one instance; built on the host by the plan.
+// Launch-variant bit of the row pass: read the per-point temperature table.
+constexpr int kRowUmap = 4;
+
 template <class R> struct InstDesc {
     cx<R>* field;          // [2][ny][nx]: A_F then A_SH
     const pt<R>* px;       // [2][nx] row factor exp(-i Kx^2 dz/2k_j) exp(-alpha_j dz/2) / nx
     const pt<R>* py;       // [2][ny] column factor exp(-i Ky^2 dz/2k_j) / ny
     const cx<R>* eph;      // [4 nz + 1] e^{i theta(q dz/4)}, theta = (dk0 + g T_off) z mod 2 pi
     const cx<R>* ttab;     // [tz][ty][tx] (dT, C) or nullptr for a uniform temperature
+    const cx<R>* umap;     // [tz][ny][nx] (dT, C) of every map layer bilinearly sampled at
+                           // every field point, or nullptr (sample ttab in the pass)
     int tx, ty, tz;
     R tx0, tdx_inv, ty0, tdy_inv, tdz_inv;  // node 0 position and 1/spacing of the map
     R x0, dx, y0, dy;      // field sample positions x_m = x0 + m dx
@@ -86,6 +91,24 @@ template <class C> SHG_D void cp_async(C* smem_dst, const C* gsrc) {
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc));
     else
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gsrc));
+}
+// 8-byte cp.async whose L2 lines are the first to be evicted (data streamed
+// once per pass, so that it does not push re-read data such as the fields out
+// of L2).
+SHG_D uint64_t l2_evict_first_policy() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
+    return pol;
+}
+template <class C> SHG_D void cp_async_stream(C* smem_dst, const C* gsrc, uint64_t pol) {
+    static_assert(sizeof(C) == 8, "8-byte elements");
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s),
+                 "l"(gsrc), "l"(pol));
+}
+SHG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N> SHG_D void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 SHG_D void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::);

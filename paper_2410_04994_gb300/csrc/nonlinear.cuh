@@ -66,6 +66,23 @@ template <class R> struct TempSampler {
     }
 };
 
+// The same interface over values already sampled at the point: the (dT, C)
+// of consecutive map layers lmin, lmin + 1, ... held in shared memory
+// `stride` elements apart (the pass prefetches them from the per-point table).
+template <class R> struct SlotSampler {
+    using V = cx<R>;
+    const V* base;       // layer lmin
+    int stride, lmin;
+
+    SHG_D V at(int l, R t) const {
+        const V va = base[(l - lmin) * stride], vb = base[(l - lmin + 1) * stride];
+        V r;
+        r.x = va.x + t * (vb.x - va.x);
+        r.y = va.y + t * (vb.y - va.y);
+        return r;
+    }
+};
+
 template <class R> SHG_D void sincos_r(R x, R* s, R* c);
 // The argument is reduced to [-pi, pi] first; there the hardware
 // approximation has an absolute error of ~4e-7 (|g C| is a small phase in
@@ -94,9 +111,8 @@ template <class R> SHG_D StageZ<R> stage_z(const InstDesc<R>& d, int q) {
 }
 
 // Stage coefficients at a stage point for the sampler's point.
-template <class R>
-SHG_D Coef<R> coef_at(const InstDesc<R>& d, const StageZ<R>& z, bool thermal,
-                      TempSampler<R>& ts) {
+template <class R, class Sampler>
+SHG_D Coef<R> coef_at(const InstDesc<R>& d, const StageZ<R>& z, bool thermal, Sampler& ts) {
     using C = cx<R>;
     Coef<R> k;
     if (!thermal) {

@@ -25,13 +25,21 @@ constexpr int kPassThreads = 256;
 // Resident CTAs per SM the launch is compiled for (register budget).
 template <int V> struct MinBlocks { static constexpr int value = V == 0 ? 2 : 3; };
 
+// Per-thread prefetch slots of the per-point temperature table (FP32): two
+// buffers x up to three map layers x the two points of one loop iteration.
+constexpr int kSlotLayers = 3;
+template <class R> constexpr size_t slot_bytes() {
+    return sizeof(R) == 4 ? size_t(2) * kSlotLayers * 2 * kPassThreads * sizeof(cx<R>) : 0;
+}
+
 template <class R, int N, int V = 0> struct RowGeom {
     using F = FftCfg<R, N, V>;
     static constexpr int T = F::T;
     static constexpr int ROWS = kPassThreads / T;
     static constexpr int S = padded_len<R>(N, T < Bank<R>::W ? T : 1);
-    static constexpr size_t smem = size_t(2) * ROWS * S * sizeof(cx<R>);
+    static constexpr size_t fields = size_t(2) * ROWS * S * sizeof(cx<R>);
 };
+
 
 template <class R, int N, int V = 0> struct ColGeom {
     using F = FftCfg<R, N, V>;
@@ -77,16 +85,38 @@ SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, cons
     ts.la = -2;
 }
 
+// Copy (cp.async, one group, L2 evict-first) the per-point table values of map layers
+// lmin .. lmin + nl - 1 at points x0 and x0 + T of row y into the calling
+// thread's slots: slot (layer k, point p) at slots[(2k + p) * 256 + thread].
+template <int NX, int T, class C>
+SHG_D void prefetch_slots(C* slots, const C* umap, int lmin, int nl, int ny, int y, int x0) {
+    const uint64_t pol = l2_evict_first_policy();
+#pragma unroll 1
+    for (int k = 0; k < nl; ++k) {
+        const int o = ((lmin + k) * ny + y) * NX + x0;  // < 2^31: the table is <= 4 GiB
+        C* dst = slots + 2 * k * kPassThreads + threadIdx.x;
+        cp_async_stream(dst, umap + o, pol);
+        cp_async_stream(dst + kPassThreads, umap + o + T, pol);
+    }
+    cp_async_commit();
+}
+
 // Row pass R(s).  grid = (ceil(ny / ROWS), instances); block = 256.
 //
 // The CTA's rows of both fields are copied into padded shared buffers with
 // cp.async (all copies in flight at once).  Each thread owns the points
 // x = t + T*m of its row; the nonlinear part runs point by point in a rolled
 // loop on the shared copy, so no register array is indexed dynamically, and
-// the transforms then run field by field from the same buffers.  The heat
-// deposit at z_s (THERMAL plans) is binned per CTA in shared memory and added
-// to the heat grid with one double-precision atomic per touched node.
-template <class R, int NX, int V = 0>
+// the transforms then run field by field from the same buffers.  With a
+// per-point temperature table (FP32), the (dT, C) of the map layers that this
+// step's stage points fall between are streamed from it by cp.async into
+// per-thread slots one loop iteration ahead (UM: the launcher has checked
+// that every instance with a map has that table and that one step spans less
+// than one map layer, so at most three layers are touched); otherwise each
+// point samples the node table bilinearly.  The heat deposit at z_s (THERMAL plans) is binned
+// per CTA in shared memory and added to the heat grid with one
+// double-precision atomic per touched node.
+template <class R, int NX, int V = 0, bool UM = false>
 __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
@@ -120,14 +150,33 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
         }
     }
     const bool dep = descs[blockIdx.y].Q != nullptr;
-    float* bins = reinterpret_cast<float*>(smem + 2 * ROWS * S);
+    C* slots = reinterpret_cast<C*>(smem_raw + G::fields);
+    float* bins = reinterpret_cast<float*>(smem_raw + G::fields + (UM ? slot_bytes<R>() : 0));
     const int nb = dep ? ROWS * descs[blockIdx.y].hx : 0;
     for (int i = threadIdx.x; i < nb; i += kPassThreads) bins[i] = 0.f;
     __syncthreads();
     const InstDesc<R>& d = dsh;
     const bool thermal = d.ttab != nullptr;
     const MapView<R> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
-    cp_async_wait_all();
+    // Layers lmin .. lmin + nl - 1 hold every stage point of this pass (the
+    // stage layers are non-decreasing in q).
+    const int lmin = zsh[0].l, nl = zsh[4].l + 2 - zsh[0].l;
+    const bool um = UM && thermal;
+    if (um && (d.umap == nullptr || nl > kSlotLayers)) {  // excluded by the launcher
+        cp_async_wait_all();
+        if (threadIdx.x == 0 && d.status) atomicExch(d.status, int(SHG_ERR_STATE));
+        return;
+    }
+    bool staged = false;
+    if constexpr (UM) {
+        if (um && active) {
+            cp_async_commit();  // the field rows
+            prefetch_slots<NX, T>(slots, d.umap, lmin, nl, ny, y, t);
+            cp_async_wait_group<1>();
+            staged = true;
+        }
+    }
+    if (!staged) cp_async_wait_all();
     __syncthreads();
     const R h = R(0.5) * d.dz;
     const int l_dep = dep ? d.hlz[s] : -1;
@@ -135,9 +184,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     const R w_dep = dep ? d.dxdy * d.dz * ((s == 0 || s == nz) ? R(0.5) : R(1)) : R(0);
     const RowCell<R> rc = thermal ? row_cell(d, y) : RowCell<R>{0, R(0)};
     // One point: N_b(s-1) [z_s - dz/2 -> z_s], deposit at z_s, N_a(s).
-    auto point = [&](int xi, C& aF, C& aS) {
-        TempSampler<R> ts;
-        if (thermal) make_sampler(d, mv, xi, rc, ts);
+    auto point = [&](int xi, C& aF, C& aS, auto& ts) {
         const Coef<R> cz = coef_at(d, zsh[2], thermal, ts);  // z_s, shared by both halves
         if (s > 0) {
             const Coef<R> c0 = coef_at(d, zsh[0], thermal, ts);
@@ -167,8 +214,34 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
             const int x0 = t + T * m, x1 = x0 + T;
             C aF0 = sF[pidx<R>(x0)], aS0 = sS[pidx<R>(x0)];
             C aF1 = sF[pidx<R>(x1)], aS1 = sS[pidx<R>(x1)];
-            point(x0, aF0, aS0);
-            point(x1, aF1, aS1);
+            if constexpr (UM) {
+                const int buf = (m >> 1) & 1;
+                if (um) {
+                    if (m + 2 < E) {
+                        prefetch_slots<NX, T>(slots + (buf ^ 1) * kSlotLayers * 2 * kPassThreads,
+                                              d.umap, lmin, nl, ny, y, x1 + T);
+                        cp_async_wait_group<1>();
+                    } else {
+                        cp_async_wait_group<0>();
+                    }
+                }
+                const C* b0 = slots + (buf * kSlotLayers * 2) * kPassThreads + threadIdx.x;
+                SlotSampler<R> s0{b0, 2 * kPassThreads, lmin};
+                SlotSampler<R> s1{b0 + kPassThreads, 2 * kPassThreads, lmin};
+                point(x0, aF0, aS0, s0);
+                point(x1, aF1, aS1, s1);
+            } else {
+                {
+                    TempSampler<R> s0;
+                    if (thermal) make_sampler(d, mv, x0, rc, s0);
+                    point(x0, aF0, aS0, s0);
+                }
+                {
+                    TempSampler<R> s1;
+                    if (thermal) make_sampler(d, mv, x1, rc, s1);
+                    point(x1, aF1, aS1, s1);
+                }
+            }
             sF[pidx<R>(x0)] = aF0;
             sS[pidx<R>(x0)] = aS0;
             sF[pidx<R>(x1)] = aF1;
@@ -318,6 +391,21 @@ __global__ void __launch_bounds__(kPassThreads, 2)
             for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
         }
     }
+}
+
+// Per-point temperature table: umap[l][y][x] = the bilinear sample of map
+// layer l at field point (x, y), with the same cell arithmetic as the passes'
+// node sampler.  grid = (ceil(nx / 256), ny, tz); block = 256.
+template <class R>
+__global__ void k_upsample_map(const InstDesc<R>* __restrict__ dp, cx<R>* __restrict__ out,
+                               int nx, int ny) {
+    const InstDesc<R>& d = *dp;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y, l = blockIdx.z;
+    if (x >= nx) return;
+    const MapView<R> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
+    TempSampler<R> ts;
+    make_sampler(d, mv, x, row_cell(d, y), ts);
+    out[(size_t(l) * ny + y) * nx + x] = ts.bil(l);
 }
 
 }  // namespace shg

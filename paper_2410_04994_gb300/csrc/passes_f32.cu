@@ -11,21 +11,29 @@ namespace shg {
 
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
-cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
-                    const void* tw, int hx, cudaStream_t st) {
+// v: FFT shape (0 or 1), plus kRowUmap to read the per-point temperature table.
+template <bool UM>
+static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
+                              const void* tw, int hx, cudaStream_t st) {
     if (v == 1) {
         switch (nx) {
-#define X(n) case n: return row_launch<float, n, 1>(descs, ninst, ny, nz, s, tw, hx, st);
+#define X(n) case n: return row_launch<float, n, 1, UM>(descs, ninst, ny, nz, s, tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
     }
     switch (nx) {
-#define X(n) case n: return row_launch<float, n>(descs, ninst, ny, nz, s, tw, hx, st);
+#define X(n) case n: return row_launch<float, n, 0, UM>(descs, ninst, ny, nz, s, tw, hx, st);
         SHG_F32_SIZES(X)
 #undef X
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
+                    const void* tw, int hx, cudaStream_t st) {
+    return (v & kRowUmap) ? row_f32_um<true>(nx, v & ~kRowUmap, descs, ninst, ny, nz, s, tw, hx, st)
+                          : row_f32_um<false>(nx, v, descs, ninst, ny, nz, s, tw, hx, st);
 }
 
 // Column tile width of the TMA-staged column pass for length ny (0: none).
@@ -62,15 +70,26 @@ cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const v
     return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, int tz,
+                                cudaStream_t st) {
+    if (tz > 65535) return cudaErrorInvalidValue;
+    dim3 grid((nx + 255) / 256, ny, tz);
+    k_upsample_map<float><<<grid, 256, 0, st>>>(static_cast<const InstDesc<float>*>(desc),
+                                                static_cast<cx<float>*>(umap), nx, ny);
+    return cudaGetLastError();
+}
+
 cudaError_t attr_f32() {
     cudaError_t e = cudaSuccess;
-#define X(n)                                        \
-    if (e == cudaSuccess) e = row_attr<float, n>(); \
+#define X(n)                                                    \
+    if (e == cudaSuccess) e = row_attr<float, n>();             \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true>();    \
     if (e == cudaSuccess) e = col_attr<float, n>();
     SHG_F32_SIZES(X)
 #undef X
-#define X(n)                                           \
-    if (e == cudaSuccess) e = row_attr<float, n, 1>(); \
+#define X(n)                                                    \
+    if (e == cudaSuccess) e = row_attr<float, n, 1>();          \
+    if (e == cudaSuccess) e = row_attr<float, n, 1, true>();    \
     if (e == cudaSuccess) e = col_attr<float, n, 1>();
     SHG_F32_VARIANT_SIZES(X)
 #undef X
@@ -82,15 +101,17 @@ cudaError_t attr_f32() {
 }
 
 size_t row_smem_f32(int nx, int v, int hx) {
+    const size_t slots = (v & kRowUmap) ? slot_bytes<float>() : 0;
+    v &= ~kRowUmap;
     if (v == 1) {
         switch (nx) {
-#define X(n) case n: return row_smem<float, n, 1>(hx);
+#define X(n) case n: return row_smem<float, n, 1>(hx) + slots;
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
     }
     switch (nx) {
-#define X(n) case n: return row_smem<float, n>(hx);
+#define X(n) case n: return row_smem<float, n>(hx) + slots;
         SHG_F32_SIZES(X)
 #undef X
     }

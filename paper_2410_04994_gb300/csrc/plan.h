@@ -52,6 +52,8 @@ struct shg_plan {
     void* eph = nullptr;      // [4 nz + 1]
     void* tw = nullptr;       // [1024]
     void* ttab = nullptr;     // [tz][ty][tx] (dT, C) in the plan's precision
+    void* umap = nullptr;     // FP32: [tz][ny][nx] (dT, C) at every field point, or nullptr
+    size_t umap_bytes = 0;
     float* tmap = nullptr;    // [tz][ty][tx] dT as set
     int tx = 0, ty = 0, tz = 0;
     double tlx = 0, tly = 0;
@@ -122,7 +124,11 @@ bool has_fft_variant(bool fp64, int n);
 // SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.
 int fft_variant(bool fp64, int n, int pass);
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st, const void* tmaps);
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits);
+// kRowUmap if the row passes of these plans (one grid) read the per-point
+// temperature table: every plan with a map keeps one, and one z-step spans
+// less than one map layer (so a pass touches at most three layers); else 0.
+int row_umap_bit(const std::vector<shg_plan*>& plans);
 cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
                         const void* descs, int nx, int ny, cudaStream_t st);
 cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
@@ -130,6 +136,10 @@ cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, i
 cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
                               double dZ, cudaStream_t st);
 cudaError_t setup_pass_attributes();
+// Fill the per-point temperature table of an FP32 plan from its uploaded
+// descriptor (node table, map geometry): tz layers of ny x nx (dT, C).
+cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, int tz,
+                                cudaStream_t st);
 
 // Enqueue the whole forward propagation of instances sharing one grid.
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
