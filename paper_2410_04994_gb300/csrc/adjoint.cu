@@ -304,7 +304,8 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
             if (s + 1 < se) {
                 // the same FFT shapes as the forward sweep, to replay its states
                 SHG_CK(launch_row(p->fp64, nx, a->descW, 1, ny, nz, s, p->tw, 0, st,
-                                  fft_variant(p->fp64, nx, 0) | row_umap_bit({p})));
+                                  fft_variant(p->fp64, nx, 0, row_umap_bit({p})) |
+                                      row_umap_bit({p})));
                 if (s < nz)
                     SHG_CK(launch_col(p->fp64, ny, a->descW, 1, nx, p->tw, st,
                                       fft_variant(p->fp64, ny, 1)));

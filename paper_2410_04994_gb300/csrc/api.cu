@@ -341,7 +341,7 @@ static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     return c;
 }
 
-int fft_variant(bool fp64, int n, int pass) {
+int fft_variant(bool fp64, int n, int pass, int row_bits) {
     const int f = forced_variant();
     if (f >= 0) {
         if (f == 1 && !has_fft_variant(fp64, n)) return 0;
@@ -349,14 +349,16 @@ int fft_variant(bool fp64, int n, int pass) {
         return f;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    auto it = g_tuned.find(std::make_tuple(fp64, n, pass));
+    auto it = g_tuned.find(std::make_tuple(fp64, n, pass + (row_bits ? 2 : 0)));
     return it == g_tuned.end() ? 0 : it->second;
 }
 
-// Time every candidate flavour of each pass of this group on its own data
-// (one warm-up and three launches each, CUDA events on `st`) and keep the
-// fastest for the rest of the process.  The group's fields are modified;
-// every propagation re-initialises them first.
+// Time every candidate flavour of each pass of this group on its own data and
+// keep the fastest for the rest of the process.  After one warm-up launch
+// each, the candidates take turns for three rounds of two launches (CUDA
+// events on `st`), so that none profits from caches the others warmed; a
+// candidate's time is its best round.  The group's fields are modified; every
+// propagation re-initialises them first.
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
                         const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits) {
     if (forced_variant() >= 0) return SHG_OK;
@@ -366,35 +368,47 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         if (cand.size() < 2) continue;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
-            if (g_tuned.count(std::make_tuple(fp64, n, pass))) continue;
+            if (g_tuned.count(std::make_tuple(fp64, n, pass + (pass == 0 && row_bits ? 2 : 0))))
+                continue;
         }
         cudaEvent_t e0, e1;
         SHG_CK(cudaEventCreate(&e0));
         SHG_CK(cudaEventCreate(&e1));
         const int s = nz > 1 ? 1 : 0;
-        int best_v = 0;
-        float best_t = 1e30f;
+        auto launch = [&](int v) {
+            return pass == 0 ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v | row_bits)
+                             : launch_col(fp64, ny, descs, ninst, nx, tw, st, v, tmaps);
+        };
+        std::vector<float> best(cand.size(), 1e30f);
         for (int v : cand) {
-            for (int rep = 0; rep < 4; ++rep) {
-                if (rep == 1) SHG_CK(cudaEventRecord(e0, st));
-                const cudaError_t e = pass == 0
-                    ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v | row_bits)
-                    : launch_col(fp64, ny, descs, ninst, nx, tw, st, v, tmaps);
-                if (e != cudaSuccess) return cuda_fail(e, "tune_group");
-            }
-            SHG_CK(cudaEventRecord(e1, st));
-            SHG_CK(cudaEventSynchronize(e1));
-            float t = 0;
-            SHG_CK(cudaEventElapsedTime(&t, e0, e1));
-            if (t < best_t) {
-                best_t = t;
-                best_v = v;
+            const cudaError_t e = launch(v);
+            if (e != cudaSuccess) return cuda_fail(e, "tune_group");
+        }
+        for (int round = 0; round < 3; ++round) {
+            for (size_t c = 0; c < cand.size(); ++c) {
+                SHG_CK(cudaEventRecord(e0, st));
+                for (int rep = 0; rep < 2; ++rep) {
+                    const cudaError_t e = launch(cand[c]);
+                    if (e != cudaSuccess) return cuda_fail(e, "tune_group");
+                }
+                SHG_CK(cudaEventRecord(e1, st));
+                SHG_CK(cudaEventSynchronize(e1));
+                float t = 0;
+                SHG_CK(cudaEventElapsedTime(&t, e0, e1));
+                best[c] = std::min(best[c], t);
             }
         }
+        int best_v = cand[0];
+        float best_t = best[0];
+        for (size_t c = 1; c < cand.size(); ++c)
+            if (best[c] < best_t) {
+                best_t = best[c];
+                best_v = cand[c];
+            }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[std::make_tuple(fp64, n, pass)] = best_v;
+        g_tuned[std::make_tuple(fp64, n, pass + (pass == 0 && row_bits ? 2 : 0))] = best_v;
     }
     return SHG_OK;
 }
@@ -420,7 +434,8 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     int hx = 0;
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
-    const int vr = fft_variant(fp64, nx, 0) | row_umap_bit(plans), vc = fft_variant(fp64, ny, 1);
+    const int rb = row_umap_bit(plans);
+    const int vr = fft_variant(fp64, nx, 0, rb) | rb, vc = fft_variant(fp64, ny, 1);
     for (int s = 0; s <= nz; ++s) {
         for (shg_plan* p : plans) {
             shg_status_t r = adjoint_checkpoint(p, s, st);
@@ -1063,7 +1078,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             }
             e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
                            g.plans[0]->tw, hx, st,
-                           fft_variant(g.fp64, g.nx, 0) | row_umap_bit(g.plans));
+                           fft_variant(g.fp64, g.nx, 0, row_umap_bit(g.plans)) |
+                               row_umap_bit(g.plans));
             cudaEventRecord(E[1], st);
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);

@@ -200,4 +200,108 @@ SHG_D void rk4(const InstDesc<R>& d, cx<R>& aF, cx<R>& aS, const Coef<R>& c0,
     aS.x += h6 * accSr; aS.y += h6 * accSi;
 }
 
+// ---------------------------------------------------------------------------
+// Two points at once (FP32).  Two FP32 values share one 64-bit register and are
+// operated on by the packed add/sub/mul/fma.f32x2 instructions of sm_100 and
+// later: one instruction advances both points of a pair, and each lane is
+// rounded exactly as the scalar instruction would round it.
+struct f32x2 {
+    unsigned long long v;
+};
+SHG_D f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+SHG_D void up2(f32x2 x, float& a, float& b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x.v)); }
+SHG_D f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+SHG_D f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+SHG_D f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+SHG_D f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {  // a * b + c
+    f32x2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+
+// Stage coefficients of a pair of points.
+struct Coef2 {
+    f32x2 er, ei, pF, pS;
+};
+SHG_D Coef2 pack2(const Coef<float>& a, const Coef<float>& b) {
+    return {pk2(a.er, b.er), pk2(a.ei, b.ei), pk2(a.pF, b.pF), pk2(a.pS, b.pS)};
+}
+
+// One complex field of a pair of points: (re, im) of each, lane-wise.
+struct Cx2 {
+    f32x2 r, i;
+};
+
+// The right-hand side of both equations for a pair of points, written as
+//   f_F  = (g_F + i psi_F) A_F  + i kF (A_SH conj(A_F)) e^{-i phi},  g_F  = -bF |A_F|^2
+//   f_SH = (g_S + i psi_SH) A_SH + i kS A_F^2 e^{+i phi},            g_S = -bS |A_SH|^2
+SHG_D void rhs2(const InstDesc<float>& d, const Coef2& k, const Cx2& aF, const Cx2& aS, Cx2& fF,
+                Cx2& fS) {
+    const f32x2 rr = mul2(aF.r, aF.r), ii = mul2(aF.i, aF.i);
+    const f32x2 gF = mul2(pk2(-d.bF, -d.bF), add2(rr, ii));
+    const f32x2 gS = mul2(pk2(-d.bS, -d.bS), fma2(aS.r, aS.r, mul2(aS.i, aS.i)));
+    fF.r = sub2(mul2(gF, aF.r), mul2(k.pF, aF.i));
+    fF.i = fma2(gF, aF.i, mul2(k.pF, aF.r));
+    fS.r = sub2(mul2(gS, aS.r), mul2(k.pS, aS.i));
+    fS.i = fma2(gS, aS.i, mul2(k.pS, aS.r));
+    if (!d.undepleted) {
+        const f32x2 tr = fma2(aS.r, aF.r, mul2(aS.i, aF.i));  // A_SH conj(A_F)
+        const f32x2 ti = sub2(mul2(aS.i, aF.r), mul2(aS.r, aF.i));
+        const f32x2 ur = fma2(tr, k.er, mul2(ti, k.ei));      // * e^{-i phi}
+        const f32x2 ui = sub2(mul2(ti, k.er), mul2(tr, k.ei));
+        fF.r = fma2(pk2(-d.kF, -d.kF), ui, fF.r);
+        fF.i = fma2(pk2(d.kF, d.kF), ur, fF.i);
+    }
+    const f32x2 vr = sub2(rr, ii);                             // A_F^2
+    const f32x2 vi = mul2(add2(aF.r, aF.r), aF.i);
+    const f32x2 wr = sub2(mul2(vr, k.er), mul2(vi, k.ei));     // * e^{+i phi}
+    const f32x2 wi = fma2(vr, k.ei, mul2(vi, k.er));
+    fS.r = fma2(pk2(-d.kS, -d.kS), wi, fS.r);
+    fS.i = fma2(pk2(d.kS, d.kS), wr, fS.i);
+}
+
+// One RK4 step of size h for a pair of points (the stages of rk4 above).
+SHG_D void rk4_2(const InstDesc<float>& d, Cx2& aF, Cx2& aS, const Coef2& c0, const Coef2& cm,
+                 const Coef2& c1, float h) {
+    const f32x2 hh = pk2(0.5f * h, 0.5f * h), hf = pk2(h, h), two = pk2(2.f, 2.f);
+    Cx2 kF, kS, yF, yS;
+    rhs2(d, c0, aF, aS, kF, kS);
+    Cx2 accF = kF, accS = kS;
+    yF = {fma2(hh, kF.r, aF.r), fma2(hh, kF.i, aF.i)};
+    yS = {fma2(hh, kS.r, aS.r), fma2(hh, kS.i, aS.i)};
+    rhs2(d, cm, yF, yS, kF, kS);
+    accF = {fma2(two, kF.r, accF.r), fma2(two, kF.i, accF.i)};
+    accS = {fma2(two, kS.r, accS.r), fma2(two, kS.i, accS.i)};
+    yF = {fma2(hh, kF.r, aF.r), fma2(hh, kF.i, aF.i)};
+    yS = {fma2(hh, kS.r, aS.r), fma2(hh, kS.i, aS.i)};
+    rhs2(d, cm, yF, yS, kF, kS);
+    accF = {fma2(two, kF.r, accF.r), fma2(two, kF.i, accF.i)};
+    accS = {fma2(two, kS.r, accS.r), fma2(two, kS.i, accS.i)};
+    yF = {fma2(hf, kF.r, aF.r), fma2(hf, kF.i, aF.i)};
+    yS = {fma2(hf, kS.r, aS.r), fma2(hf, kS.i, aS.i)};
+    rhs2(d, c1, yF, yS, kF, kS);
+    accF = {add2(kF.r, accF.r), add2(kF.i, accF.i)};
+    accS = {add2(kS.r, accS.r), add2(kS.i, accS.i)};
+    const float h6s = h * (1.f / 6.f);
+    const f32x2 h6 = pk2(h6s, h6s);
+    aF = {fma2(h6, accF.r, aF.r), fma2(h6, accF.i, aF.i)};
+    aS = {fma2(h6, accS.r, aS.r), fma2(h6, accS.i, aS.i)};
+}
+
 }  // namespace shg

@@ -183,6 +183,16 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     const int j_dep = (dep && active) ? d.hiy[y] : -1;
     const R w_dep = dep ? d.dxdy * d.dz * ((s == 0 || s == nz) ? R(0.5) : R(1)) : R(0);
     const RowCell<R> rc = thermal ? row_cell(d, y) : RowCell<R>{0, R(0)};
+    // Heat deposit of one point at z_s.
+    auto deposit = [&](int xi, const C& aF, const C& aS) {
+        const int i = __ldg(&d.hix[xi]);
+        if (i >= 0) {
+            const R aF2 = aF.x * aF.x + aF.y * aF.y;
+            const R aS2 = aS.x * aS.x + aS.y * aS.y;
+            const R q = aF2 * (d.qaF + d.qbF * aF2) + aS2 * (d.qaS + d.qbS * aS2);
+            atomicAdd(&bins[lr * d.hx + i], float(q * w_dep));
+        }
+    };
     // One point: N_b(s-1) [z_s - dz/2 -> z_s], deposit at z_s, N_a(s).
     auto point = [&](int xi, C& aF, C& aS, auto& ts) {
         const Coef<R> cz = coef_at(d, zsh[2], thermal, ts);  // z_s, shared by both halves
@@ -191,23 +201,47 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
             const Coef<R> cm = coef_at(d, zsh[1], thermal, ts);
             rk4(d, aF, aS, c0, cm, cz, h);
         }
-        if (l_dep >= 0 && j_dep >= 0) {
-            const int i = __ldg(&d.hix[xi]);
-            if (i >= 0) {
-                const R aF2 = aF.x * aF.x + aF.y * aF.y;
-                const R aS2 = aS.x * aS.x + aS.y * aS.y;
-                const R q = aF2 * (d.qaF + d.qbF * aF2) + aS2 * (d.qaS + d.qbS * aS2);
-                atomicAdd(&bins[lr * d.hx + i], float(q * w_dep));
-            }
-        }
+        if (l_dep >= 0 && j_dep >= 0) deposit(xi, aF, aS);
         if (s < nz) {
             const Coef<R> cm = coef_at(d, zsh[3], thermal, ts);
             const Coef<R> c1 = coef_at(d, zsh[4], thermal, ts);
             rk4(d, aF, aS, cz, cm, c1, h);
         }
     };
+    // The same for two points at once in packed FP32 arithmetic (the body
+    // exists for FP32 only).
+    auto pair = [&](int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1, auto& sa, auto& sb) {
+        if constexpr (sizeof(R) == 4) {
+            const Coef<R> za = coef_at(d, zsh[2], thermal, sa);
+            const Coef<R> zb = coef_at(d, zsh[2], thermal, sb);
+            Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, S{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
+            if (s > 0) {
+                const Coef2 c0 = pack2(coef_at(d, zsh[0], thermal, sa), coef_at(d, zsh[0], thermal, sb));
+                const Coef2 cm = pack2(coef_at(d, zsh[1], thermal, sa), coef_at(d, zsh[1], thermal, sb));
+                rk4_2(dsh, F, S, c0, cm, pack2(za, zb), h);
+            }
+            if (l_dep >= 0 && j_dep >= 0) {
+                up2(F.r, aF0.x, aF1.x);
+                up2(F.i, aF0.y, aF1.y);
+                up2(S.r, aS0.x, aS1.x);
+                up2(S.i, aS0.y, aS1.y);
+                deposit(xa, aF0, aS0);
+                deposit(xb, aF1, aS1);
+            }
+            if (s < nz) {
+                const Coef2 cm = pack2(coef_at(d, zsh[3], thermal, sa), coef_at(d, zsh[3], thermal, sb));
+                const Coef2 c1 = pack2(coef_at(d, zsh[4], thermal, sa), coef_at(d, zsh[4], thermal, sb));
+                rk4_2(dsh, F, S, pack2(za, zb), cm, c1, h);
+            }
+            up2(F.r, aF0.x, aF1.x);
+            up2(F.i, aF0.y, aF1.y);
+            up2(S.r, aS0.x, aS1.x);
+            up2(S.i, aS0.y, aS1.y);
+        }
+    };
     if (active) {
-        // two independent points per iteration give the scheduler two RK4
+        // two independent points per iteration: in FP32 they advance together
+        // in packed arithmetic; in FP64 they give the scheduler two RK4
         // dependency chains to interleave
 #pragma unroll 1
         for (int m = 0; m < E; m += 2) {
@@ -228,8 +262,14 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
                 const C* b0 = slots + (buf * kSlotLayers * 2) * kPassThreads + threadIdx.x;
                 SlotSampler<R> s0{b0, 2 * kPassThreads, lmin};
                 SlotSampler<R> s1{b0 + kPassThreads, 2 * kPassThreads, lmin};
-                point(x0, aF0, aS0, s0);
-                point(x1, aF1, aS1, s1);
+                pair(x0, x1, aF0, aS0, aF1, aS1, s0, s1);
+            } else if constexpr (sizeof(R) == 4) {
+                TempSampler<R> s0, s1;
+                if (thermal) {
+                    make_sampler(d, mv, x0, rc, s0);
+                    make_sampler(d, mv, x1, rc, s1);
+                }
+                pair(x0, x1, aF0, aS0, aF1, aS1, s0, s1);
             } else {
                 {
                     TempSampler<R> s0;

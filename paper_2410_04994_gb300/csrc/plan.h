@@ -119,10 +119,10 @@ cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, 
                        cudaStream_t st, int variant = 0, const void* tmaps = nullptr);
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
-// Kernel flavour picked for (precision, length, pass) by the autotuner:
+// Kernel flavour picked for (precision, length, pass, row-pass table bit) by the autotuner:
 // measured once per process on the first group that uses it, unless
 // SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.
-int fft_variant(bool fp64, int n, int pass);
+int fft_variant(bool fp64, int n, int pass, int row_bits = 0);
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
                         const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits);
 // kRowUmap if the row passes of these plans (one grid) read the per-point
