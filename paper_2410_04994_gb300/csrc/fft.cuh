@@ -157,8 +157,20 @@ template <int R, int DIR, class C> SHG_D void dft_reg(C (&u)[R]) {
     for (int k = 0; k < R; ++k) u[k] = o[k];
 }
 
+// Where the constant tables of a transform live.  TL = 0: the plan's tables
+// in global memory, twiddles W_1024^k (read through the read-only cache).
+// TL = N > 0: copies in shared memory, twiddles W_N^k, k < N (so that
+// streamed tiles cannot evict them from L1).
+template <int TL> constexpr int tab_len() { return TL == 0 ? 1024 : TL; }
+template <int TL, class P> SHG_D P ld_tab(const P* p) {
+    if constexpr (TL == 0)
+        return __ldg(p);
+    else
+        return *p;
+}
+
 // One Stockham stage on the thread's E registers.
-template <int N, int E, int T, int R, int NS, bool LAST, int DIR, class C>
+template <int N, int E, int T, int R, int NS, bool LAST, int DIR, int TL, class C>
 SHG_D void stage(C (&v)[E], C* sm, int t, const pt<decltype(C::x)>* __restrict__ tw) {
     using RT = decltype(C::x);
     constexpr int B = E / R;
@@ -172,7 +184,7 @@ SHG_D void stage(C (&v)[E], C* sm, int t, const pt<decltype(C::x)>* __restrict__
         if (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const auto w = __ldg(&tw[jm * r * (1024 / (NS * R))]);
+                const auto w = ld_tab<TL>(&tw[jm * r * (tab_len<TL>() / (NS * R))]);
                 u[r] = DIR < 0 ? pmul(u[r], w) : pmulc(u[r], w);
                 // bound the number of (hi, lo) twiddles the compiler keeps in
                 // flight: without this it hoists them all and spills
@@ -200,30 +212,30 @@ template <int E, int T, class C> SHG_D void reload(C (&v)[E], const C* sm, int t
 // Forward (DIR = -1) or inverse (DIR = +1, unnormalised) transform of one
 // sequence held as E registers per thread.  Every thread of the block must
 // call this (it contains __syncthreads).
-template <class RT, int N, int V, int DIR, class C>
+template <class RT, int N, int V, int DIR, int TL = 0, class C>
 SHG_D void fft1(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
     using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
     constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2, R3 = F::R3;
     constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2), L2 = (F::NST == 3);
-    stage<N, E, T, R0, 1, L0, DIR>(a, sa, t, tw);
+    stage<N, E, T, R0, 1, L0, DIR, TL>(a, sa, t, tw);
     if constexpr (F::NST >= 2) {
         __syncthreads();
         reload<E, T>(a, sa, t);
         __syncthreads();
-        stage<N, E, T, (R1 > 1 ? R1 : 2), R0, L1, DIR>(a, sa, t, tw);
+        stage<N, E, T, (R1 > 1 ? R1 : 2), R0, L1, DIR, TL>(a, sa, t, tw);
     }
     if constexpr (F::NST >= 3) {
         __syncthreads();
         reload<E, T>(a, sa, t);
         __syncthreads();
-        stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, L2, DIR>(a, sa, t, tw);
+        stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, L2, DIR, TL>(a, sa, t, tw);
     }
     if constexpr (F::NST >= 4) {
         __syncthreads();
         reload<E, T>(a, sa, t);
         __syncthreads();
-        stage<N, E, T, (R3 > 1 ? R3 : 2), R0 * R1 * R2, true, DIR>(a, sa, t, tw);
+        stage<N, E, T, (R3 > 1 ? R3 : 2), R0 * R1 * R2, true, DIR, TL>(a, sa, t, tw);
     }
 }
 
@@ -231,16 +243,30 @@ SHG_D void fft1(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restr
 // linear operator F^{-1} diag(p) F along the thread group's axis.  The 1/N of
 // the inverse is folded into the factor table.  No barrier is needed between
 // the two transforms: every thread has passed the barrier that follows the
-// forward transform's last reload before any inverse store happens.
-template <class RT, int N, int V = 0, class C>
+// forward transform's last reload before any inverse store happens.  With
+// TL = N the twiddles (W_N^k) and the factors p are read from shared memory.
+template <class RT, int N, int V = 0, int TL = 0, class C>
 SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw,
                         const pt<RT>* __restrict__ p) {
     using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
-    fft1<RT, N, V, -1>(a, sa, t, tw);
+    fft1<RT, N, V, -1, TL>(a, sa, t, tw);
 #pragma unroll
-    for (int m = 0; m < E; ++m) a[m] = pmul(a[m], __ldg(&p[t + T * m]));
-    fft1<RT, N, V, +1>(a, sa, t, tw);
+    for (int m = 0; m < E; ++m) a[m] = pmul(a[m], ld_tab<TL>(&p[t + T * m]));
+    fft1<RT, N, V, +1, TL>(a, sa, t, tw);
+}
+
+// Copy the twiddles W_N^k (every (1024/N)-th entry of the plan's table) and
+// the 2N factors of both fields into shared memory (cp.async, 16 B each; the
+// caller commits and waits, then synchronises the block).
+template <class RT, int N>
+SHG_D void stage_tables(pt<RT>* twS, pt<RT>* pS, const pt<RT>* tw, const pt<RT>* p) {
+    for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) {
+        if (k < N)
+            cp_async(&twS[k], &tw[k * (1024 / N)]);
+        else
+            cp_async(&pS[k - N], &p[k - N]);
+    }
 }
 
 }  // namespace shg

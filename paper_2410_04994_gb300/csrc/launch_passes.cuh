@@ -26,7 +26,7 @@ template <class R, int N, int V = 0, bool UM = false> cudaError_t row_attr() {
 // Dynamic shared memory of a row pass: transform buffers + table prefetch
 // slots (UM) + deposit bins.
 template <class R, int N, int V = 0, bool UM = false> size_t row_smem(int hx) {
-    return RowGeom<R, N, V>::fields + (UM ? slot_bytes<R>() : 0) +
+    return RowGeom<R, N, V>::fields + (UM ? slot_bytes<R>() : 0) + RowGeom<R, N, V>::tables +
            size_t(RowGeom<R, N, V>::ROWS) * hx * sizeof(float);
 }
 template <class R, int N, int V = 0> cudaError_t col_attr() {

@@ -38,6 +38,7 @@ template <class R, int N, int V = 0> struct RowGeom {
     static constexpr int ROWS = kPassThreads / T;
     static constexpr int S = padded_len<R>(N, T < Bank<R>::W ? T : 1);
     static constexpr size_t fields = size_t(2) * ROWS * S * sizeof(cx<R>);
+    static constexpr size_t tables = size_t(3) * N * sizeof(pt<R>);  // twiddles + 2 factor rows
 };
 
 
@@ -46,7 +47,8 @@ template <class R, int N, int V = 0> struct ColGeom {
     static constexpr int T = F::T;
     static constexpr int TILE = kPassThreads / T;
     static constexpr int S = padded_len<R>(N, TILE < Bank<R>::W ? Bank<R>::W / TILE : 1);
-    static constexpr size_t smem = size_t(2) * TILE * S * sizeof(cx<R>);
+    static constexpr size_t fields = size_t(2) * TILE * S * sizeof(cx<R>);
+    static constexpr size_t smem = fields + size_t(3) * N * sizeof(pt<R>);  // + twiddles, factors
 };
 
 // Where the row pass reads the temperature map from ([tz][ty][tx] storage with
@@ -132,6 +134,9 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     const bool active = y < ny;
     C* sF = smem + lr * S;
     C* sS = smem + (ROWS + lr) * S;
+    // shared copies of the twiddles and of the row factors of both fields
+    pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields + (UM ? slot_bytes<R>() : 0));
+    pt<R>* pS = twS + NX;
     {
         const InstDesc<R>& dg = descs[blockIdx.y];
         C* rowF = dg.field + size_t(y) * NX;
@@ -143,6 +148,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
                 cp_async(&sS[pidx<R>(t + T * m)], &rowS[t + T * m]);
             }
         }
+        stage_tables<R, NX>(twS, pS, tw, dg.px);
         if (threadIdx.x == 0) dsh = dg;
         if (threadIdx.x < 5) {
             const int q = 4 * s - 2 + threadIdx.x;
@@ -151,7 +157,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     }
     const bool dep = descs[blockIdx.y].Q != nullptr;
     C* slots = reinterpret_cast<C*>(smem_raw + G::fields);
-    float* bins = reinterpret_cast<float*>(smem_raw + G::fields + (UM ? slot_bytes<R>() : 0));
+    float* bins = reinterpret_cast<float*>(pS + 2 * NX);
     const int nb = dep ? ROWS * descs[blockIdx.y].hx : 0;
     for (int i = threadIdx.x; i < nb; i += kPassThreads) bins[i] = 0.f;
     __syncthreads();
@@ -310,7 +316,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         if (s < nz) {
             __syncthreads();  // the transform's first stores reuse the staging buffer
-            fft_mul_ifft<R, NX, V>(v, sb, t, tw, d.px + f * NX);
+            fft_mul_ifft<R, NX, V, NX>(v, sb, t, twS, pS + f * NX);
         }
         if (active) {
 #pragma unroll
@@ -321,7 +327,9 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
 
 // Column pass C(s).  grid = (ceil(nx / TILE), instances); block = 256.
 // The TILE columns of both fields are staged into padded shared buffers with
-// cp.async, transformed field by field, and written back from registers.
+// cp.async, one commit group per field, transformed field by field (the
+// second field is still landing while the first is transformed), and written
+// back from registers.
 template <class R, int NY, int V = 0>
 __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     k_col_pass(const InstDesc<R>* __restrict__ descs, int nx, const pt<R>* __restrict__ tw) {
@@ -330,30 +338,36 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     constexpr int E = FftCfg<R, NY, V>::E, T = G::T, TILE = G::TILE, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
+    pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields);
+    pt<R>* pS = twS + NY;
     C* field = descs[blockIdx.y].field;
-    const pt<R>* py = descs[blockIdx.y].py;
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = blockIdx.x * TILE + c;
     const bool active = x < nx;
-    if (active) {
 #pragma unroll
-        for (int f = 0; f < 2; ++f) {
+    for (int f = 0; f < 2; ++f) {
+        if (active) {
             const C* col = field + size_t(f) * NY * nx + x;
             C* sb = smem + (f * TILE + c) * S;
 #pragma unroll
             for (int m = 0; m < E; ++m)
                 cp_async(&sb[pidx<R>(t + T * m)], col + size_t(t + T * m) * nx);
         }
+        if (f == 0) stage_tables<R, NY>(twS, pS, tw, descs[blockIdx.y].py);
+        cp_async_commit();
     }
-    cp_async_wait_all();
 #pragma unroll 1
     for (int f = 0; f < 2; ++f) {
+        if (f == 0)
+            cp_async_wait_group<1>();
+        else
+            cp_async_wait_group<0>();
         C* sb = smem + (f * TILE + c) * S;
         C v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         __syncthreads();  // all staged values read before the transform's stores
-        fft_mul_ifft<R, NY, V>(v, sb, t, tw, py + f * NY);
+        fft_mul_ifft<R, NY, V, NY>(v, sb, t, twS, pS + f * NY);
         if (active) {
             C* col = field + size_t(f) * NY * nx + x;
 #pragma unroll
@@ -373,7 +387,8 @@ template <int NY> struct ColTma {
     using G = ColGeom<float, NY, 0>;
     static constexpr int TILE = G::TILE, S = G::S, BY = NY < 256 ? NY : 256;
     static constexpr size_t stage_bytes = size_t(2) * NY * TILE * sizeof(float2);
-    static constexpr size_t smem = 128 + stage_bytes + size_t(TILE) * S * sizeof(float2) + 16;
+    static constexpr size_t tables = size_t(3) * NY * sizeof(float4);
+    static constexpr size_t smem = 128 + stage_bytes + size_t(TILE) * S * sizeof(float2) + tables + 16;
 };
 
 constexpr unsigned kTmaMaxPolls = 1u << 20;
@@ -389,7 +404,9 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     float2* stage = reinterpret_cast<float2*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) &
                                               ~uintptr_t(127));
     float2* exch = stage + 2 * NY * TILE;
-    uint64_t* bar = reinterpret_cast<uint64_t*>(exch + TILE * S);
+    float4* twS = reinterpret_cast<float4*>(exch + TILE * S);
+    float4* pS = twS + NY;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(pS + 2 * NY);
     const InstDesc<float>& d = descs[blockIdx.y];
     const int x0 = blockIdx.x * TILE;
     if (threadIdx.x == 0) {
@@ -406,6 +423,8 @@ __global__ void __launch_bounds__(kPassThreads, 2)
             for (int yb = 0; yb < NY; yb += BY)
                 tma_load_3d(stage + (size_t(f) * NY + yb) * TILE, tm, x0, yb, f, bar);
     }
+    stage_tables<float, NY>(twS, pS, tw, d.py);
+    cp_async_wait_all();
     const bool ok = mbar_wait_bounded(bar, 0, d.wait_polls);
     if (__syncthreads_or(!ok)) {
         // Give up on this tile: report, then let the copies already issued
@@ -424,7 +443,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = stage[(size_t(f) * NY + t + T * m) * TILE + c];
-        fft_mul_ifft<float, NY, 0>(v, exch + c * S, t, tw, d.py + f * NY);
+        fft_mul_ifft<float, NY, 0, NY>(v, exch + c * S, t, twS, pS + f * NY);
         if (active) {
             float2* col = d.field + size_t(f) * NY * nx + x;
 #pragma unroll
