@@ -38,6 +38,32 @@ SHG_HD double2 pmul(double2 a, double2 p) {
 template <class C> SHG_HD C mk(decltype(C::x) a, decltype(C::x) b) { C c; c.x = a; c.y = b; return c; }
 template <class C> SHG_HD C cadd(C a, C b) { return mk<C>(a.x + b.x, a.y + b.y); }
 template <class C> SHG_HD C csub(C a, C b) { return mk<C>(a.x - b.x, a.y - b.y); }
+// Single precision: on the device both components in one packed f32x2
+// instruction (rounded exactly as the two scalar ones).
+template <> SHG_HD float2 cadd<float2>(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    float2 r;
+    asm("{\n .reg .b64 a, b, r;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+        " add.rn.f32x2 r, a, b;\n mov.b64 {%0, %1}, r;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+#else
+    return mk<float2>(a.x + b.x, a.y + b.y);
+#endif
+}
+template <> SHG_HD float2 csub<float2>(float2 a, float2 b) {
+#ifdef __CUDA_ARCH__
+    float2 r;
+    asm("{\n .reg .b64 a, b, r;\n mov.b64 a, {%2, %3};\n mov.b64 b, {%4, %5};\n"
+        " sub.rn.f32x2 r, a, b;\n mov.b64 {%0, %1}, r;\n}"
+        : "=f"(r.x), "=f"(r.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return r;
+#else
+    return mk<float2>(a.x - b.x, a.y - b.y);
+#endif
+}
 template <class C> SHG_HD C cmul(C a, C b) {
     return mk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
