@@ -84,6 +84,8 @@ class Params:
     ddk_dT: float = 0.0
     dn_dT: float = 0.0
     undepleted: bool = False
+    walkoff_f: float = 0.0      # spatial walk-off angles rho_j (rad) toward +x
+    walkoff_sh: float = 0.0
 
     @property
     def lambda_sh(self) -> float:
@@ -125,7 +127,8 @@ def params_from_workload(w) -> Params:
                   lambda_f=w.lambda_f, n_f=w.n_f, n_sh=w.n_sh, d_eff=w.d_eff,
                   alpha_f=w.alpha_f, alpha_sh=w.alpha_sh, beta_f=w.beta_f,
                   beta_sh=w.beta_sh, dk0=w.dk0, ddk_dT=w.ddk_dT, dn_dT=w.dn_dT,
-                  undepleted=bool(w.undepleted))
+                  undepleted=bool(w.undepleted), walkoff_f=getattr(w, "walkoff_f", 0.0),
+                  walkoff_sh=getattr(w, "walkoff_sh", 0.0))
 
 
 # ---------------------------------------------------------------- grid ----
@@ -286,7 +289,10 @@ class Nonlinear:
 # -------------------------------------------------------- linear step ----
 
 class Linear:
-    """exp(L dz) applied in K-space: diffraction (reading 1) and exp(-alpha dz/2)."""
+    """exp(L dz) applied in K-space: diffraction (reading 1), exp(-alpha dz/2)
+    and the walk-off term.  The walk-off term (Sec. 6, App. B) adds -tan(rho) dA/dx to
+    dA/dz, i.e. the factor exp(-i tan(rho) Kx dz): the field drifts toward +x
+    by tan(rho) per unit length."""
 
     def __init__(self, p: Params):
         Kx = wavenumbers(p.nx, p.lx)
@@ -295,6 +301,8 @@ class Linear:
         dz = p.dz
         self.PF = torch.exp(-1j * K2 * dz / (2.0 * p.k_f)) * math.exp(-0.5 * p.alpha_f * dz)
         self.PS = torch.exp(-1j * K2 * dz / (2.0 * p.k_sh)) * math.exp(-0.5 * p.alpha_sh * dz)
+        self.PF = self.PF * torch.exp(-1j * math.tan(p.walkoff_f) * Kx[None, :] * dz)
+        self.PS = self.PS * torch.exp(-1j * math.tan(p.walkoff_sh) * Kx[None, :] * dz)
 
     def __call__(self, AF, AS):
         AF = torch.fft.ifft2(self.PF * torch.fft.fft2(AF))

@@ -7,6 +7,8 @@ or a transposed operand fails at least one of them:
 * initial pump (Eq. 5/6)           -> analytic Gaussian, discrete power = P1
 * diffraction (App. A, reading 1)  -> analytic Gaussian beam at z, w(z) law
 * linear absorption in L           -> Beer-Lambert
+* walk-off term in L (Sec. 6)      -> exact integer-cell translation,
+                                      centroid drift tan(rho) z
 * coupling terms (Eq. 1/2, kappa)  -> plane-wave tanh^2 law, Manley-Rowe,
                                       Boyd-Kleinman h(sigma, xi)
 * phase sign and Dk (Eq. 3/4)      -> Boyd-Kleinman at sigma = +-0.57
@@ -127,6 +129,41 @@ def _uniform_run(w, AF0, AS0):
     p = _p(w)
     temp = ssfm.TemperatureField(p, None, 0, 0, w.t_off)
     return p, ssfm.propagate(p, AF0, AS0, temp)
+
+
+def test_walkoff_is_an_exact_translation():
+    """With tan(rho) dz equal to m grid cells, the walk-off factor is the
+    shift theorem for an m-cell translation toward +x: the step with walk-off
+    equals the step without it followed by a circular roll of m cells (SH
+    only, the pump untouched)."""
+    n, m = 32, 3
+    base = W.plain_focused(n=n, nz=50)
+    dx, dz = base.lx / n, base.L / base.nz
+    w = base.with_(walkoff_sh=math.atan(m * dx / dz))
+    rng = np.random.default_rng(5)
+    AF = torch.tensor(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    AS = torch.tensor(rng.normal(size=(n, n)) + 1j * rng.normal(size=(n, n)))
+    f1, s1 = ssfm.Linear(_p(w))(AF, AS)
+    f0, s0 = ssfm.Linear(_p(base))(AF, AS)
+    assert torch.max(torch.abs(f1 - f0)) < 1e-12
+    assert torch.max(torch.abs(s1 - torch.roll(s0, m, dims=1))) < 1e-11
+
+
+def test_walkoff_moves_the_beam_centroid_at_tan_rho():
+    """Linear propagation of the pump alone (no coupling, no losses) with a
+    walk-off angle: the centroid of |A_F|^2 moves along x by tan(rho) z, while
+    diffraction alone leaves it in place."""
+    rho = 1e-3  # a 2-cell drift over L, so that the beam stays clear of the window edge
+    w = W.plain_focused(n=64, nz=40).with_(d_eff=0.0, walkoff_f=rho)
+    p = _p(w)
+    AF0 = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus)
+    AF, _, _ = ssfm.run(w)
+    x = ssfm.axis(w.nx, w.lx)
+    def cx(a):
+        I = (a.abs() ** 2).sum(dim=0)
+        return float((I * x).sum() / I.sum())
+    assert abs(cx(AF0)) < 1e-12 * w.lx
+    assert abs(cx(AF) - math.tan(rho) * w.L) < 1e-8 * (w.lx / w.nx)
 
 
 def test_plane_wave_conversion_follows_tanh_squared():

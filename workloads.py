@@ -94,6 +94,8 @@ class Workload:
     kappa_th: float = KAPPA_TH
     wx: float = CRYSTAL_WX
     wy: float = CRYSTAL_WY
+    walkoff_f: float = 0.0      # walk-off angles (rad) toward +x
+    walkoff_sh: float = 0.0
     # beams
     p1: float = 1.0
     w0: float = 30e-6
