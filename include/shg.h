@@ -78,6 +78,11 @@ typedef struct {
     double alpha_f, alpha_sh, beta_f, beta_sh;
     double dk0, ddk_dT, dn_dT;
     double kappa_th, wx, wy;
+    /* Spatial walk-off angles rho (rad, |rho| < 1.5) of the fundamental and
+     * the SH toward +x (Sec. 6 and App. B: the tan(rho) dA/dx term of the propagator,
+     * for birefringently phase-matched crystals; 0 for the QPM examples):
+     * each step multiplies the field's spectrum by exp(-i tan(rho) Kx dz). */
+    double walkoff_f, walkoff_sh;
 } shg_crystal_t;
 
 /* Beams: pump power P1 (W), waist w0 (m), focus position z_focus (m from the
@@ -172,8 +177,10 @@ shg_status_t shg_batch_submit(shg_plan_t *const *plans, int n, double *eta_host_
  * the heat grid by red-black SOR (double precision, warm-started from the
  * previous solution) from the q_dot deposited by the last THERMAL
  * propagation, until the largest Jacobi correction is below tol (K) or
- * max_sweeps sweeps.  Installs dT as the plan's temperature map.
- * Returns the final correction and sweep count.  Synchronises `stream`. */
+ * max_sweeps sweeps.  The correction is checked every 8 sweeps, so up to 7
+ * sweeps may follow the first converged one.  Installs dT as the plan's
+ * temperature map.  Returns the final correction and sweep count.
+ * Synchronises `stream`. */
 shg_status_t shg_heat_solve(shg_plan_t *plan, int max_sweeps, double tol, double *resid,
                             int *sweeps, shg_stream_t stream);
 

@@ -41,7 +41,7 @@ class shg_grid_t(ctypes.Structure):
 class shg_crystal_t(ctypes.Structure):
     _fields_ = [(n, ctypes.c_double) for n in (
         "L", "lambda_f", "n_f", "n_sh", "d_eff", "alpha_f", "alpha_sh", "beta_f", "beta_sh",
-        "dk0", "ddk_dT", "dn_dT", "kappa_th", "wx", "wy")]
+        "dk0", "ddk_dT", "dn_dT", "kappa_th", "wx", "wy", "walkoff_f", "walkoff_sh")]
 
 
 class shg_beams_t(ctypes.Structure):
@@ -258,7 +258,8 @@ def structs_from(w, flags: int = 0):
     grid = shg_grid_t(w.nx, w.ny, w.nz, w.lx, w.ly, getattr(w, "hx", 0), getattr(w, "hy", 0),
                       getattr(w, "hz", 0))
     crystal = shg_crystal_t(w.L, w.lambda_f, w.n_f, w.n_sh, w.d_eff, w.alpha_f, w.alpha_sh,
-                            w.beta_f, w.beta_sh, w.dk0, w.ddk_dT, w.dn_dT, w.kappa_th, w.wx, w.wy)
+                            w.beta_f, w.beta_sh, w.dk0, w.ddk_dT, w.dn_dT, w.kappa_th, w.wx, w.wy,
+                            getattr(w, "walkoff_f", 0.0), getattr(w, "walkoff_sh", 0.0))
     beams = shg_beams_t(w.p1, w.w0, w.z_focus, w.t_off, 1 if w.undepleted else 0)
     return grid, crystal, beams
 

@@ -89,13 +89,15 @@ static shg_status_t upload(void* dst, const std::vector<unsigned char>& src) {
 static double k_f(const shg_plan* p) { return 2 * kPi * p->c.n_f / p->c.lambda_f; }
 static double k_sh(const shg_plan* p) { return 2 * kPi * p->c.n_sh / (0.5 * p->c.lambda_f); }
 
-// Row and column K-space factors, with the linear absorption and the 1/n of
-// the inverse transforms folded in (App. A, Eq. (A.4)-(A.5), reading 1).
+// Row and column K-space factors, with the linear absorption, the walk-off
+// phase exp(-i tan(rho_j) Kx dz) (row factor) and the 1/n of the inverse
+// transforms folded in (App. A, Eq. (A.4)-(A.5), reading 1).
 static shg_status_t build_prop_tables(shg_plan* p) {
     const int nx = p->g.nx, ny = p->g.ny;
     const double dz = p->c.L / p->g.nz;
     const double kj[2] = {k_f(p), k_sh(p)};
     const double al[2] = {p->c.alpha_f, p->c.alpha_sh};
+    const double tr[2] = {std::tan(p->c.walkoff_f), std::tan(p->c.walkoff_sh)};  // walk-off
     const size_t ps = prop_size(p);
     std::vector<unsigned char> hx(2 * nx * ps), hy(2 * ny * ps);
     std::vector<unsigned char> hxc(2 * nx * ps), hyc(2 * ny * ps);
@@ -103,7 +105,7 @@ static shg_status_t build_prop_tables(shg_plan* p) {
         const double att = std::exp(-0.5 * al[j] * dz);
         for (int k = 0; k < nx; ++k) {
             const double K = kvec(k, nx, p->g.lx);
-            const double ph = -K * K * dz / (2 * kj[j]);
+            const double ph = -K * K * dz / (2 * kj[j]) - tr[j] * K * dz;
             put_p(p, hx, j * nx + k, att * std::cos(ph) / nx, att * std::sin(ph) / nx);
             put_p(p, hxc, j * nx + k, att * std::cos(ph) / nx, -att * std::sin(ph) / nx);
         }
@@ -538,7 +540,8 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     if (!pow2_in(grid->nx, 8, hi) || !pow2_in(grid->ny, 8, hi)) return SHG_ERR_UNSUPPORTED_GRID;
     if (grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0)) return SHG_ERR_INVALID_ARG;
     if (!(crystal->L > 0) || !(crystal->lambda_f > 0) || !(crystal->n_f > 0) ||
-        !(crystal->n_sh > 0) || !(beams->w0 > 0) || !(beams->p1 >= 0))
+        !(crystal->n_sh > 0) || !(beams->w0 > 0) || !(beams->p1 >= 0) ||
+        !(std::fabs(crystal->walkoff_f) < 1.5) || !(std::fabs(crystal->walkoff_sh) < 1.5))
         return SHG_ERR_INVALID_ARG;
     if (flags & SHG_FLAG_THERMAL) {
         if (grid->hx < 3 || grid->hy < 3 || grid->hz < 3 || !(crystal->wx > 0) ||

@@ -141,3 +141,15 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     assert abs(eta / eta_ref - 1) < ETA_TOL
     with pytest.raises(pkg.ShgError):
         pkg.shg_set_wait_limit(None, 0)
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32"])
+def test_walkoff_of_both_waves(precision):
+    """Walk-off of both waves (opposite directions), with coupling, losses and
+    a seeded temperature map, against the oracle."""
+    w = W.depleted_absorbing(n=64, nz=40, tgrid=(9, 7, 5), p1=400.0).with_(
+        walkoff_f=2e-3, walkoff_sh=-5e-3, precision=precision)
+    if precision == "f64":
+        _compare(w, 1e-9, 1e-9)
+    else:
+        _compare(w, ETA_TOL, FIELD_TOL)
