@@ -15,7 +15,7 @@ static cudaError_t row_adj_launch(const void* dl, const void* Y, AdjAcc acc, int
         attr = true;
     }
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, 1);
-    k_row_adj<R, N><<<grid, kPassThreads, G::fields, st>>>(
+    k_row_adj<R, N><<<grid, kPassThreads, G::fields + G::tables, st>>>(
         static_cast<const InstDesc<R>*>(dl), static_cast<const cx<R>*>(Y), acc, ny, nz, s,
         static_cast<const pt<R>*>(tw));
     return cudaGetLastError();

@@ -24,6 +24,10 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     const bool active = y < ny;
     C* sF = smem + lr * S;
     C* sS = smem + (ROWS + lr) * S;
+    // shared copies of the twiddles and of the (conjugate) row factors
+    pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields);
+    pt<R>* pS = twS + NX;
+    stage_tables<R, NX>(twS, pS, tw, dl->px);
     if (active) {
         const C* rF = dl->field + size_t(y) * NX;
         const C* rS = dl->field + (size_t(ny) + y) * NX;
@@ -50,7 +54,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
             __syncthreads();
-            fft_mul_ifft<R, NX>(v, sb, t, tw, d.px + f * NX);
+            fft_mul_ifft<R, NX, 0, NX>(v, sb, t, twS, pS + f * NX);
             __syncthreads();
 #pragma unroll
             for (int m = 0; m < E; ++m) sb[pidx<R>(t + T * m)] = v[m];
