@@ -85,8 +85,9 @@ template <class R> struct InstDesc {
     const pt<R>* py;       // [2][ny] column factor exp(-i Ky^2 dz/2k_j) / ny
     const cx<R>* eph;      // [4 nz + 1] e^{i theta(q dz/4)}, theta = (dk0 + g T_off) z mod 2 pi
     const cx<R>* ttab;     // [tz][ty][tx] (dT, C) or nullptr for a uniform temperature
-    const cx<R>* umap;     // [tz][ny][nx] (dT, C) of every map layer bilinearly sampled at
-                           // every field point, or nullptr (sample ttab in the pass)
+    const cx<R>* umap;     // FP32: every map layer bilinearly sampled at every field
+                           // point, [tz][ny][nx/2] of (dT_2j, dT_2j+1, C_2j, C_2j+1),
+                           // or nullptr (sample ttab in the pass)
     int tx, ty, tz;
     R tx0, tdx_inv, ty0, tdy_inv, tdz_inv;  // node 0 position and 1/spacing of the map
     R x0, dx, y0, dy;      // field sample positions x_m = x0 + m dx
@@ -127,10 +128,14 @@ SHG_D uint64_t l2_evict_first_policy() {
     return pol;
 }
 template <class C> SHG_D void cp_async_stream(C* smem_dst, const C* gsrc, uint64_t pol) {
-    static_assert(sizeof(C) == 8, "8-byte elements");
+    static_assert(sizeof(C) == 8 || sizeof(C) == 16, "8- or 16-byte elements");
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
-    asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s),
-                 "l"(gsrc), "l"(pol));
+    if constexpr (sizeof(C) == 8)
+        asm volatile("cp.async.ca.shared.global.L2::cache_hint [%0], [%1], 8, %2;\n" ::"r"(s),
+                     "l"(gsrc), "l"(pol));
+    else
+        asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s),
+                     "l"(gsrc), "l"(pol));
 }
 SHG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> SHG_D void cp_async_wait_group() {

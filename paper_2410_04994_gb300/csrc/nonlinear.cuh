@@ -239,6 +239,41 @@ SHG_D f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {  // a * b + c
 struct Coef2 {
     f32x2 er, ei, pF, pS;
 };
+SHG_D f32x2 bc2(float a) { return pk2(a, a); }
+
+// The (dT, C) of a pair of adjacent points from per-thread slots in shared
+// memory: slot k (layers lmin + k, `stride` float4 apart) holds
+// (dT_a, dT_b, C_a, C_b); at() interpolates linearly in z, lane by lane.
+struct PairSampler {
+    const float4* base;
+    int stride, lmin;
+    SHG_D void at(int l, float t, f32x2& dT, f32x2& Cz) const {
+        const float4 a = base[(l - lmin) * stride], b = base[(l - lmin + 1) * stride];
+        const f32x2 t2 = bc2(t), da = pk2(a.x, a.y), ca = pk2(a.z, a.w);
+        dT = fma2(t2, sub2(pk2(b.x, b.y), da), da);
+        Cz = fma2(t2, sub2(pk2(b.z, b.w), ca), ca);
+    }
+};
+
+// Stage coefficients of a pair of points at stage point z (the arithmetic of
+// coef_at, lane by lane; the sine and cosine per lane).
+SHG_D Coef2 coef2_at(const InstDesc<float>& d, const StageZ<float>& z, bool thermal,
+                     const PairSampler& ps) {
+    if (!thermal) return {bc2(z.e.x), bc2(z.e.y), bc2(d.psi0F), bc2(d.psi0S)};
+    f32x2 dT, Cz;
+    ps.at(z.l, z.t, dT, Cz);
+    float a0, a1, s0, c0, s1, c1;
+    up2(mul2(bc2(d.g), Cz), a0, a1);
+    sincos_r<float>(a0, &s0, &c0);
+    sincos_r<float>(a1, &s1, &c1);
+    const f32x2 c = pk2(c0, c1), sn = pk2(s0, s1), ex = bc2(z.e.x), ey = bc2(z.e.y);
+    Coef2 k;
+    k.er = sub2(mul2(ex, c), mul2(ey, sn));
+    k.ei = fma2(ex, sn, mul2(ey, c));
+    k.pF = fma2(bc2(d.lF), dT, bc2(d.psi0F));
+    k.pS = fma2(bc2(d.lS), dT, bc2(d.psi0S));
+    return k;
+}
 SHG_D Coef2 pack2(const Coef<float>& a, const Coef<float>& b) {
     return {pk2(a.er, b.er), pk2(a.ei, b.ei), pk2(a.pF, b.pF), pk2(a.pS, b.pS)};
 }
@@ -249,31 +284,30 @@ struct Cx2 {
 };
 
 // The right-hand side of both equations for a pair of points, written as
-//   f_F  = (g_F + i psi_F) A_F  + i kF (A_SH conj(A_F)) e^{-i phi},  g_F  = -bF |A_F|^2
-//   f_SH = (g_S + i psi_SH) A_SH + i kS A_F^2 e^{+i phi},            g_S = -bS |A_SH|^2
+//   f_F  = (g_F + i psi_F) A_F  + i kF A_SH conj(u),   g_F  = -bF |A_F|^2
+//   f_SH = (g_S + i psi_SH) A_SH + i kS A_F u,          g_S = -bS |A_SH|^2
+// with u = A_F e^{i phi}: A_SH conj(A_F) e^{-i phi} = A_SH conj(u) and
+// A_F^2 e^{+i phi} = A_F u share the one product u.
 SHG_D void rhs2(const InstDesc<float>& d, const Coef2& k, const Cx2& aF, const Cx2& aS, Cx2& fF,
                 Cx2& fS) {
-    const f32x2 rr = mul2(aF.r, aF.r), ii = mul2(aF.i, aF.i);
-    const f32x2 gF = mul2(pk2(-d.bF, -d.bF), add2(rr, ii));
+    const f32x2 gF = mul2(pk2(-d.bF, -d.bF), fma2(aF.r, aF.r, mul2(aF.i, aF.i)));
     const f32x2 gS = mul2(pk2(-d.bS, -d.bS), fma2(aS.r, aS.r, mul2(aS.i, aS.i)));
     fF.r = sub2(mul2(gF, aF.r), mul2(k.pF, aF.i));
     fF.i = fma2(gF, aF.i, mul2(k.pF, aF.r));
     fS.r = sub2(mul2(gS, aS.r), mul2(k.pS, aS.i));
     fS.i = fma2(gS, aS.i, mul2(k.pS, aS.r));
+    const f32x2 ur = sub2(mul2(aF.r, k.er), mul2(aF.i, k.ei));  // u = A_F e^{i phi}
+    const f32x2 ui = fma2(aF.r, k.ei, mul2(aF.i, k.er));
     if (!d.undepleted) {
-        const f32x2 tr = fma2(aS.r, aF.r, mul2(aS.i, aF.i));  // A_SH conj(A_F)
-        const f32x2 ti = sub2(mul2(aS.i, aF.r), mul2(aS.r, aF.i));
-        const f32x2 ur = fma2(tr, k.er, mul2(ti, k.ei));      // * e^{-i phi}
-        const f32x2 ui = sub2(mul2(ti, k.er), mul2(tr, k.ei));
-        fF.r = fma2(pk2(-d.kF, -d.kF), ui, fF.r);
-        fF.i = fma2(pk2(d.kF, d.kF), ur, fF.i);
+        const f32x2 c1r = fma2(aS.r, ur, mul2(aS.i, ui));      // A_SH conj(u)
+        const f32x2 c1i = sub2(mul2(aS.i, ur), mul2(aS.r, ui));
+        fF.r = fma2(pk2(-d.kF, -d.kF), c1i, fF.r);
+        fF.i = fma2(pk2(d.kF, d.kF), c1r, fF.i);
     }
-    const f32x2 vr = sub2(rr, ii);                             // A_F^2
-    const f32x2 vi = mul2(add2(aF.r, aF.r), aF.i);
-    const f32x2 wr = sub2(mul2(vr, k.er), mul2(vi, k.ei));     // * e^{+i phi}
-    const f32x2 wi = fma2(vr, k.ei, mul2(vi, k.er));
-    fS.r = fma2(pk2(-d.kS, -d.kS), wi, fS.r);
-    fS.i = fma2(pk2(d.kS, d.kS), wr, fS.i);
+    const f32x2 c2r = sub2(mul2(aF.r, ur), mul2(aF.i, ui));    // A_F u
+    const f32x2 c2i = fma2(aF.r, ui, mul2(aF.i, ur));
+    fS.r = fma2(pk2(-d.kS, -d.kS), c2i, fS.r);
+    fS.i = fma2(pk2(d.kS, d.kS), c2r, fS.i);
 }
 
 // One RK4 step of size h for a pair of points (the stages of rk4 above).

@@ -26,7 +26,8 @@ constexpr int kPassThreads = 256;
 template <int V> struct MinBlocks { static constexpr int value = V == 0 ? 2 : 3; };
 
 // Per-thread prefetch slots of the per-point temperature table (FP32): two
-// buffers x up to three map layers x the two points of one loop iteration.
+// buffers x up to three map layers x one float4 (the point pair of one loop
+// iteration).
 constexpr int kSlotLayers = 3;
 template <class R> constexpr size_t slot_bytes() {
     return sizeof(R) == 4 ? size_t(2) * kSlotLayers * 2 * kPassThreads * sizeof(cx<R>) : 0;
@@ -87,18 +88,16 @@ SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, cons
     ts.la = -2;
 }
 
-// Copy (cp.async, one group, L2 evict-first) the per-point table values of map layers
-// lmin .. lmin + nl - 1 at points x0 and x0 + T of row y into the calling
-// thread's slots: slot (layer k, point p) at slots[(2k + p) * 256 + thread].
-template <int NX, int T, class C>
-SHG_D void prefetch_slots(C* slots, const C* umap, int lmin, int nl, int ny, int y, int x0) {
+// Copy (cp.async, one group, L2 evict-first) the per-point table entries of
+// map layers lmin .. lmin + nl - 1 for the point pair (2j, 2j + 1) of row y
+// into the calling thread's slots: layer k at slots[k * 256 + thread].
+template <int NX>
+SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, int ny, int y, int j) {
     const uint64_t pol = l2_evict_first_policy();
 #pragma unroll 1
     for (int k = 0; k < nl; ++k) {
-        const int o = ((lmin + k) * ny + y) * NX + x0;  // < 2^31: the table is <= 4 GiB
-        C* dst = slots + 2 * k * kPassThreads + threadIdx.x;
-        cp_async_stream(dst, umap + o, pol);
-        cp_async_stream(dst + kPassThreads, umap + o + T, pol);
+        const int o = ((lmin + k) * ny + y) * (NX / 2) + j;  // < 2^31: the table is <= 4 GiB
+        cp_async_stream(slots + k * kPassThreads + threadIdx.x, umap + o, pol);
     }
     cp_async_commit();
 }
@@ -106,10 +105,12 @@ SHG_D void prefetch_slots(C* slots, const C* umap, int lmin, int nl, int ny, int
 // Row pass R(s).  grid = (ceil(ny / ROWS), instances); block = 256.
 //
 // The CTA's rows of both fields are copied into padded shared buffers with
-// cp.async (all copies in flight at once).  Each thread owns the points
-// x = t + T*m of its row; the nonlinear part runs point by point in a rolled
-// loop on the shared copy, so no register array is indexed dynamically, and
-// the transforms then run field by field from the same buffers.  With a
+// cp.async (all copies in flight at once).  The nonlinear part runs on the
+// shared copy in a rolled loop, so that no register array is indexed
+// dynamically: iteration i of thread t advances the adjacent points 2j and
+// 2j + 1, j = t + T*i (in FP32 together, in packed arithmetic).  The
+// transforms then run field by field from the same buffers, each thread on
+// the points x = t + T*m.  With a
 // per-point temperature table (FP32), the (dT, C) of the map layers that this
 // step's stage points fall between are streamed from it by cp.async into
 // per-thread slots one loop iteration ahead (UM: the launcher has checked
@@ -156,7 +157,8 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
         }
     }
     const bool dep = descs[blockIdx.y].Q != nullptr;
-    C* slots = reinterpret_cast<C*>(smem_raw + G::fields);
+    float4* slots = reinterpret_cast<float4*>(smem_raw + G::fields);
+    const float4* umap4 = reinterpret_cast<const float4*>(descs[blockIdx.y].umap);
     float* bins = reinterpret_cast<float*>(pS + 2 * NX);
     const int nb = dep ? ROWS * descs[blockIdx.y].hx : 0;
     for (int i = threadIdx.x; i < nb; i += kPassThreads) bins[i] = 0.f;
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     if constexpr (UM) {
         if (um && active) {
             cp_async_commit();  // the field rows
-            prefetch_slots<NX, T>(slots, d.umap, lmin, nl, ny, y, t);
+            prefetch_slots<NX>(slots, umap4, lmin, nl, ny, y, t);
             cp_async_wait_group<1>();
             staged = true;
         }
@@ -214,17 +216,17 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
             rk4(d, aF, aS, cz, cm, c1, h);
         }
     };
-    // The same for two points at once in packed FP32 arithmetic (the body
-    // exists for FP32 only).
-    auto pair = [&](int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1, auto& sa, auto& sb) {
+    // The same for two points at once in packed FP32 arithmetic, with the
+    // stage coefficients of stage point q from cq(q) (the body exists for
+    // FP32 only).
+    auto pair = [&](int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1, auto&& cq) {
         if constexpr (sizeof(R) == 4) {
-            const Coef<R> za = coef_at(d, zsh[2], thermal, sa);
-            const Coef<R> zb = coef_at(d, zsh[2], thermal, sb);
+            const Coef2 z2 = cq(2);  // z_s, shared by both halves
             Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, S{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
             if (s > 0) {
-                const Coef2 c0 = pack2(coef_at(d, zsh[0], thermal, sa), coef_at(d, zsh[0], thermal, sb));
-                const Coef2 cm = pack2(coef_at(d, zsh[1], thermal, sa), coef_at(d, zsh[1], thermal, sb));
-                rk4_2(dsh, F, S, c0, cm, pack2(za, zb), h);
+                const Coef2 c0 = cq(0);
+                const Coef2 cm = cq(1);
+                rk4_2(dsh, F, S, c0, cm, z2, h);
             }
             if (l_dep >= 0 && j_dep >= 0) {
                 up2(F.r, aF0.x, aF1.x);
@@ -235,9 +237,9 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
                 deposit(xb, aF1, aS1);
             }
             if (s < nz) {
-                const Coef2 cm = pack2(coef_at(d, zsh[3], thermal, sa), coef_at(d, zsh[3], thermal, sb));
-                const Coef2 c1 = pack2(coef_at(d, zsh[4], thermal, sa), coef_at(d, zsh[4], thermal, sb));
-                rk4_2(dsh, F, S, pack2(za, zb), cm, c1, h);
+                const Coef2 cm = cq(3);
+                const Coef2 c1 = cq(4);
+                rk4_2(dsh, F, S, z2, cm, c1, h);
             }
             up2(F.r, aF0.x, aF1.x);
             up2(F.i, aF0.y, aF1.y);
@@ -246,36 +248,38 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
         }
     };
     if (active) {
-        // two independent points per iteration: in FP32 they advance together
-        // in packed arithmetic; in FP64 they give the scheduler two RK4
+        // two adjacent points per iteration: in FP32 they advance together in
+        // packed arithmetic; in FP64 they give the scheduler two RK4
         // dependency chains to interleave
 #pragma unroll 1
-        for (int m = 0; m < E; m += 2) {
-            const int x0 = t + T * m, x1 = x0 + T;
+        for (int i = 0; i < E / 2; ++i) {
+            const int j = t + T * i, x0 = 2 * j, x1 = x0 + 1;
             C aF0 = sF[pidx<R>(x0)], aS0 = sS[pidx<R>(x0)];
             C aF1 = sF[pidx<R>(x1)], aS1 = sS[pidx<R>(x1)];
             if constexpr (UM) {
-                const int buf = (m >> 1) & 1;
+                const int buf = i & 1;
                 if (um) {
-                    if (m + 2 < E) {
-                        prefetch_slots<NX, T>(slots + (buf ^ 1) * kSlotLayers * 2 * kPassThreads,
-                                              d.umap, lmin, nl, ny, y, x1 + T);
+                    if (i + 1 < E / 2) {
+                        prefetch_slots<NX>(slots + (buf ^ 1) * kSlotLayers * kPassThreads, umap4,
+                                           lmin, nl, ny, y, j + T);
                         cp_async_wait_group<1>();
                     } else {
                         cp_async_wait_group<0>();
                     }
                 }
-                const C* b0 = slots + (buf * kSlotLayers * 2) * kPassThreads + threadIdx.x;
-                SlotSampler<R> s0{b0, 2 * kPassThreads, lmin};
-                SlotSampler<R> s1{b0 + kPassThreads, 2 * kPassThreads, lmin};
-                pair(x0, x1, aF0, aS0, aF1, aS1, s0, s1);
+                const PairSampler ps{slots + buf * kSlotLayers * kPassThreads + threadIdx.x,
+                                     kPassThreads, lmin};
+                pair(x0, x1, aF0, aS0, aF1, aS1,
+                     [&](int q) { return coef2_at(dsh, zsh[q], thermal, ps); });
             } else if constexpr (sizeof(R) == 4) {
                 TempSampler<R> s0, s1;
                 if (thermal) {
                     make_sampler(d, mv, x0, rc, s0);
                     make_sampler(d, mv, x1, rc, s1);
                 }
-                pair(x0, x1, aF0, aS0, aF1, aS1, s0, s1);
+                pair(x0, x1, aF0, aS0, aF1, aS1, [&](int q) {
+                    return pack2(coef_at(d, zsh[q], thermal, s0), coef_at(d, zsh[q], thermal, s1));
+                });
             } else {
                 {
                     TempSampler<R> s0;
@@ -294,6 +298,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
             sS[pidx<R>(x1)] = aS1;
         }
     }
+    __syncthreads();  // the transforms read points that other threads advanced
     if (dep) {
         __syncthreads();
         const int y0 = blockIdx.x * ROWS;
@@ -452,9 +457,10 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     }
 }
 
-// Per-point temperature table: umap[l][y][x] = the bilinear sample of map
-// layer l at field point (x, y), with the same cell arithmetic as the passes'
-// node sampler.  grid = (ceil(nx / 256), ny, tz); block = 256.
+// Per-point temperature table: the bilinear sample (dT, C) of map layer l at
+// field point (x, y), with the same cell arithmetic as the passes' node
+// sampler, stored per adjacent point pair as (dT_2j, dT_2j+1, C_2j, C_2j+1)
+// ([tz][ny][nx/2] float4).  grid = (ceil(nx / 256), ny, tz); block = 256.
 template <class R>
 __global__ void k_upsample_map(const InstDesc<R>* __restrict__ dp, cx<R>* __restrict__ out,
                                int nx, int ny) {
@@ -464,7 +470,11 @@ __global__ void k_upsample_map(const InstDesc<R>* __restrict__ dp, cx<R>* __rest
     const MapView<R> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
     TempSampler<R> ts;
     make_sampler(d, mv, x, row_cell(d, y), ts);
-    out[(size_t(l) * ny + y) * nx + x] = ts.bil(l);
+    const cx<R> v = ts.bil(l);
+    // pair layout: (dT_2j, dT_2j+1, C_2j, C_2j+1) at pair j = x / 2
+    R* o = reinterpret_cast<R*>(out) + ((size_t(l) * ny + y) * (nx / 2) + x / 2) * 4 + (x & 1);
+    o[0] = v.x;
+    o[2] = v.y;
 }
 
 }  // namespace shg
