@@ -383,9 +383,10 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
 
 // Column pass staged by TMA (FP32).  One elected thread issues 3-D box copies
 // of the CTA's TILE columns of both fields ([field][row][column] boxes of up
-// to 256 rows) from the instance's tensor map into a dense shared buffer;
-// the block waits on an mbarrier with a bounded number of polls (on expiry it
-// records SHG_ERR_TIMEOUT in the instance status and returns).  Each field is
+// to 256 rows) from the instance's tensor map into a dense shared buffer, one
+// mbarrier per field; before each field the block waits on its barrier with
+// a bounded number of polls (on expiry it records SHG_ERR_TIMEOUT in the
+// instance status, lets the issued copies land and returns).  Each field is
 // then transformed from that buffer through one padded exchange buffer and
 // written back from registers.  grid = (ceil(nx / TILE), instances).
 template <int NY> struct ColTma {
@@ -415,36 +416,39 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     const InstDesc<float>& d = descs[blockIdx.y];
     const int x0 = blockIdx.x * TILE;
     if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
         mbar_init_fence();
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        mbar_arrive_expect_tx(bar, unsigned(K::stage_bytes));
+        // one barrier per field, so that field 0 is transformed while field 1 lands
         const CUtensorMap* tm = tmaps + blockIdx.y;
 #pragma unroll
-        for (int f = 0; f < 2; ++f)
+        for (int f = 0; f < 2; ++f) {
+            mbar_arrive_expect_tx(&bar[f], unsigned(K::stage_bytes / 2));
 #pragma unroll
             for (int yb = 0; yb < NY; yb += BY)
-                tma_load_3d(stage + (size_t(f) * NY + yb) * TILE, tm, x0, yb, f, bar);
+                tma_load_3d(stage + (size_t(f) * NY + yb) * TILE, tm, x0, yb, f, &bar[f]);
+        }
     }
     stage_tables<float, NY>(twS, pS, tw, d.py);
     cp_async_wait_all();
-    const bool ok = mbar_wait_bounded(bar, 0, d.wait_polls);
-    if (__syncthreads_or(!ok)) {
-        // Give up on this tile: report, then let the copies already issued
-        // land (bounded again) before the CTA's shared memory is released.
-        if (threadIdx.x == 0) {
-            if (d.status) atomicExch(d.status, int(SHG_ERR_TIMEOUT));
-            mbar_wait_bounded(bar, 0, kTmaMaxPolls);
-        }
-        return;
-    }
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = x0 + c;
     const bool active = x < nx;
 #pragma unroll 1
     for (int f = 0; f < 2; ++f) {
+        const bool ok = mbar_wait_bounded(&bar[f], 0, d.wait_polls);
+        if (__syncthreads_or(!ok)) {
+            // Give up on this tile: report, then let the copies already issued
+            // land (bounded again) before the CTA's shared memory is released.
+            if (threadIdx.x == 0) {
+                if (d.status) atomicExch(d.status, int(SHG_ERR_TIMEOUT));
+                for (int g = f; g < 2; ++g) mbar_wait_bounded(&bar[g], 0, kTmaMaxPolls);
+            }
+            return;
+        }
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = stage[(size_t(f) * NY + t + T * m) * TILE + c];
