@@ -38,8 +38,12 @@ class SHGEfficiency(torch.autograd.Function):
             g_dT = torch.empty(ctx.dT_shape, dtype=torch.float32, device="cuda")
         gw, gz, gt = shg_propagate_adjoint(plan.handle, float(grad_eta), g_dT)
         dev_out = g_dT.to(ctx.dT_dtype) if g_dT is not None else None
-        to = lambda v: torch.tensor(v, dtype=torch.float64)  # noqa: E731
-        return None, to(gw), to(gz), to(gt), dev_out
+        need = ctx.needs_input_grad  # plain-number inputs get None
+
+        def to(i, v):
+            return torch.tensor(v, dtype=torch.float64) if need[i] else None
+
+        return None, to(1, gw), to(2, gz), to(3, gt), dev_out if need[4] else None
 
 
 def efficiency(plan: Plan, w0, z_focus, t_off, dT=None):

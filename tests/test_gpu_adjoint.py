@@ -117,3 +117,18 @@ def test_adjoint_full_size_fp32_vs_fp64_and_invariant():
     assert np.abs(gT32 - gT64).max() <= 1e-3 * np.abs(gT64).max()
     for g, gT in ((g32, gT32), (g64, gT64)):
         assert abs(g[2] - gT.sum()) <= 1e-3 * np.abs(gT).sum()
+
+
+def test_autograd_with_plain_number_inputs():
+    """Only w0 requires a gradient; z_focus and T_off are plain numbers and dT
+    a tensor without grad: the backward returns no gradient for them, and
+    w0's gradient equals the one of the all-tensor call."""
+    import paper_2410_04994_gb300 as pkg
+    from paper_2410_04994_gb300.autograd import efficiency
+    w = _grad_case(precision="f64")
+    _, g_all, _ = _gpu_grads(w)
+    plan = pkg.Plan(w, adjoint=True)
+    w0 = torch.tensor(w.w0, dtype=torch.float64, requires_grad=True)
+    eta = efficiency(plan, w0, w.z_focus, w.t_off, torch.tensor(w.dT, device="cuda"))
+    eta.backward()
+    assert abs(float(w0.grad) - g_all[0]) <= 1e-12 * abs(g_all[0])
