@@ -321,7 +321,7 @@ static std::map<std::tuple<bool, int, int>, int> g_tuned;
 
 static int forced_variant() {
     const char* f = getenv("SHG_FFT_VARIANT");
-    return (f && f[0] >= '0' && f[0] <= '2' && f[1] == 0) ? f[0] - '0' : -1;
+    return (f && f[0] >= '0' && f[0] <= '3' && f[1] == 0) ? f[0] - '0' : -1;
 }
 
 int row_umap_bit(const std::vector<shg_plan*>& plans) {
@@ -335,11 +335,13 @@ int row_umap_bit(const std::vector<shg_plan*>& plans) {
 }
 
 // Candidate flavours of a pass for a length: the default shape, the
-// alternative shape, and (column pass) the TMA-staged kernel.
+// alternative shape, and (column pass) the TMA-staged kernel and the default
+// shape in 128-thread CTAs.
 static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     std::vector<int> c{0};
     if (has_fft_variant(fp64, n)) c.push_back(1);
     if (pass == 1 && tmaps && col_tma_tile(fp64, n) > 0) c.push_back(2);
+    if (pass == 1 && has_col_small(fp64, n)) c.push_back(3);
     return c;
 }
 
@@ -347,7 +349,8 @@ int fft_variant(bool fp64, int n, int pass, int row_bits) {
     const int f = forced_variant();
     if (f >= 0) {
         if (f == 1 && !has_fft_variant(fp64, n)) return 0;
-        if (f == 2 && pass == 0) return 0;
+        if (f >= 2 && pass == 0) return 0;
+        if (f == 3 && !has_col_small(fp64, n)) return 0;
         return f;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);

@@ -11,10 +11,12 @@ cudaError_t col_f32(int, int, const void*, int, int, const void*, cudaStream_t, 
 cudaError_t col_f64(int, int, const void*, int, int, const void*, cudaStream_t, const void*);
 int col_tma_tile_f32(int);
 bool has_variant_f32(int);
+bool has_col_small_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
 
 bool has_fft_variant(bool fp64, int n) { return !fp64 && has_variant_f32(n); }
+bool has_col_small(bool fp64, int n) { return !fp64 && has_col_small_f32(n); }
 
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
                        const void* tw, int hx, cudaStream_t st, int variant) {

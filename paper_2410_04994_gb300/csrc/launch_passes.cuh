@@ -29,8 +29,8 @@ template <class R, int N, int V = 0, bool UM = false> size_t row_smem(int hx) {
     return RowGeom<R, N, V>::fields + (UM ? slot_bytes<R>() : 0) + RowGeom<R, N, V>::tables +
            size_t(RowGeom<R, N, V>::ROWS) * hx * sizeof(float);
 }
-template <class R, int N, int V = 0> cudaError_t col_attr() {
-    return allow_max_dyn_smem(k_col_pass<R, N, V>);
+template <class R, int N, int V = 0, int NTH = kPassThreads> cudaError_t col_attr() {
+    return allow_max_dyn_smem(k_col_pass<R, N, V, NTH>);
 }
 
 template <class R, int N, int V = 0, bool UM = false>
@@ -43,11 +43,11 @@ cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, cons
     return cudaGetLastError();
 }
 
-template <class R, int N, int V = 0>
+template <class R, int N, int V = 0, int NTH = kPassThreads>
 cudaError_t col_launch(const void* descs, int ninst, int nx, const void* tw, cudaStream_t st) {
-    using G = ColGeom<R, N, V>;
+    using G = ColGeom<R, N, V, NTH>;
     dim3 grid((nx + G::TILE - 1) / G::TILE, ninst);
-    k_col_pass<R, N, V><<<grid, kPassThreads, G::smem, st>>>(static_cast<const InstDesc<R>*>(descs),
+    k_col_pass<R, N, V, NTH><<<grid, NTH, G::smem, st>>>(static_cast<const InstDesc<R>*>(descs),
                                                           nx, static_cast<const pt<R>*>(tw));
     return cudaGetLastError();
 }

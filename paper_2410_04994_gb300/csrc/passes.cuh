@@ -43,10 +43,10 @@ template <class R, int N, int V = 0> struct RowGeom {
 };
 
 
-template <class R, int N, int V = 0> struct ColGeom {
+template <class R, int N, int V = 0, int NTH = kPassThreads> struct ColGeom {
     using F = FftCfg<R, N, V>;
     static constexpr int T = F::T;
-    static constexpr int TILE = kPassThreads / T;
+    static constexpr int TILE = NTH / T;  // columns per CTA of NTH threads
     static constexpr int S = padded_len<R>(N, TILE < Bank<R>::W ? Bank<R>::W / TILE : 1);
     static constexpr size_t fields = size_t(2) * TILE * S * sizeof(cx<R>);
     static constexpr size_t smem = fields + size_t(3) * N * sizeof(pt<R>);  // + twiddles, factors
@@ -330,16 +330,17 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     }
 }
 
-// Column pass C(s).  grid = (ceil(nx / TILE), instances); block = 256.
+// Column pass C(s).  grid = (ceil(nx / TILE), instances); block = NTH (256,
+// or 128 for half as many columns per CTA and twice as many resident CTAs).
 // The TILE columns of both fields are staged into padded shared buffers with
 // cp.async, one commit group per field, transformed field by field (the
 // second field is still landing while the first is transformed), and written
 // back from registers.
-template <class R, int NY, int V = 0>
-__global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
+template <class R, int NY, int V = 0, int NTH = kPassThreads>
+__global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
     k_col_pass(const InstDesc<R>* __restrict__ descs, int nx, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = ColGeom<R, NY, V>;
+    using G = ColGeom<R, NY, V, NTH>;
     constexpr int E = FftCfg<R, NY, V>::E, T = G::T, TILE = G::TILE, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);

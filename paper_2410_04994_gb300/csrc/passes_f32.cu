@@ -10,6 +10,7 @@ namespace shg {
 #define SHG_F32_TMA_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(1024)
 
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
+bool has_col_small_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
 // v: FFT shape (0 or 1), plus kRowUmap to read the per-point temperature table.
 template <bool UM>
@@ -55,6 +56,13 @@ cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const v
 #undef X
         }
     }
+    if (v == 3) {
+        switch (ny) {
+#define X(n) case n: return col_launch<float, n, 0, 128>(descs, ninst, nx, tw, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     if (v == 1) {
         switch (ny) {
 #define X(n) case n: return col_launch<float, n, 1>(descs, ninst, nx, tw, st);
@@ -90,7 +98,8 @@ cudaError_t attr_f32() {
 #define X(n)                                                    \
     if (e == cudaSuccess) e = row_attr<float, n, 1>();          \
     if (e == cudaSuccess) e = row_attr<float, n, 1, true>();    \
-    if (e == cudaSuccess) e = col_attr<float, n, 1>();
+    if (e == cudaSuccess) e = col_attr<float, n, 1>();          \
+    if (e == cudaSuccess) e = col_attr<float, n, 0, 128>();
     SHG_F32_VARIANT_SIZES(X)
 #undef X
 #define X(n) \

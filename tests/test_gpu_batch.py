@@ -81,11 +81,11 @@ def test_sweep_instances_full_length(n):
     assert rel_l2(a_f.cpu(), AF) < FIELD_TOL
 
 
-@pytest.mark.parametrize("variant", ["1", "2"])
+@pytest.mark.parametrize("variant", ["1", "2", "3"])
 def test_batch_with_each_forced_kernel_flavour(variant, monkeypatch):
-    """The batch path with the alternative FFT shape (1) or the TMA-staged
-    column pass over the group's tensor-map array (2) forced, against the
-    oracle per instance."""
+    """The batch path with the alternative FFT shape (1), the TMA-staged
+    column pass over the group's tensor-map array (2) or the 128-thread column
+    pass (3) forced, against the oracle per instance."""
     import paper_2410_04994_gb300 as pkg
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
     insts = W.sweep_instances(nz=12, groups=((64, 2), (128, 2), (256, 1)), tgrid=(9, 9, 12))
