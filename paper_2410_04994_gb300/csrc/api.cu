@@ -318,6 +318,32 @@ static shg_status_t quiesce(shg_plan* p) {
 
 static std::mutex g_tune_mu;
 static std::map<std::tuple<bool, int, int>, int> g_tuned;
+static bool g_cache_loaded = false;
+
+// Optional persistent tuner decisions: with SHG_TUNE_CACHE=<file>, decisions
+// found in the file are used instead of timing, and new decisions are
+// appended ("fp64 n pass flavour" per line; pass 0 row, 1 column, 2 row with
+// the per-point table).  Caller holds g_tune_mu.
+static void load_tune_cache() {
+    if (g_cache_loaded) return;
+    g_cache_loaded = true;
+    const char* path = getenv("SHG_TUNE_CACHE");
+    if (!path || !path[0]) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    int fp64, n, pass, v;
+    while (fscanf(f, "%d %d %d %d", &fp64, &n, &pass, &v) == 4)
+        if (v >= 0 && v <= 3) g_tuned.emplace(std::make_tuple(fp64 != 0, n, pass), v);
+    fclose(f);
+}
+static void save_tune_decision(bool fp64, int n, int pass, int v) {
+    const char* path = getenv("SHG_TUNE_CACHE");
+    if (!path || !path[0]) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%d %d %d %d\n", fp64 ? 1 : 0, n, pass, v);
+    fclose(f);
+}
 
 static int forced_variant() {
     const char* f = getenv("SHG_FFT_VARIANT");
@@ -354,6 +380,7 @@ int fft_variant(bool fp64, int n, int pass, int row_bits) {
         return f;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_cache();
     auto it = g_tuned.find(std::make_tuple(fp64, n, pass + (row_bits ? 2 : 0)));
     return it == g_tuned.end() ? 0 : it->second;
 }
@@ -373,6 +400,7 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         if (cand.size() < 2) continue;
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
+            load_tune_cache();
             if (g_tuned.count(std::make_tuple(fp64, n, pass + (pass == 0 && row_bits ? 2 : 0))))
                 continue;
         }
@@ -413,7 +441,9 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[std::make_tuple(fp64, n, pass + (pass == 0 && row_bits ? 2 : 0))] = best_v;
+        const int key = pass + (pass == 0 && row_bits ? 2 : 0);
+        g_tuned[std::make_tuple(fp64, n, key)] = best_v;
+        save_tune_decision(fp64, n, key, best_v);
     }
     return SHG_OK;
 }

@@ -96,3 +96,37 @@ def test_batch_with_each_forced_kernel_flavour(variant, monkeypatch):
         assert abs(e / eta_ref - 1) < ETA_TOL, (w.name, e, eta_ref)
         a_f, a_sh = p.fields()
         assert rel_l2(a_sh.cpu(), AS) < FIELD_TOL
+
+
+def test_tuner_cache_file_records_and_replays_decisions(tmp_path):
+    """SHG_TUNE_CACHE: a fresh process records one decision per (size, pass)
+    of the batch; a second process that reads a doctored file (every column
+    pass forced to the TMA flavour) uses it without re-timing and still
+    matches the first process's result to FP32 rounding."""
+    import json
+    import os
+    import subprocess
+    import sys
+    cache = tmp_path / "tune.txt"
+    script = (
+        "import json, torch, workloads as W, paper_2410_04994_gb300 as pkg\n"
+        "insts = W.sweep_instances(nz=8, groups=((64, 2), (128, 2)), tgrid=(9, 9, 12))\n"
+        "plans = [pkg.Plan(w) for w in insts]\n"
+        "[p.set_temperature(torch.as_tensor(w.dT), w.t_lx, w.t_ly) for p, w in zip(plans, insts)]\n"
+        "print(json.dumps(pkg.shg_batch_submit([p.handle for p in plans])))\n")
+    env = dict(os.environ, SHG_TUNE_CACHE=str(cache))
+    env.pop("SHG_FFT_VARIANT", None)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out1 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root, check=True,
+                          capture_output=True, text=True).stdout
+    lines = [tuple(map(int, l.split())) for l in cache.read_text().splitlines()]
+    keys = {(n, p) for _, n, p, _ in lines}
+    # one column decision and one row decision (pass 0 or 2) per size
+    assert {(64, 1), (128, 1)} <= keys and len(lines) == 4, lines
+    cache.write_text("".join(f"{f} {n} {p} {2 if p == 1 else v}\n" for f, n, p, v in lines))
+    out2 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root, check=True,
+                          capture_output=True, text=True).stdout
+    assert len(cache.read_text().splitlines()) == 4      # nothing re-timed
+    e1, e2 = json.loads(out1.strip().splitlines()[-1]), json.loads(out2.strip().splitlines()[-1])
+    for a, b in zip(e1, e2):
+        assert abs(a / b - 1) < 1e-5
