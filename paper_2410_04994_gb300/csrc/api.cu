@@ -361,13 +361,13 @@ int row_umap_bit(const std::vector<shg_plan*>& plans) {
 }
 
 // Candidate flavours of a pass for a length: the default shape, the
-// alternative shape, and (column pass) the TMA-staged kernel and the default
-// shape in 128-thread CTAs.
+// alternative shape, the default shape in 128-thread CTAs and (column pass)
+// the TMA-staged kernel.
 static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     std::vector<int> c{0};
     if (has_fft_variant(fp64, n)) c.push_back(1);
     if (pass == 1 && tmaps && col_tma_tile(fp64, n) > 0) c.push_back(2);
-    if (pass == 1 && has_col_small(fp64, n)) c.push_back(3);
+    if (has_col_small(fp64, n)) c.push_back(3);
     return c;
 }
 
@@ -375,7 +375,7 @@ int fft_variant(bool fp64, int n, int pass, int row_bits) {
     const int f = forced_variant();
     if (f >= 0) {
         if (f == 1 && !has_fft_variant(fp64, n)) return 0;
-        if (f >= 2 && pass == 0) return 0;
+        if (f == 2 && pass == 0) return 0;
         if (f == 3 && !has_col_small(fp64, n)) return 0;
         return f;
     }
@@ -581,7 +581,7 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
             !(crystal->wy > 0) || !(crystal->kappa_th > 0))
             return SHG_ERR_INVALID_ARG;
         // the row pass bins the heat deposit per CTA in shared memory
-        for (int v : {0, 1, kRowUmap, 1 | kRowUmap})
+        for (int v : {0, 1, 3, kRowUmap, 1 | kRowUmap, 3 | kRowUmap})
             if (row_pass_smem(fp64, grid->nx, grid->hx, v) > 223 * 1024)
                 return SHG_ERR_UNSUPPORTED_GRID;
     }

@@ -19,26 +19,28 @@ template <class K> cudaError_t allow_max_dyn_smem(K kernel) {
     return e;
 }
 
-template <class R, int N, int V = 0, bool UM = false> cudaError_t row_attr() {
-    return allow_max_dyn_smem(k_row_pass<R, N, V, UM>);
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads>
+cudaError_t row_attr() {
+    return allow_max_dyn_smem(k_row_pass<R, N, V, UM, NTH>);
 }
 
 // Dynamic shared memory of a row pass: transform buffers + table prefetch
 // slots (UM) + deposit bins.
-template <class R, int N, int V = 0, bool UM = false> size_t row_smem(int hx) {
-    return RowGeom<R, N, V>::fields + (UM ? slot_bytes<R>() : 0) + RowGeom<R, N, V>::tables +
-           size_t(RowGeom<R, N, V>::ROWS) * hx * sizeof(float);
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads>
+size_t row_smem(int hx) {
+    using G = RowGeom<R, N, V, NTH>;
+    return G::fields + (UM ? slot_bytes<R, NTH>() : 0) + G::tables + size_t(G::ROWS) * hx * sizeof(float);
 }
 template <class R, int N, int V = 0, int NTH = kPassThreads> cudaError_t col_attr() {
     return allow_max_dyn_smem(k_col_pass<R, N, V, NTH>);
 }
 
-template <class R, int N, int V = 0, bool UM = false>
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads>
 cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, const void* tw,
                        int hx, cudaStream_t st) {
-    using G = RowGeom<R, N, V>;
+    using G = RowGeom<R, N, V, NTH>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    k_row_pass<R, N, V, UM><<<grid, kPassThreads, row_smem<R, N, V, UM>(hx), st>>>(
+    k_row_pass<R, N, V, UM, NTH><<<grid, NTH, row_smem<R, N, V, UM, NTH>(hx), st>>>(
         static_cast<const InstDesc<R>*>(descs), ny, nz, s, static_cast<const pt<R>*>(tw));
     return cudaGetLastError();
 }

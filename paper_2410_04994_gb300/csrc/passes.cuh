@@ -29,14 +29,14 @@ template <int V> struct MinBlocks { static constexpr int value = V == 0 ? 2 : 3;
 // buffers x up to three map layers x one float4 (the point pair of one loop
 // iteration).
 constexpr int kSlotLayers = 3;
-template <class R> constexpr size_t slot_bytes() {
-    return sizeof(R) == 4 ? size_t(2) * kSlotLayers * 2 * kPassThreads * sizeof(cx<R>) : 0;
+template <class R, int NTH = kPassThreads> constexpr size_t slot_bytes() {
+    return sizeof(R) == 4 ? size_t(2) * kSlotLayers * NTH * sizeof(float4) : 0;
 }
 
-template <class R, int N, int V = 0> struct RowGeom {
+template <class R, int N, int V = 0, int NTH = kPassThreads> struct RowGeom {
     using F = FftCfg<R, N, V>;
     static constexpr int T = F::T;
-    static constexpr int ROWS = kPassThreads / T;
+    static constexpr int ROWS = NTH / T;  // rows per CTA of NTH threads
     static constexpr int S = padded_len<R>(N, T < Bank<R>::W ? T : 1);
     static constexpr size_t fields = size_t(2) * ROWS * S * sizeof(cx<R>);
     static constexpr size_t tables = size_t(3) * N * sizeof(pt<R>);  // twiddles + 2 factor rows
@@ -90,19 +90,20 @@ SHG_D void make_sampler(const InstDesc<R>& d, const MapView<R>& mv, int xi, cons
 
 // Copy (cp.async, one group, L2 evict-first) the per-point table entries of
 // map layers lmin .. lmin + nl - 1 for the point pair (2j, 2j + 1) of row y
-// into the calling thread's slots: layer k at slots[k * 256 + thread].
-template <int NX>
+// into the calling thread's slots: layer k at slots[k * NTH + thread].
+template <int NX, int NTH>
 SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, int ny, int y, int j) {
     const uint64_t pol = l2_evict_first_policy();
 #pragma unroll 1
     for (int k = 0; k < nl; ++k) {
         const int o = ((lmin + k) * ny + y) * (NX / 2) + j;  // < 2^31: the table is <= 4 GiB
-        cp_async_stream(slots + k * kPassThreads + threadIdx.x, umap + o, pol);
+        cp_async_stream(slots + k * NTH + threadIdx.x, umap + o, pol);
     }
     cp_async_commit();
 }
 
-// Row pass R(s).  grid = (ceil(ny / ROWS), instances); block = 256.
+// Row pass R(s).  grid = (ceil(ny / ROWS), instances); block = NTH (256, or
+// 128 for half as many rows per CTA).
 //
 // The CTA's rows of both fields are copied into padded shared buffers with
 // cp.async (all copies in flight at once).  The nonlinear part runs on the
@@ -119,12 +120,12 @@ SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, i
 // point samples the node table bilinearly.  The heat deposit at z_s (THERMAL plans) is binned
 // per CTA in shared memory and added to the heat grid with one
 // double-precision atomic per touched node.
-template <class R, int NX, int V = 0, bool UM = false>
-__global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
+template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads>
+__global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = RowGeom<R, NX, V>;
+    using G = RowGeom<R, NX, V, NTH>;
     constexpr int E = FftCfg<R, NX, V>::E, T = G::T, ROWS = G::ROWS, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<R> dsh;
@@ -136,7 +137,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     C* sF = smem + lr * S;
     C* sS = smem + (ROWS + lr) * S;
     // shared copies of the twiddles and of the row factors of both fields
-    pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields + (UM ? slot_bytes<R>() : 0));
+    pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields + (UM ? slot_bytes<R, NTH>() : 0));
     pt<R>* pS = twS + NX;
     {
         const InstDesc<R>& dg = descs[blockIdx.y];
@@ -161,7 +162,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     const float4* umap4 = reinterpret_cast<const float4*>(descs[blockIdx.y].umap);
     float* bins = reinterpret_cast<float*>(pS + 2 * NX);
     const int nb = dep ? ROWS * descs[blockIdx.y].hx : 0;
-    for (int i = threadIdx.x; i < nb; i += kPassThreads) bins[i] = 0.f;
+    for (int i = threadIdx.x; i < nb; i += NTH) bins[i] = 0.f;
     __syncthreads();
     const InstDesc<R>& d = dsh;
     const bool thermal = d.ttab != nullptr;
@@ -179,7 +180,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     if constexpr (UM) {
         if (um && active) {
             cp_async_commit();  // the field rows
-            prefetch_slots<NX>(slots, umap4, lmin, nl, ny, y, t);
+            prefetch_slots<NX, NTH>(slots, umap4, lmin, nl, ny, y, t);
             cp_async_wait_group<1>();
             staged = true;
         }
@@ -260,15 +261,14 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
                 const int buf = i & 1;
                 if (um) {
                     if (i + 1 < E / 2) {
-                        prefetch_slots<NX>(slots + (buf ^ 1) * kSlotLayers * kPassThreads, umap4,
-                                           lmin, nl, ny, y, j + T);
+                        prefetch_slots<NX, NTH>(slots + (buf ^ 1) * kSlotLayers * NTH, umap4,
+                                                lmin, nl, ny, y, j + T);
                         cp_async_wait_group<1>();
                     } else {
                         cp_async_wait_group<0>();
                     }
                 }
-                const PairSampler ps{slots + buf * kSlotLayers * kPassThreads + threadIdx.x,
-                                     kPassThreads, lmin};
+                const PairSampler ps{slots + buf * kSlotLayers * NTH + threadIdx.x, NTH, lmin};
                 pair(x0, x1, aF0, aS0, aF1, aS1,
                      [&](int q) { return coef2_at(dsh, zsh[q], thermal, ps); });
             } else if constexpr (sizeof(R) == 4) {
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kPassThreads, MinBlocks<V>::value)
     if (dep) {
         __syncthreads();
         const int y0 = blockIdx.x * ROWS;
-        for (int k = threadIdx.x; k < nb; k += kPassThreads) {
+        for (int k = threadIdx.x; k < nb; k += NTH) {
             const float v = bins[k];
             if (v != 0.f && l_dep >= 0) {
                 const int r = k / d.hx, i = k - r * d.hx;

@@ -12,10 +12,18 @@ namespace shg {
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
 bool has_col_small_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
-// v: FFT shape (0 or 1), plus kRowUmap to read the per-point temperature table.
+// v: flavour (0, 1: FFT shape; 3: shape 0 in 128-thread CTAs), plus kRowUmap
+// to read the per-point temperature table.
 template <bool UM>
 static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
                               const void* tw, int hx, cudaStream_t st) {
+    if (v == 3) {
+        switch (nx) {
+#define X(n) case n: return row_launch<float, n, 0, UM, 128>(descs, ninst, ny, nz, s, tw, hx, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     if (v == 1) {
         switch (nx) {
 #define X(n) case n: return row_launch<float, n, 1, UM>(descs, ninst, ny, nz, s, tw, hx, st);
@@ -95,10 +103,12 @@ cudaError_t attr_f32() {
     if (e == cudaSuccess) e = col_attr<float, n>();
     SHG_F32_SIZES(X)
 #undef X
-#define X(n)                                                    \
-    if (e == cudaSuccess) e = row_attr<float, n, 1>();          \
-    if (e == cudaSuccess) e = row_attr<float, n, 1, true>();    \
-    if (e == cudaSuccess) e = col_attr<float, n, 1>();          \
+#define X(n)                                                     \
+    if (e == cudaSuccess) e = row_attr<float, n, 1>();           \
+    if (e == cudaSuccess) e = row_attr<float, n, 1, true>();     \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, false, 128>(); \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true, 128>();  \
+    if (e == cudaSuccess) e = col_attr<float, n, 1>();           \
     if (e == cudaSuccess) e = col_attr<float, n, 0, 128>();
     SHG_F32_VARIANT_SIZES(X)
 #undef X
@@ -110,17 +120,24 @@ cudaError_t attr_f32() {
 }
 
 size_t row_smem_f32(int nx, int v, int hx) {
-    const size_t slots = (v & kRowUmap) ? slot_bytes<float>() : 0;
+    const bool um = (v & kRowUmap) != 0;
     v &= ~kRowUmap;
+    if (v == 3) {
+        switch (nx) {
+#define X(n) case n: return um ? row_smem<float, n, 0, true, 128>(hx) : row_smem<float, n, 0, false, 128>(hx);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     if (v == 1) {
         switch (nx) {
-#define X(n) case n: return row_smem<float, n, 1>(hx) + slots;
+#define X(n) case n: return um ? row_smem<float, n, 1, true>(hx) : row_smem<float, n, 1>(hx);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
     }
     switch (nx) {
-#define X(n) case n: return row_smem<float, n>(hx) + slots;
+#define X(n) case n: return um ? row_smem<float, n, 0, true>(hx) : row_smem<float, n>(hx);
         SHG_F32_SIZES(X)
 #undef X
     }
