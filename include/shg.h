@@ -129,7 +129,12 @@ shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
  * [-t_ly/2, t_ly/2] x [0, L]; t_lx or t_ly <= 0 means the field window.
  * Copied into the plan together with its cumulative z-integral (Eq. 3,
  * trapezoid on the nodes).  tx, ty, tz >= 2.  dT_dev == NULL clears the map
- * (uniform temperature T_off).  FP32 plans without SHG_FLAG_NODE_SAMPLER also
+ * (uniform temperature T_off).  A map of the shape and extent already
+ * installed is rebuilt asynchronously: the copy from dT_dev and the table
+ * kernels are enqueued on `stream`, after the plan's last propagation, and
+ * the call returns without waiting (later propagations on any stream wait
+ * for them); dT_dev must stay unchanged until `stream` has reached them.
+ * Any other change synchronises.  FP32 plans without SHG_FLAG_NODE_SAMPLER also
  * keep every map layer bilinearly sampled at every field point (tz*ny*nx*8
  * bytes of device memory; the nodes are sampled in the passes instead when
  * that table would exceed 4 GiB). */

@@ -257,6 +257,7 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
     if (!(p->b.p1 > 0)) return SHG_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     SHG_CK(cudaStreamSynchronize(p->last_stream));
+    if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(st, p->ready, 0));
     const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
     const size_t npts = size_t(nx) * ny;
     const bool thermal = p->ttab != nullptr;

@@ -616,6 +616,9 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     ALLOC(p->red, 2 * kRedBlocks * sizeof(double));
     ALLOC(p->pw, 2 * sizeof(double));
     ALLOC(p->status, sizeof(int));
+    if ((e = cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(e, "cudaEventCreate");
     if (flags & SHG_FLAG_THERMAL) {
         const size_t nh = size_t(grid->hx) * grid->hy * grid->hz;
         ALLOC(p->Q, nh * sizeof(double));
@@ -656,6 +659,8 @@ static void plan_free(shg_plan* p) {
     shg::free_adjoint(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->done) cudaEventDestroy(p->done);
+    if (p->ready) cudaEventDestroy(p->ready);
     void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
                     p->tw,    p->ttab,   p->umap, p->tmap, p->desc, p->idesc, p->red, p->pw,
                     p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->theat_f,
@@ -696,9 +701,29 @@ shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
 shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int ty, int tz,
                                  double t_lx, double t_ly, shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // Fast path: a new map of the shape and extent already installed.  The
+    // tables are rebuilt in place, stream-ordered after the last propagation
+    // (event), with no host synchronisation and no descriptor change.
+    if (dT_dev != nullptr && p->ttab != nullptr && p->tx == tx && p->ty == ty && p->tz == tz &&
+        p->tlx == (t_lx > 0 ? t_lx : p->g.lx) && p->tly == (t_ly > 0 ? t_ly : p->g.ly)) {
+        const size_t n = size_t(tx) * ty * tz;
+        if (p->done_valid) SHG_CK(cudaStreamWaitEvent(s, p->done, 0));
+        if (dT_dev != p->tmap)
+            SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   s));
+        SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+        if (p->umap) SHG_CK(launch_upsample_map(p->desc, p->umap, p->g.nx, p->g.ny, tz, s));
+        SHG_CK(cudaEventRecord(p->ready, s));
+        p->ready_pending = true;
+        return SHG_OK;
+    }
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->ready_pending) {
+        SHG_CK(cudaEventSynchronize(p->ready));
+        p->ready_pending = false;
+    }
     if (dT_dev == nullptr) {
         if (p->ttab) {
             cudaFree(p->ttab);
@@ -781,8 +806,11 @@ shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh
 shg_status_t shg_propagate(shg_plan_t* p, shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(s, p->ready, 0));
     shg_status_t st = plan_forward(p, s);
     if (st != SHG_OK) return st;
+    SHG_CK(cudaEventRecord(p->done, s));
+    p->done_valid = true;
     p->has_result = true;
     p->batch_result = false;
     p->last_stream = s;
@@ -1017,8 +1045,10 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
             return r;
         }
     }
-    for (auto p : key)
+    for (auto p : key) {
         if (p->has_result) cudaStreamSynchronize(p->last_stream);
+        if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(st, p->ready, 0));
+    }
     if ((r = refresh_entry(ent, st)) != SHG_OK) return r;
     for (auto& g : ent->groups) {
         int hx = 0;
@@ -1065,6 +1095,8 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         p->last_stream = st;
         p->has_result = true;
         p->batch_result = true;
+        p->ready_pending = false;  // the batch waited for it and has completed
+        p->done_valid = false;
     }
     return finite ? SHG_OK : SHG_ERR_NONFINITE;
 }
@@ -1078,6 +1110,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
     for (auto p : key)
         if (!p) return SHG_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    for (int i = 0; i < n; ++i)
+        if (plans[i] && plans[i]->ready_pending) SHG_CK(cudaStreamWaitEvent(st, plans[i]->ready, 0));
     BatchEntry* ent = nullptr;
     shg_status_t r = build_entry(key, &ent);
     if (r != SHG_OK) return r;

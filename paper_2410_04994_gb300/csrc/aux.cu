@@ -213,11 +213,22 @@ __global__ void k_build_ttab(const float* __restrict__ dT, V* __restrict__ tt, i
     double c = 0;
     float prev = dT[col];
     tt[col] = mk<V>(prev, 0);
-    for (int l = 1; l < tz; ++l) {
-        const float cur = dT[l * plane + col];
-        c += 0.5 * dZ * (double(prev) + double(cur));
-        tt[l * plane + col] = mk<V>(cur, c);
-        prev = cur;
+    // layers in chunks of 16: the loads of a chunk are independent and in
+    // flight together; the sum runs in layer order
+    constexpr int K = 16;
+    for (int l0 = 1; l0 < tz; l0 += K) {
+        float cur[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (l0 + k < tz) cur[k] = dT[(l0 + k) * plane + col];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (l0 + k < tz) {
+                c += 0.5 * dZ * (double(prev) + double(cur[k]));
+                tt[(l0 + k) * plane + col] = mk<V>(cur[k], c);
+                prev = cur[k];
+            }
+        }
     }
 }
 

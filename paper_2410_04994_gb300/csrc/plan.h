@@ -65,6 +65,11 @@ struct shg_plan {
     bool has_result = false;
     bool batch_result = false;  // pw_host holds the last batch's powers
     cudaStream_t last_stream = nullptr;
+    // Stream ordering without host synchronisation: `done` is recorded after
+    // each propagation (its kernels read the map tables), `ready` after the
+    // table rebuild of an asynchronous shg_set_temperature.
+    cudaEvent_t done = nullptr, ready = nullptr;
+    bool done_valid = false, ready_pending = false;
 
     // heat grid
     double* Q = nullptr;      // [hz][hy][hx]

@@ -82,3 +82,30 @@ def test_batch_recaptures_when_a_new_map_changes_the_row_path():
         eta_ref, AF, AS = oracle_run(w)
         assert abs(e / eta_ref - 1) <= ETA_TOL, (w.name, e, eta_ref)
         assert rel_l2(p.fields()[1].cpu(), AS) <= FIELD_TOL
+
+
+def test_same_shape_map_update_is_stream_ordered():
+    """A second map of the same shape takes the asynchronous path of
+    shg_set_temperature. It is enqueued on stream b, after the propagation
+    still running on stream a. A propagation on a must wait for that rebuild,
+    and a batch on a must too; both see the new map."""
+    import paper_2410_04994_gb300 as pkg
+    w1 = W.depleted_absorbing(n=64, nz=12, tgrid=(9, 7, 5), p1=300.0, seed=0)
+    w2 = w1.with_(dT=W.depleted_absorbing(n=64, nz=12, tgrid=(9, 7, 5), p1=300.0, seed=3).dT)
+    a, b = torch.cuda.Stream(), torch.cuda.Stream()
+    plan = pkg.Plan(w1)
+    plan.set_temperature(torch.as_tensor(w1.dT), w1.t_lx, w1.t_ly, stream=a)
+    plan.propagate(stream=a)
+    m2 = torch.as_tensor(w2.dT).cuda()
+    torch.cuda.synchronize()
+    plan.set_temperature(m2, w2.t_lx, w2.t_ly, stream=b)
+    plan.propagate(stream=a)
+    eta, _, _ = plan.efficiency()
+    eta_ref, _, AS = oracle_run(w2)
+    assert abs(eta / eta_ref - 1) <= ETA_TOL, (eta, eta_ref, oracle_run(w1)[0])
+    # back to map 1 on b, then a batch on a
+    m1 = torch.as_tensor(w1.dT).cuda()
+    torch.cuda.synchronize()
+    plan.set_temperature(m1, w1.t_lx, w1.t_ly, stream=b)
+    e1 = pkg.shg_batch_submit([plan.handle], stream=a)[0]
+    assert abs(e1 / oracle_run(w1)[0] - 1) <= ETA_TOL
