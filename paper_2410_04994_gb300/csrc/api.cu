@@ -513,6 +513,7 @@ static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
 
 static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
     std::vector<shg_plan*> one{p};
+    PdlScope pdl(true);  // one grid group
     const void* tmaps = p->has_cmap ? p->cmap_dev : nullptr;
     auto body = [&](cudaStream_t s) {
         return enqueue_forward(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, p->idesc, 1, p->tw,
@@ -984,6 +985,7 @@ static shg_status_t enqueue_batch(BatchEntry* b, cudaStream_t st) {
     // fork the groups onto side streams so that instances of different grids
     // overlap, then join
     const int ng = int(b->groups.size());
+    PdlScope pdl(ng == 1);
     cudaEvent_t fork = b->ev.back();
     SHG_CK(cudaEventRecord(fork, st));
     for (int i = 0; i < ng; ++i) {

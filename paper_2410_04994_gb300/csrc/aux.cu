@@ -15,6 +15,8 @@ bool has_col_small_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
 
+thread_local bool pdl_enabled = false;
+
 bool has_fft_variant(bool fp64, int n) { return !fp64 && has_variant_f32(n); }
 bool has_col_small(bool fp64, int n) { return !fp64 && has_col_small_f32(n); }
 

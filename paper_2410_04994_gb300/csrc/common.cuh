@@ -137,6 +137,14 @@ template <class C> SHG_D void cp_async_stream(C* smem_dst, const C* gsrc, uint64
         asm volatile("cp.async.cg.shared.global.L2::cache_hint [%0], [%1], 16, %2;\n" ::"r"(s),
                      "l"(gsrc), "l"(pol));
 }
+// Programmatic dependent launch (sm_90 and later).  pdl_trigger lets the
+// next kernel of the stream be scheduled now (its prologue overlaps this
+// kernel's tail); pdl_wait blocks until the previous kernel of the stream has
+// completed and its writes are visible.  Both are no-ops for a kernel
+// launched without the programmatic-serialisation attribute.
+SHG_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+SHG_D void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 SHG_D void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 template <int N> SHG_D void cp_async_wait_group() {
     asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");

@@ -139,8 +139,17 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     // shared copies of the twiddles and of the row factors of both fields
     pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields + (UM ? slot_bytes<R, NTH>() : 0));
     pt<R>* pS = twS + NX;
+    pdl_trigger();
     {
+        // constant tables first: they do not depend on the previous kernel
         const InstDesc<R>& dg = descs[blockIdx.y];
+        stage_tables<R, NX>(twS, pS, tw, dg.px);
+        if (threadIdx.x == 0) dsh = dg;
+        if (threadIdx.x < 5) {
+            const int q = 4 * s - 2 + threadIdx.x;
+            zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
+        }
+        pdl_wait();  // the fields are the previous pass's output
         C* rowF = dg.field + size_t(y) * NX;
         C* rowS = dg.field + (size_t(ny) + y) * NX;
         if (active) {
@@ -149,12 +158,6 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
                 cp_async(&sF[pidx<R>(t + T * m)], &rowF[t + T * m]);
                 cp_async(&sS[pidx<R>(t + T * m)], &rowS[t + T * m]);
             }
-        }
-        stage_tables<R, NX>(twS, pS, tw, dg.px);
-        if (threadIdx.x == 0) dsh = dg;
-        if (threadIdx.x < 5) {
-            const int q = 4 * s - 2 + threadIdx.x;
-            zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
     }
     const bool dep = descs[blockIdx.y].Q != nullptr;
@@ -350,6 +353,9 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = blockIdx.x * TILE + c;
     const bool active = x < nx;
+    pdl_trigger();
+    stage_tables<R, NY>(twS, pS, tw, descs[blockIdx.y].py);  // independent of the previous pass
+    pdl_wait();
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
         if (active) {
@@ -359,7 +365,6 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             for (int m = 0; m < E; ++m)
                 cp_async(&sb[pidx<R>(t + T * m)], col + size_t(t + T * m) * nx);
         }
-        if (f == 0) stage_tables<R, NY>(twS, pS, tw, descs[blockIdx.y].py);
         cp_async_commit();
     }
 #pragma unroll 1
@@ -416,12 +421,15 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     uint64_t* bar = reinterpret_cast<uint64_t*>(pS + 2 * NY);
     const InstDesc<float>& d = descs[blockIdx.y];
     const int x0 = blockIdx.x * TILE;
+    pdl_trigger();
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_init_fence();
     }
+    stage_tables<float, NY>(twS, pS, tw, d.py);  // independent of the previous pass
     __syncthreads();
+    pdl_wait();
     if (threadIdx.x == 0) {
         // one barrier per field, so that field 0 is transformed while field 1 lands
         const CUtensorMap* tm = tmaps + blockIdx.y;
@@ -433,7 +441,6 @@ __global__ void __launch_bounds__(kPassThreads, 2)
                 tma_load_3d(stage + (size_t(f) * NY + yb) * TILE, tm, x0, yb, f, &bar[f]);
         }
     }
-    stage_tables<float, NY>(twS, pS, tw, d.py);
     cp_async_wait_all();
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = x0 + c;

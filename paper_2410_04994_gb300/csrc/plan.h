@@ -3,6 +3,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -148,6 +149,18 @@ cudaError_t setup_pass_attributes();
 // descriptor (node table, map geometry): tz layers of ny x nx (dT, C).
 cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, int tz,
                                 cudaStream_t st);
+
+// Whether the pass launches of the calling thread use programmatic dependent
+// launch; set per enqueue by pdl_scope (SHG_PDL=0|1 overrides the choice).
+extern thread_local bool pdl_enabled;
+struct PdlScope {
+    bool prev;
+    explicit PdlScope(bool single_group) : prev(pdl_enabled) {
+        const char* v = getenv("SHG_PDL");
+        pdl_enabled = (v && (v[0] == '0' || v[0] == '1')) ? v[0] == '1' : single_group;
+    }
+    ~PdlScope() { pdl_enabled = prev; }
+};
 
 // Enqueue the whole forward propagation of instances sharing one grid.
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
