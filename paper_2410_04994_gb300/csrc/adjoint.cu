@@ -34,6 +34,12 @@ struct Adjoint {
     float* gdT = nullptr;      // [tz][ty][tx]
     int ntz = 0, nty = 0, ntx = 0;
     bool have_forward = false;
+    // the reverse sweep (segment recomputation and transposed passes) as one
+    // CUDA graph, reused while the buffers and kernel flavours it baked in hold
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t sweep = nullptr;
+    const void* sweep_key[2] = {nullptr, nullptr};
+    int sweep_vr = -1, sweep_vc = -1;
 };
 
 void free_adjoint(shg_plan* p) {
@@ -43,6 +49,8 @@ void free_adjoint(shg_plan* p) {
                     a->descW, a->descL, a->nodes, a->gdT};
     for (void* b : bufs)
         if (b) cudaFree(b);
+    if (a->sweep) cudaGraphExecDestroy(a->sweep);
+    if (a->cap) cudaStreamDestroy(a->cap);
     delete a;
     p->adj = nullptr;
 }
@@ -63,6 +71,7 @@ shg_status_t adjoint_alloc(shg_plan* p) {
     SHG_CK(cudaMalloc((void**)&a->red, 8 * 1024 * sizeof(double)));
     SHG_CK(cudaMalloc(&a->descW, desc));
     SHG_CK(cudaMalloc(&a->descL, desc));
+    SHG_CK(cudaStreamCreateWithFlags(&a->cap, cudaStreamNonBlocking));
     return SHG_OK;
 }
 
@@ -292,33 +301,60 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
                                                static_cast<float2*>(a->lam), npts, scale);
     SHG_CK(cudaGetLastError());
     AdjAcc acc{a->Gc, a->Gt, a->Gs};
-    std::vector<shg_plan*> none;
+    // the same FFT shapes as the forward sweep, to replay its states
+    const int vr = fft_variant(p->fp64, nx, 0, row_umap_bit({p})) | row_umap_bit({p});
+    const int vc = fft_variant(p->fp64, ny, 1);
     // segments from the last to the first
-    for (int c = a->nck - 1; c >= 0; --c) {
-        const int sb = c * a->K, se = std::min(sb + a->K, nz + 1);
-        if (sb > nz) continue;
-        SHG_CK(cudaMemcpyAsync(a->work, static_cast<char*>(a->ckpt) + size_t(c) * a->sbytes,
-                               a->sbytes, cudaMemcpyDeviceToDevice, st));
-        for (int s = sb; s < se; ++s) {
-            SHG_CK(cudaMemcpyAsync(static_cast<char*>(a->seg) + size_t(s - sb) * a->sbytes,
-                                   a->work, a->sbytes, cudaMemcpyDeviceToDevice, st));
-            if (s + 1 < se) {
-                // the same FFT shapes as the forward sweep, to replay its states
-                SHG_CK(launch_row(p->fp64, nx, a->descW, 1, ny, nz, s, p->tw, 0, st,
-                                  fft_variant(p->fp64, nx, 0, row_umap_bit({p})) |
-                                      row_umap_bit({p})));
-                if (s < nz)
-                    SHG_CK(launch_col(p->fp64, ny, a->descW, 1, nx, p->tw, st,
-                                      fft_variant(p->fp64, ny, 1)));
+    auto reverse_sweep = [&](cudaStream_t q) -> shg_status_t {
+        for (int c = a->nck - 1; c >= 0; --c) {
+            const int sb = c * a->K, se = std::min(sb + a->K, nz + 1);
+            if (sb > nz) continue;
+            SHG_CK(cudaMemcpyAsync(a->work, static_cast<char*>(a->ckpt) + size_t(c) * a->sbytes,
+                                   a->sbytes, cudaMemcpyDeviceToDevice, q));
+            for (int s = sb; s < se; ++s) {
+                SHG_CK(cudaMemcpyAsync(static_cast<char*>(a->seg) + size_t(s - sb) * a->sbytes,
+                                       a->work, a->sbytes, cudaMemcpyDeviceToDevice, q));
+                if (s + 1 < se) {
+                    SHG_CK(launch_row(p->fp64, nx, a->descW, 1, ny, nz, s, p->tw, 0, q, vr));
+                    if (s < nz) SHG_CK(launch_col(p->fp64, ny, a->descW, 1, nx, p->tw, q, vc));
+                }
+            }
+            for (int s = se - 1; s >= sb; --s) {
+                if (s < nz) SHG_CK(launch_col(p->fp64, ny, a->descL, 1, nx, p->tw, q));
+                const void* Y = static_cast<char*>(a->seg) + size_t(s - sb) * a->sbytes;
+                SHG_CK(p->fp64 ? row_adj_f64(nx, a->descL, Y, acc, ny, nz, s, p->tw, q)
+                               : row_adj_f32(nx, a->descL, Y, acc, ny, nz, s, p->tw, q));
             }
         }
-        for (int s = se - 1; s >= sb; --s) {
-            if (s < nz) SHG_CK(launch_col(p->fp64, ny, a->descL, 1, nx, p->tw, st));
-            const void* Y = static_cast<char*>(a->seg) + size_t(s - sb) * a->sbytes;
-            SHG_CK(p->fp64 ? row_adj_f64(nx, a->descL, Y, acc, ny, nz, s, p->tw, st)
-                           : row_adj_f32(nx, a->descL, Y, acc, ny, nz, s, p->tw, st));
-        }
+        return SHG_OK;
+    };
+    // captured once into a graph (2-3 small operations per step would
+    // otherwise be launched one by one from the host)
+    if (a->sweep && (a->sweep_key[0] != a->Gc || a->sweep_key[1] != a->Gt ||
+                     a->sweep_vr != vr || a->sweep_vc != vc)) {
+        cudaGraphExecDestroy(a->sweep);
+        a->sweep = nullptr;
     }
+    if (!a->sweep) {
+        PdlScope pdl(true);  // one instance
+        cudaGraph_t graph = nullptr;
+        SHG_CK(cudaStreamBeginCapture(a->cap, cudaStreamCaptureModeThreadLocal));
+        const shg_status_t r = reverse_sweep(a->cap);
+        const cudaError_t e = cudaStreamEndCapture(a->cap, &graph);
+        if (r != SHG_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "adjoint capture");
+        const cudaError_t e2 = cudaGraphInstantiate(&a->sweep, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e2 != cudaSuccess) return cuda_fail(e2, "adjoint graph");
+        a->sweep_key[0] = a->Gc;
+        a->sweep_key[1] = a->Gt;
+        a->sweep_vr = vr;
+        a->sweep_vc = vc;
+    }
+    SHG_CK(cudaGraphLaunch(a->sweep, st));
     // gradients of the initial pump
     double gw = 0, gz = 0;
     if (!p->custom_init) {

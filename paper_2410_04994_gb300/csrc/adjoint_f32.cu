@@ -4,18 +4,21 @@
 
 namespace shg {
 
+// The adjoint sweep runs one instance, so its row kernel uses small CTAs
+// (NTH = max(64, T) threads, a few rows each) to spread the rows over more SMs.
 template <class R, int N>
 static cudaError_t row_adj_launch(const void* dl, const void* Y, AdjAcc acc, int ny, int nz,
                                   int s, const void* tw, cudaStream_t st) {
-    using G = RowGeom<R, N>;
+    constexpr int T = FftCfg<R, N>::T, NTH = T > 64 ? T : 64;
+    using G = RowGeom<R, N, 0, NTH>;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = allow_max_dyn_smem(k_row_adj<R, N>);
+        cudaError_t e = allow_max_dyn_smem(k_row_adj<R, N, NTH>);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, 1);
-    k_row_adj<R, N><<<grid, kPassThreads, G::fields + G::tables, st>>>(
+    k_row_adj<R, N, NTH><<<grid, NTH, G::fields + G::tables, st>>>(
         static_cast<const InstDesc<R>*>(dl), static_cast<const cx<R>*>(Y), acc, ny, nz, s,
         static_cast<const pt<R>*>(tw));
     return cudaGetLastError();

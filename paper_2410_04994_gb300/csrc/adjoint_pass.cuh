@@ -5,15 +5,15 @@
 
 namespace shg {
 
-// grid = (ceil(ny / ROWS), 1); block = 256.  `dl` describes the adjoint field
+// grid = (ceil(ny / ROWS), 1); block = NTH.  `dl` describes the adjoint field
 // (its K-space tables are the conjugates of the forward ones); Y is the state
 // that entered the forward row pass R(s).  The adjoint is updated in place.
-template <class R, int NX>
-__global__ void __launch_bounds__(kPassThreads, 2)
+template <class R, int NX, int NTH = kPassThreads>
+__global__ void __launch_bounds__(NTH, 2 * (kPassThreads / NTH))
     k_row_adj(const InstDesc<R>* __restrict__ dl, const cx<R>* __restrict__ Y, AdjAcc acc,
               int ny, int nz, int s, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = RowGeom<R, NX>;
+    using G = RowGeom<R, NX, 0, NTH>;
     constexpr int E = FftCfg<R, NX>::E, T = G::T, ROWS = G::ROWS, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<R> dsh;
