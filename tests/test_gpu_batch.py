@@ -63,7 +63,7 @@ def test_batch_rejects_bad_input():
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("n", [64, 128])
+@pytest.mark.parametrize("n", [64, 128, 256])
 def test_sweep_instances_full_length(n):
     """The first instance of a size group of the 384-instance sweep (seeded
     map, losses, oven offset), propagated inside the full-size mixed batch at
@@ -130,3 +130,19 @@ def test_tuner_cache_file_records_and_replays_decisions(tmp_path):
     e1, e2 = json.loads(out1.strip().splitlines()[-1]), json.loads(out2.strip().splitlines()[-1])
     for a, b in zip(e1, e2):
         assert abs(a / b - 1) < 1e-5
+
+
+@pytest.mark.slow
+def test_full_sweep_power_budget_of_every_instance():
+    """All 384 instances of the benchmark sweep at nz = 2000, in the batch the
+    benchmark times: every eta is finite and in (0, 1), and no instance ends
+    with more power than it started with (losses only remove power; the
+    coupling conserves it)."""
+    import paper_2410_04994_gb300 as pkg
+    insts = W.sweep_instances()
+    plans = _plans(insts)
+    etas = pkg.shg_batch_submit([p.handle for p in plans])
+    for p, w, e in zip(plans, insts, etas):
+        eta, p_f, p_sh = p.efficiency()
+        assert eta == e and 0 < e < 1
+        assert p_f + p_sh <= w.p1 * (1 + 1e-5), (w.name, p_f, p_sh, w.p1)
