@@ -141,6 +141,17 @@ shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
 shg_status_t shg_set_temperature(shg_plan_t *plan, const float *dT_dev, int tx, int ty,
                                  int tz, double t_lx, double t_ly, shg_stream_t stream);
 
+/* shg_set_temperature for n plans at once, with maps of one shape
+ * (dT_devs[k] for plans[k], extents t_lx[k] x t_ly[k]).  The plans whose
+ * installed map already has that shape and extent are rebuilt by a few
+ * launches for all of them (stream-ordered, no host synchronisation, as the
+ * single-plan fast path); the others are set one by one.  The host arrays
+ * may be reused once the call returns; the maps must stay unchanged until
+ * `stream` has reached the rebuild. */
+shg_status_t shg_set_temperature_batch(shg_plan_t *const *plans, int n, const float *const *dT_devs,
+                                       int tx, int ty, int tz, const double *t_lx,
+                                       const double *t_ly, shg_stream_t stream);
+
 /* Use the given fields (device, [ny][nx], the plan's precision) as the state
  * at z = 0 instead of the Gaussian pump of Eq. (6) and a zero SH.  Either
  * pointer may be NULL (zero field). */

@@ -69,6 +69,8 @@ _SIGS = {
                         ctypes.POINTER(shg_beams_t), _I, ctypes.POINTER(_P)],
     "shg_plan_destroy": [_P],
     "shg_set_wait_limit": [_P, ctypes.c_uint],
+    "shg_set_temperature_batch": [ctypes.POINTER(_P), _I, ctypes.POINTER(_P), _I, _I, _I, _DP,
+                                  _DP, _P],
     "shg_set_beams": [_P, ctypes.POINTER(shg_beams_t)],
     "shg_set_temperature": [_P, _P, _I, _I, _I, _D, _D, _P],
     "shg_set_fields": [_P, _P, _P, _P],
@@ -165,6 +167,20 @@ def shg_set_temperature(plan: int, dT, t_lx: float = 0.0, t_ly: float = 0.0, str
     tz, ty, tx = dT.shape
     _check(_lib().shg_set_temperature(plan, _ptr(dT), tx, ty, tz, float(t_lx), float(t_ly),
                                       _stream(stream)), "shg_set_temperature")
+
+
+def shg_set_temperature_batch(plans: Sequence[int], maps, t_lx, t_ly, stream=None) -> None:
+    """maps: contiguous float32 CUDA tensors [tz][ty][tx] of one shape, one per plan."""
+    n = len(plans)
+    if n == 0 or len(maps) != n:
+        raise ValueError("one map per plan")
+    tz, ty, tx = maps[0].shape
+    arr = (_P * n)(*plans)
+    ptrs = (_P * n)(*[_ptr(m) for m in maps])
+    lx = (_D * n)(*[float(v) for v in t_lx])
+    ly = (_D * n)(*[float(v) for v in t_ly])
+    _check(_lib().shg_set_temperature_batch(arr, n, ptrs, tx, ty, tz, lx, ly, _stream(stream)),
+           "shg_set_temperature_batch")
 
 
 def shg_set_fields(plan: int, a_f=None, a_sh=None, stream=None) -> None:

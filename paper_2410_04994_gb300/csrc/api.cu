@@ -781,6 +781,79 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
     return SHG_OK;
 }
 
+shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const float* const* dT_devs,
+                                       int tx, int ty, int tz, const double* t_lx,
+                                       const double* t_ly, shg_stream_t stream) {
+    if (!plans || n <= 0 || !dT_devs || !t_lx || !t_ly) return SHG_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // plans whose installed map has this shape and extent are rebuilt together;
+    // the others take the single-plan path (which may allocate and synchronise)
+    std::vector<int> fast;
+    for (int k = 0; k < n; ++k) {
+        shg_plan* p = plans[k];
+        if (!p || !dT_devs[k]) return SHG_ERR_INVALID_ARG;
+        const bool same = p->ttab != nullptr && p->tx == tx && p->ty == ty && p->tz == tz &&
+                          p->tlx == (t_lx[k] > 0 ? t_lx[k] : p->g.lx) &&
+                          p->tly == (t_ly[k] > 0 ? t_ly[k] : p->g.ly);
+        if (same) {
+            fast.push_back(k);
+        } else {
+            const shg_status_t r = shg_set_temperature(p, dT_devs[k], tx, ty, tz, t_lx[k],
+                                                       t_ly[k], stream);
+            if (r != SHG_OK) return r;
+        }
+    }
+    if (fast.empty()) return SHG_OK;
+    for (int k : fast)
+        if (plans[k]->done_valid) SHG_CK(cudaStreamWaitEvent(s, plans[k]->done, 0));
+    // (dT, C) tables, one launch per precision
+    for (int prec = 0; prec < 2; ++prec) {
+        std::vector<TtabJob> jobs;
+        for (int k : fast) {
+            shg_plan* p = plans[k];
+            if (p->fp64 != (prec == 1)) continue;
+            jobs.push_back(TtabJob{dT_devs[k], p->tmap, p->ttab, p->c.L / (tz - 1)});
+        }
+        if (jobs.empty()) continue;
+        void* dj = nullptr;
+        SHG_CK(cudaMallocAsync(&dj, jobs.size() * sizeof(TtabJob), s));
+        SHG_CK(cudaMemcpyAsync(dj, jobs.data(), jobs.size() * sizeof(TtabJob),
+                               cudaMemcpyHostToDevice, s));
+        SHG_CK(launch_build_ttab_batch(prec == 1, static_cast<const TtabJob*>(dj), int(jobs.size()),
+                                       tx, ty, tz, s));
+        SHG_CK(cudaFreeAsync(dj, s));
+    }
+    // per-point tables, one launch per grid
+    std::map<std::pair<int, int>, std::vector<int>> grids;
+    for (int k : fast)
+        if (plans[k]->umap) grids[{plans[k]->g.nx, plans[k]->g.ny}].push_back(k);
+    for (auto& kv : grids) {
+        const std::vector<int>& ks = kv.second;
+        const int chunk = std::max(1, 65535 / tz);
+        for (size_t b = 0; b < ks.size(); b += chunk) {
+            const size_t m = std::min(ks.size() - b, size_t(chunk));
+            std::vector<const void*> ptrs(2 * m);
+            for (size_t i = 0; i < m; ++i) {
+                ptrs[i] = plans[ks[b + i]]->desc;
+                ptrs[m + i] = plans[ks[b + i]]->umap;
+            }
+            void* dp = nullptr;
+            SHG_CK(cudaMallocAsync(&dp, ptrs.size() * sizeof(void*), s));
+            SHG_CK(cudaMemcpyAsync(dp, ptrs.data(), ptrs.size() * sizeof(void*),
+                                   cudaMemcpyHostToDevice, s));
+            void* const* dv = static_cast<void* const*>(dp);
+            SHG_CK(launch_upsample_map_batch(reinterpret_cast<const void* const*>(dv), dv + m,
+                                             int(m), kv.first.first, kv.first.second, tz, s));
+            SHG_CK(cudaFreeAsync(dp, s));
+        }
+    }
+    for (int k : fast) {
+        SHG_CK(cudaEventRecord(plans[k]->ready, s));
+        plans[k]->ready_pending = true;
+    }
+    return SHG_OK;
+}
+
 shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh_dev,
                             shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;

@@ -234,6 +234,47 @@ __global__ void k_build_ttab(const float* __restrict__ dT, V* __restrict__ tt, i
     }
 }
 
+// The same for many maps of one shape at once: job k (blockIdx.y) builds
+// jobs[k].tt from jobs[k].src and keeps a copy of the map in jobs[k].copy.
+template <class V>
+__global__ void k_build_ttab_batch(const TtabJob* __restrict__ jobs, int tx, int ty, int tz) {
+    const TtabJob j = jobs[blockIdx.y];
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= tx * ty) return;
+    const size_t plane = size_t(tx) * ty;
+    V* tt = static_cast<V*>(j.tt);
+    double c = 0;
+    float prev = j.src[col];
+    j.copy[col] = prev;
+    tt[col] = mk<V>(prev, 0);
+    constexpr int K = 16;
+    for (int l0 = 1; l0 < tz; l0 += K) {
+        float cur[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k)
+            if (l0 + k < tz) cur[k] = j.src[(l0 + k) * plane + col];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            if (l0 + k < tz) {
+                c += 0.5 * j.dZ * (double(prev) + double(cur[k]));
+                tt[(l0 + k) * plane + col] = mk<V>(cur[k], c);
+                j.copy[(l0 + k) * plane + col] = cur[k];
+                prev = cur[k];
+            }
+        }
+    }
+}
+
+cudaError_t launch_build_ttab_batch(bool fp64, const TtabJob* jobs, int njobs, int tx, int ty,
+                                    int tz, cudaStream_t st) {
+    dim3 grid((tx * ty + 127) / 128, njobs);
+    if (fp64)
+        k_build_ttab_batch<double2><<<grid, 128, 0, st>>>(jobs, tx, ty, tz);
+    else
+        k_build_ttab_batch<float2><<<grid, 128, 0, st>>>(jobs, tx, ty, tz);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
                               double dZ, cudaStream_t st) {
     const int cols = tx * ty;

@@ -95,6 +95,16 @@ cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, in
     return cudaGetLastError();
 }
 
+cudaError_t launch_upsample_map_batch(const void* const* descs, void* const* umaps, int n, int nx,
+                                      int ny, int tz, cudaStream_t st) {
+    if (size_t(n) * tz > 65535) return cudaErrorInvalidValue;
+    dim3 grid((nx + 255) / 256, ny, n * tz);
+    k_upsample_map_batch<float><<<grid, 256, 0, st>>>(
+        reinterpret_cast<const InstDesc<float>* const*>(descs),
+        reinterpret_cast<cx<float>* const*>(umaps), nx, ny, tz);
+    return cudaGetLastError();
+}
+
 cudaError_t attr_f32() {
     cudaError_t e = cudaSuccess;
 #define X(n)                                                    \

@@ -144,6 +144,19 @@ cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, i
                          int ny, cudaStream_t st);
 cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
                               double dZ, cudaStream_t st);
+// One map update of a batched temperature update (device-resident array).
+struct TtabJob {
+    const float* src;  // the new map [tz][ty][tx]
+    float* copy;       // the plan's copy of it
+    void* tt;          // the plan's (dT, C) table
+    double dZ;         // layer spacing L / (tz - 1)
+};
+cudaError_t launch_build_ttab_batch(bool fp64, const TtabJob* jobs, int njobs, int tx, int ty,
+                                    int tz, cudaStream_t st);
+// Per-point tables of several FP32 plans of one grid: descs[k] and umaps[k]
+// are device arrays of the plans' descriptor and table pointers.
+cudaError_t launch_upsample_map_batch(const void* const* descs, void* const* umaps, int n, int nx,
+                                      int ny, int tz, cudaStream_t st);
 cudaError_t setup_pass_attributes();
 // Fill the per-point temperature table of an FP32 plan from its uploaded
 // descriptor (node table, map geometry): tz layers of ny x nx (dT, C).

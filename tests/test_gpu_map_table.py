@@ -109,3 +109,28 @@ def test_same_shape_map_update_is_stream_ordered():
     plan.set_temperature(m1, w1.t_lx, w1.t_ly, stream=b)
     e1 = pkg.shg_batch_submit([plan.handle], stream=a)[0]
     assert abs(e1 / oracle_run(w1)[0] - 1) <= ETA_TOL
+
+
+def test_batched_map_update_equals_single_updates():
+    """shg_set_temperature_batch over a mixed set: two grids, and one plan
+    without a map yet, which takes the single-plan path. Afterwards every plan
+    propagates bit-identically to the same plan updated by
+    shg_set_temperature."""
+    import paper_2410_04994_gb300 as pkg
+    base = W.sweep_instances(nz=12, groups=((64, 3), (128, 2)), tgrid=(9, 9, 12))
+    new = W.sweep_instances(nz=12, groups=((64, 3), (128, 2)), tgrid=(9, 9, 12), seed=7)
+    pa, pb = [pkg.Plan(w) for w in base], [pkg.Plan(w) for w in base]
+    for pl in (pa, pb):
+        for p, w in zip(pl[1:], base[1:]):     # plan 0 starts without a map
+            p.set_temperature(torch.as_tensor(w.dT), w.t_lx, w.t_ly)
+        pkg.shg_batch_submit([p.handle for p in pl])
+    maps = [torch.as_tensor(w.dT).cuda() for w in new]
+    pkg.shg_set_temperature_batch([p.handle for p in pa], maps, [w.t_lx for w in new],
+                                  [w.t_ly for w in new])
+    for p, m, w in zip(pb, maps, new):
+        p.set_temperature(m, w.t_lx, w.t_ly)
+    ea = pkg.shg_batch_submit([p.handle for p in pa])
+    eb = pkg.shg_batch_submit([p.handle for p in pb])
+    assert ea == eb
+    # the plans keep their beams (from `base`); only the maps changed
+    assert abs(ea[3] / oracle_run(base[3].with_(dT=new[3].dT))[0] - 1) <= ETA_TOL
