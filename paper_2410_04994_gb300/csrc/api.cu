@@ -674,6 +674,7 @@ static void plan_free(shg_plan* p) {
 shg_status_t shg_plan_destroy(shg_plan_t* p) {
     if (!p) return SHG_OK;
     if (p->has_result || p->last_stream) cudaStreamSynchronize(p->last_stream);
+    if (p->ready_pending) cudaEventSynchronize(p->ready);  // a table rebuild in flight
     plan_free(p);
     return SHG_OK;
 }
