@@ -1,7 +1,7 @@
 """FP64 CPU oracle of the split-step Fourier SHG propagation.
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
-CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
+CPU-baseline and reference legs of ``bench.py`` may import this package.  It shares no code
 with the CUDA path: plain PyTorch CPU ops in float64 / complex128, one library
 FFT (``torch.fft``) as a step, no blocking, fusion or reordering.
 
@@ -9,7 +9,8 @@ The discrete map it computes (all SI units):
 
 * Coupled-wave equations, Eqs. (1)-(2), in the operator form of Eq. (11):
   the nonlinear operator N is applied pointwise, the linear operator L
-  (diffraction + linear absorption) in K-space, App. A Eqs. (A.1)-(A.5).
+  (diffraction + linear absorption, and the walk-off term of Sec. 6 / App. B
+  when its angles are non-zero) in K-space, App. A Eqs. (A.1)-(A.5).
 * Symmetric split step, Eqs. (14)-(15): every z-step of length dz is
   N(dz/2) -> L(dz) -> N(dz/2).  Each N(dz/2) is one classical RK4 step of
   size h = dz/2 (Sec. 3.1 names RK4 for the nonlinear part); the first half
