@@ -302,8 +302,8 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
     SHG_CK(cudaGetLastError());
     AdjAcc acc{a->Gc, a->Gt, a->Gs};
     // the same FFT shapes as the forward sweep, to replay its states
-    const int vr = fft_variant(p->fp64, nx, 0, row_umap_bit({p})) | row_umap_bit({p});
-    const int vc = fft_variant(p->fp64, ny, 1);
+    const int vr = fft_variant(p->fp64, nx, 0, row_umap_bit({p}), 1) | row_umap_bit({p});
+    const int vc = fft_variant(p->fp64, ny, 1, 0, 1);
     // segments from the last to the first
     auto reverse_sweep = [&](cudaStream_t q) -> shg_status_t {
         for (int c = a->nck - 1; c >= 0; --c) {

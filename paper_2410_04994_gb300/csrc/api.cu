@@ -322,8 +322,9 @@ static bool g_cache_loaded = false;
 
 // Optional persistent tuner decisions: with SHG_TUNE_CACHE=<file>, decisions
 // found in the file are used instead of timing, and new decisions are
-// appended ("fp64 n pass flavour" per line; pass 0 row, 1 column, 2 row with
-// the per-point table).  Caller holds g_tune_mu.
+// appended ("fp64 n key flavour" per line; key as tune_key: 0 row, 1 column,
+// 2 row with the per-point table, +4 for groups of few instances).  Caller
+// holds g_tune_mu.
 static void load_tune_cache() {
     if (g_cache_loaded) return;
     g_cache_loaded = true;
@@ -333,7 +334,7 @@ static void load_tune_cache() {
     if (!f) return;
     int fp64, n, pass, v;
     while (fscanf(f, "%d %d %d %d", &fp64, &n, &pass, &v) == 4)
-        if (v >= 0 && v <= 3) g_tuned.emplace(std::make_tuple(fp64 != 0, n, pass), v);
+        if (v >= 0 && v <= 4) g_tuned.emplace(std::make_tuple(fp64 != 0, n, pass), v);
     fclose(f);
 }
 static void save_tune_decision(bool fp64, int n, int pass, int v) {
@@ -347,7 +348,7 @@ static void save_tune_decision(bool fp64, int n, int pass, int v) {
 
 static int forced_variant() {
     const char* f = getenv("SHG_FFT_VARIANT");
-    return (f && f[0] >= '0' && f[0] <= '3' && f[1] == 0) ? f[0] - '0' : -1;
+    return (f && f[0] >= '0' && f[0] <= '4' && f[1] == 0) ? f[0] - '0' : -1;
 }
 
 int row_umap_bit(const std::vector<shg_plan*>& plans) {
@@ -360,6 +361,8 @@ int row_umap_bit(const std::vector<shg_plan*>& plans) {
     return any ? kRowUmap : 0;
 }
 
+static_assert(kRowUmap > 4, "the table-path bit must not collide with a flavour number");
+
 // Candidate flavours of a pass for a length: the default shape, the
 // alternative shape, the default shape in 128-thread CTAs and (column pass)
 // the TMA-staged kernel.
@@ -367,21 +370,32 @@ static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     std::vector<int> c{0};
     if (has_fft_variant(fp64, n)) c.push_back(1);
     if (pass == 1 && tmaps && col_tma_tile(fp64, n) > 0) c.push_back(2);
+    // flavour 4 (64-thread CTAs) is not a candidate: its launches time well
+    // alone, but whole single-instance propagations (graph, programmatic
+    // launches) measured slower with it; SHG_FFT_VARIANT=4 still selects it
     if (has_col_small(fp64, n)) c.push_back(3);
     return c;
 }
 
-int fft_variant(bool fp64, int n, int pass, int row_bits) {
+// Tuner key of a pass: 0 row, 1 column, 2 row with the per-point table; +4
+// for groups of at most kFewInstances instances (decided separately, since
+// small CTAs pay off there and not in large batches).
+constexpr int kFewInstances = 8;
+static int tune_key(int pass, int row_bits, int ninst) {
+    return pass + (pass == 0 && row_bits ? 2 : 0) + (ninst <= kFewInstances ? 4 : 0);
+}
+
+int fft_variant(bool fp64, int n, int pass, int row_bits, int ninst) {
     const int f = forced_variant();
     if (f >= 0) {
         if (f == 1 && !has_fft_variant(fp64, n)) return 0;
         if (f == 2 && pass == 0) return 0;
-        if (f == 3 && !has_col_small(fp64, n)) return 0;
+        if (f >= 3 && !has_col_small(fp64, n)) return 0;
         return f;
     }
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_tune_cache();
-    auto it = g_tuned.find(std::make_tuple(fp64, n, pass + (row_bits ? 2 : 0)));
+    auto it = g_tuned.find(std::make_tuple(fp64, n, tune_key(pass, row_bits, ninst)));
     return it == g_tuned.end() ? 0 : it->second;
 }
 
@@ -401,8 +415,7 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             load_tune_cache();
-            if (g_tuned.count(std::make_tuple(fp64, n, pass + (pass == 0 && row_bits ? 2 : 0))))
-                continue;
+            if (g_tuned.count(std::make_tuple(fp64, n, tune_key(pass, row_bits, ninst)))) continue;
         }
         cudaEvent_t e0, e1;
         SHG_CK(cudaEventCreate(&e0));
@@ -441,7 +454,7 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        const int key = pass + (pass == 0 && row_bits ? 2 : 0);
+        const int key = tune_key(pass, row_bits, ninst);
         g_tuned[std::make_tuple(fp64, n, key)] = best_v;
         save_tune_decision(fp64, n, key, best_v);
     }
@@ -470,7 +483,8 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
     const int rb = row_umap_bit(plans);
-    const int vr = fft_variant(fp64, nx, 0, rb) | rb, vc = fft_variant(fp64, ny, 1);
+    const int vr = fft_variant(fp64, nx, 0, rb, ninst) | rb;
+    const int vc = fft_variant(fp64, ny, 1, 0, ninst);
     for (int s = 0; s <= nz; ++s) {
         for (shg_plan* p : plans) {
             shg_status_t r = adjoint_checkpoint(p, s, st);
@@ -582,7 +596,7 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
             !(crystal->wy > 0) || !(crystal->kappa_th > 0))
             return SHG_ERR_INVALID_ARG;
         // the row pass bins the heat deposit per CTA in shared memory
-        for (int v : {0, 1, 3, kRowUmap, 1 | kRowUmap, 3 | kRowUmap})
+        for (int v : {0, 1, 3, 4, kRowUmap, 1 | kRowUmap, 3 | kRowUmap, 4 | kRowUmap})
             if (row_pass_smem(fp64, grid->nx, grid->hx, v) > 223 * 1024)
                 return SHG_ERR_UNSUPPORTED_GRID;
     }
@@ -1224,13 +1238,13 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             }
             e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
                            g.plans[0]->tw, hx, st,
-                           fft_variant(g.fp64, g.nx, 0, row_umap_bit(g.plans)) |
+                           fft_variant(g.fp64, g.nx, 0, row_umap_bit(g.plans), int(g.plans.size())) |
                                row_umap_bit(g.plans));
             cudaEventRecord(E[1], st);
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);
                 e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st,
-                               fft_variant(g.fp64, g.ny, 1), g.tmaps);
+                               fft_variant(g.fp64, g.ny, 1, 0, int(g.plans.size())), g.tmaps);
                 cudaEventRecord(E[3], st);
             }
         }

@@ -77,7 +77,7 @@ template <class C> SHG_HD C cconj(C a) { return mk<C>(a.x, -a.y); }
 // ------------------------------------------------------ per-instance ----
 // Everything one pass needs about one instance; built on the host by the plan.
 // Launch-variant bit of the row pass: read the per-point temperature table.
-constexpr int kRowUmap = 4;
+constexpr int kRowUmap = 8;  // above every flavour number (0-4)
 
 template <class R> struct InstDesc {
     cx<R>* field;          // [2][ny][nx]: A_F then A_SH

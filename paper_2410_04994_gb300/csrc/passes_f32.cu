@@ -12,14 +12,17 @@ namespace shg {
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
 bool has_col_small_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
-// v: flavour (0, 1: FFT shape; 3: shape 0 in 128-thread CTAs), plus kRowUmap
+// v: flavour (0, 1: FFT shape; 3, 4: shape 0 in 128- or 64-thread CTAs), plus kRowUmap
 // to read the per-point temperature table.
 template <bool UM>
 static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
                               const void* tw, int hx, cudaStream_t st) {
-    if (v == 3) {
+    if (v == 3 || v == 4) {
         switch (nx) {
-#define X(n) case n: return row_launch<float, n, 0, UM, 128>(descs, ninst, ny, nz, s, tw, hx, st);
+#define X(n)                                                                               \
+    case n:                                                                                \
+        return v == 3 ? row_launch<float, n, 0, UM, 128>(descs, ninst, ny, nz, s, tw, hx, st) \
+                      : row_launch<float, n, 0, UM, 64>(descs, ninst, ny, nz, s, tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
@@ -64,9 +67,12 @@ cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const v
 #undef X
         }
     }
-    if (v == 3) {
+    if (v == 3 || v == 4) {
         switch (ny) {
-#define X(n) case n: return col_launch<float, n, 0, 128>(descs, ninst, nx, tw, st);
+#define X(n)                                                                  \
+    case n:                                                                   \
+        return v == 3 ? col_launch<float, n, 0, 128>(descs, ninst, nx, tw, st) \
+                      : col_launch<float, n, 0, 64>(descs, ninst, nx, tw, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
@@ -118,8 +124,11 @@ cudaError_t attr_f32() {
     if (e == cudaSuccess) e = row_attr<float, n, 1, true>();     \
     if (e == cudaSuccess) e = row_attr<float, n, 0, false, 128>(); \
     if (e == cudaSuccess) e = row_attr<float, n, 0, true, 128>();  \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, false, 64>();  \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true, 64>();   \
     if (e == cudaSuccess) e = col_attr<float, n, 1>();           \
-    if (e == cudaSuccess) e = col_attr<float, n, 0, 128>();
+    if (e == cudaSuccess) e = col_attr<float, n, 0, 128>();      \
+    if (e == cudaSuccess) e = col_attr<float, n, 0, 64>();
     SHG_F32_VARIANT_SIZES(X)
 #undef X
 #define X(n) \
@@ -135,6 +144,13 @@ size_t row_smem_f32(int nx, int v, int hx) {
     if (v == 3) {
         switch (nx) {
 #define X(n) case n: return um ? row_smem<float, n, 0, true, 128>(hx) : row_smem<float, n, 0, false, 128>(hx);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
+    if (v == 4) {
+        switch (nx) {
+#define X(n) case n: return um ? row_smem<float, n, 0, true, 64>(hx) : row_smem<float, n, 0, false, 64>(hx);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }

@@ -115,8 +115,8 @@ void fill_init(const shg_plan* p, InitDesc* d);
 // Kernel launchers (passes_f32.cu / passes_f64.cu / aux.cu).
 // `variant` selects the kernel flavour: 0 the default FFT shape, 1 the
 // alternative shape where it exists; for the column pass 2 is the TMA-staged
-// kernel (needs `tmaps`); 3 is the default shape in 128-thread CTAs (both
-// passes).
+// kernel (needs `tmaps`); 3 and 4 are the default shape in 128- and
+// 64-thread CTAs (both passes).
 // Unavailable choices fall back to 0.
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
                        const void* tw, int hx, cudaStream_t st, int variant = 0);
@@ -127,11 +127,11 @@ cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, 
                        cudaStream_t st, int variant = 0, const void* tmaps = nullptr);
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
-bool has_col_small(bool fp64, int n);  // row and column passes in 128-thread CTAs (flavour 3)
+bool has_col_small(bool fp64, int n);  // row and column passes in 128/64-thread CTAs (flavours 3, 4)
 // Kernel flavour picked for (precision, length, pass, row-pass table bit) by the autotuner:
 // measured once per process on the first group that uses it, unless
 // SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.
-int fft_variant(bool fp64, int n, int pass, int row_bits = 0);
+int fft_variant(bool fp64, int n, int pass, int row_bits = 0, int ninst = 1 << 30);
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
                         const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits);
 // kRowUmap if the row passes of these plans (one grid) read the per-point

@@ -81,14 +81,17 @@ def test_sweep_instances_full_length(n):
     assert rel_l2(a_f.cpu(), AF) < FIELD_TOL
 
 
-@pytest.mark.parametrize("variant", ["1", "2", "3"])
-def test_batch_with_each_forced_kernel_flavour(variant, monkeypatch):
+@pytest.mark.parametrize("tz", [12, 16])
+@pytest.mark.parametrize("variant", ["1", "2", "3", "4"])
+def test_batch_with_each_forced_kernel_flavour(variant, tz, monkeypatch):
     """The batch path with the alternative FFT shape (1), the TMA-staged
-    column pass over the group's tensor-map array (2) or the 128-thread column
-    pass (3) forced, against the oracle per instance."""
+    column pass over the group's tensor-map array (2) or the passes in 128- or
+    64-thread CTAs (3, 4) forced, against the oracle per instance. With 12 map
+    layers over nz = 12 the rows take the per-point table, with 16 layers the
+    node sampler."""
     import paper_2410_04994_gb300 as pkg
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
-    insts = W.sweep_instances(nz=12, groups=((64, 2), (128, 2), (256, 1)), tgrid=(9, 9, 12))
+    insts = W.sweep_instances(nz=12, groups=((64, 2), (128, 2), (256, 1)), tgrid=(9, 9, tz))
     plans = _plans(insts)
     etas = pkg.shg_batch_submit([p.handle for p in plans])
     for p, w, e in zip(plans, insts, etas):
@@ -117,15 +120,20 @@ def test_tuner_cache_file_records_and_replays_decisions(tmp_path):
     env = dict(os.environ, SHG_TUNE_CACHE=str(cache))
     env.pop("SHG_FFT_VARIANT", None)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-    out1 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root, check=True,
-                          capture_output=True, text=True).stdout
+    r1 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root,
+                        capture_output=True, text=True)
+    assert r1.returncode == 0, r1.stderr[-2000:]
+    out1 = r1.stdout
     lines = [tuple(map(int, l.split())) for l in cache.read_text().splitlines()]
-    keys = {(n, p) for _, n, p, _ in lines}
-    # one column decision and one row decision (pass 0 or 2) per size
-    assert {(64, 1), (128, 1)} <= keys and len(lines) == 4, lines
-    cache.write_text("".join(f"{f} {n} {p} {2 if p == 1 else v}\n" for f, n, p, v in lines))
-    out2 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root, check=True,
-                          capture_output=True, text=True).stdout
+    # one column decision (key 1, or 5 for a group of few instances) and one
+    # row decision per size
+    cols = {n for _, n, p, _ in lines if p % 4 == 1}
+    assert cols == {64, 128} and len(lines) == 4, lines
+    cache.write_text("".join(f"{f} {n} {p} {2 if p % 4 == 1 else v}\n" for f, n, p, v in lines))
+    r2 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root,
+                        capture_output=True, text=True)
+    assert r2.returncode == 0, r2.stderr[-2000:]
+    out2 = r2.stdout
     assert len(cache.read_text().splitlines()) == 4      # nothing re-timed
     e1, e2 = json.loads(out1.strip().splitlines()[-1]), json.loads(out2.strip().splitlines()[-1])
     for a, b in zip(e1, e2):

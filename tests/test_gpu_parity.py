@@ -108,12 +108,12 @@ def test_undepleted_fp32_matches_oracle():
     _compare(w, ETA_TOL, FIELD_TOL)
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3"])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
 @pytest.mark.parametrize("n", [32, 64, 128, 256, 1024])
 def test_every_kernel_flavour_of_the_autotuner(n, variant, monkeypatch):
     """Each kernel flavour the autotuner can pick, forced through
     SHG_FFT_VARIANT (0/1: the two FFT shapes with cp.async staging, 2: the
-    TMA-staged column pass, 3: the column pass in 128-thread CTAs), matches
+    TMA-staged column pass, 3/4: both passes in 128-/64-thread CTAs), matches
     the oracle on its own."""
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
     w = W.depleted_absorbing(n=n, nz=6 if n < 1024 else 1, tgrid=(9, 7, 5), p1=400.0)
