@@ -22,13 +22,16 @@
  * with kF = 2 pi d/(n_F lambda_F), kS = 2 pi d/(n_SH lambda_F), I = eps0 c n |A|^2/2,
  * phi = (dk0 + g T_off) z + g C(x,y,z) (C = cumulative trapezoid integral of the
  * temperature map along z, g = dDk/dT) and psi_j = (2 pi/lambda_j)(dn/dT)(dT + T_off);
- * L(dz) multiplies the 2-D spectrum by exp(-i K^2 dz/(2 k_j)) exp(-alpha_j dz/2).
+ * L(dz) multiplies the 2-D spectrum by exp(-i K^2 dz/(2 k_j)) exp(-alpha_j dz/2)
+ * (and by exp(-i tan(rho_j) Kx dz) with a walk-off angle rho_j).
  *
  * Conventions for every entry point:
  *   - Units are SI.  Fields are complex, stored [ny][nx] with x fastest, as
  *     float2 (default) or double2 (SHG_FLAG_FP64) pairs (re, im).
  *   - Pointers named *_dev are device pointers; the caller owns them and they
- *     are only borrowed for the duration of the call.  Everything else the
+ *     are only borrowed for the duration of the call, or, for work the call
+ *     leaves enqueued (asynchronous map updates, fields), until the stream
+ *     has reached it.  Everything else the
  *     plan needs (fields, tables, checkpoints, scratch) is allocated by
  *     shg_plan_create / shg_set_temperature and owned by the plan.
  *   - Work is enqueued on the caller's stream (a cudaStream_t; NULL is the
