@@ -1,0 +1,329 @@
+"""The oracle's pins catch plausible mistakes.
+
+Each case plants one mistake in the oracle (on the CPU, for the duration of
+the test only, by monkeypatching) and runs the pins that should notice it:
+at least one of them must fail. The planted mistakes are the kinds a
+restatement of the paper can make:
+- a dropped factor or term;
+- a flipped sign;
+- a wrong wavelength or index;
+- a transposed operand;
+- a lower-order step.
+
+A mistake that no pin catches shows a gap in the pins.
+"""
+import math
+
+import pytest
+import torch
+
+from oracle import heat, ssfm
+from tests import test_oracle_pins as P
+
+
+# ------------------------------------------------------------ the mistakes ----
+
+def _wrap_linear_init(extra):
+    """Linear.__init__ followed by extra(self, p): a changed K-space factor."""
+    orig = ssfm.Linear.__init__
+
+    def init(self, p):
+        orig(self, p)
+        extra(self, p)
+    return init
+
+
+def _k(p):
+    Kx = ssfm.wavenumbers(p.nx, p.lx)
+    Ky = ssfm.wavenumbers(p.ny, p.ly)
+    return Kx, Ky, Kx[None, :] ** 2 + Ky[:, None] ** 2
+
+
+def diffraction_sign(self, p):
+    # exp(+i K^2 dz / 2k): App. A's printed sign instead of reading 1
+    _, _, K2 = _k(p)
+    self.PF = self.PF * torch.exp(2j * K2 * p.dz / (2 * p.k_f))
+    self.PS = self.PS * torch.exp(2j * K2 * p.dz / (2 * p.k_sh))
+
+
+def absorption_on_intensity(self, p):
+    # exp(-alpha dz) on the amplitude: alpha taken as an amplitude rate
+    self.PF = self.PF * math.exp(-0.5 * p.alpha_f * p.dz)
+    self.PS = self.PS * math.exp(-0.5 * p.alpha_sh * p.dz)
+
+
+def walkoff_sign(self, p):
+    # the beam drifts toward -x
+    Kx, _, _ = _k(p)
+    self.PS = self.PS * torch.exp(2j * math.tan(p.walkoff_sh) * Kx[None, :] * p.dz)
+    self.PF = self.PF * torch.exp(2j * math.tan(p.walkoff_f) * Kx[None, :] * p.dz)
+
+
+def walkoff_along_y(self, p):
+    # the walk-off factor applied along y instead of x
+    Kx, Ky, _ = _k(p)
+    for name, rho in (("PF", p.walkoff_f), ("PS", p.walkoff_sh)):
+        t = math.tan(rho) * p.dz
+        f = torch.exp(1j * t * Kx[None, :]) * torch.exp(-1j * t * Ky[:, None])
+        setattr(self, name, getattr(self, name) * f)
+
+
+def no_negative_frequencies(monkeypatch):
+    # K = 2 pi m / L for every bin m, without the negative half of fftfreq
+    monkeypatch.setattr(ssfm, "wavenumbers",
+                        lambda n, length: 2 * math.pi * torch.arange(n, dtype=torch.float64) / length)
+
+
+def kappa_sh_with_sh_wavelength(monkeypatch):
+    # Eq. 2 as printed: 2 pi d / (n_SH lambda_SH)
+    monkeypatch.setattr(ssfm.Params, "kappa_sh",
+                        property(lambda self: 2 * math.pi * self.d_eff / (self.n_sh * self.lambda_sh)))
+
+
+def _wrap_rhs(change):
+    orig = ssfm.Nonlinear.rhs
+
+    def rhs(self, AF, AS, coef):
+        fF, fS = orig(self, AF, AS, coef)
+        return change(self, AF, AS, coef, fF, fS)
+    return rhs
+
+
+def tpa_without_half(self, AF, AS, coef, fF, fS):
+    # -beta I A instead of -(1/2) beta I A
+    p = self.p
+    IF = self.cF * AF.abs() ** 2
+    IS = self.cS * AS.abs() ** 2
+    return fF - 0.5 * p.beta_f * IF * AF, fS - 0.5 * p.beta_sh * IS * AS
+
+
+def pump_coupling_without_conjugate(self, AF, AS, coef, fF, fS):
+    # i kappa_F A_SH A_F e^{-i phi}: the conjugate of A_F dropped
+    p = self.p
+    e = torch.exp(1j * coef[0])
+    if not p.undepleted:
+        fF = (fF - 1j * p.kappa_f * AS * torch.conj(AF) * torch.conj(e)
+              + 1j * p.kappa_f * AS * AF * torch.conj(e))
+    return fF, fS
+
+
+def undepleted_drops_the_sh_drive(self, AF, AS, coef, fF, fS):
+    # the undepleted switch removes the SH equation's drive instead of the pump's
+    p = self.p
+    e = torch.exp(1j * coef[0])
+    if p.undepleted:
+        fF = fF + 1j * p.kappa_f * AS * torch.conj(AF) * torch.conj(e)
+        fS = fS - 1j * p.kappa_sh * AF * AF * e
+    return fF, fS
+
+
+def _wrap_coefficients(change):
+    orig = ssfm.Nonlinear.coefficients
+
+    def coefficients(self, z):
+        return change(self, *orig(self, z))
+    return coefficients
+
+
+def phase_sign(self, phi, psiF, psiS):
+    # e^{+i phi} on the pump and e^{-i phi} on the SH: Dk of the opposite sign
+    return -phi, psiF, psiS
+
+
+def lens_with_sh_wavelength(self, phi, psiF, psiS):
+    # psi_F computed with 2 pi / lambda_SH
+    return phi, psiF * (self.k0S / self.k0F), psiS
+
+
+def rk4_wrong_third_stage(self, AF, AS, z0, h):
+    # the third stage re-uses the first slope: k3 = f(y + h/2 k1)
+    c0 = self.coefficients(z0)
+    cm = self.coefficients(z0 + 0.5 * h)
+    c1 = self.coefficients(z0 + h)
+    k1F, k1S = self.rhs(AF, AS, c0)
+    k2F, k2S = self.rhs(AF + 0.5 * h * k1F, AS + 0.5 * h * k1S, cm)
+    k3F, k3S = self.rhs(AF + 0.5 * h * k1F, AS + 0.5 * h * k1S, cm)
+    k4F, k4S = self.rhs(AF + h * k3F, AS + h * k3S, c1)
+    return (AF + (h / 6.0) * (k1F + 2 * k2F + 2 * k3F + k4F),
+            AS + (h / 6.0) * (k1S + 2 * k2S + 2 * k3S + k4S))
+
+
+def rk4_frozen_coefficients(self, AF, AS, z0, h):
+    # the stage coefficients of z0 used at every stage of the step
+    c0 = self.coefficients(z0)
+    k1F, k1S = self.rhs(AF, AS, c0)
+    k2F, k2S = self.rhs(AF + 0.5 * h * k1F, AS + 0.5 * h * k1S, c0)
+    k3F, k3S = self.rhs(AF + 0.5 * h * k2F, AS + 0.5 * h * k2S, c0)
+    k4F, k4S = self.rhs(AF + h * k3F, AS + h * k3S, c0)
+    return (AF + (h / 6.0) * (k1F + 2 * k2F + 2 * k3F + k4F),
+            AS + (h / 6.0) * (k1S + 2 * k2S + 2 * k3S + k4S))
+
+
+def power_without_half(monkeypatch):
+    # P = eps0 c n sum |A|^2 dx dy: the 1/2 of the intensity dropped
+    monkeypatch.setattr(ssfm, "power", lambda A, n_j, dx, dy: EPS0C * n_j * (A.abs() ** 2).sum() * dx * dy)
+
+
+EPS0C = ssfm.EPS0 * ssfm.C_LIGHT
+
+
+def pump_curvature_sign(monkeypatch):
+    # tau0 = +f / z_R: the beam starts diverging instead of converging
+    orig = ssfm.initial_pump
+    monkeypatch.setattr(ssfm, "initial_pump",
+                        lambda p, p1, w0, z_focus: orig(p, p1, w0, -ssfm._t(z_focus)))
+
+
+def cumulative_left_sum(monkeypatch):
+    # C by the left Riemann sum instead of the trapezoid rule
+    def cum(dT, L):
+        dZ = L / (dT.shape[0] - 1)
+        rows = [torch.zeros_like(dT[0])]
+        for l in range(1, dT.shape[0]):
+            rows.append(rows[-1] + dZ * dT[l - 1])
+        return torch.stack(rows, 0)
+    monkeypatch.setattr(ssfm, "cumulative_dT", cum)
+
+
+def bilinear_transposed(monkeypatch):
+    # the x and y fractions swapped in the transverse interpolation
+    def bil(self, t):
+        ix, fx, iy, fy = self.ix, self.fx, self.iy, self.fy
+        n = min(len(fx), len(fy))
+        fx2 = fx.clone()
+        fy2 = fy.clone()
+        fx2[:n], fy2[:n] = fy[:n], fx[:n]
+        t00 = t[iy][:, ix]
+        t01 = t[iy][:, ix + 1]
+        t10 = t[iy + 1][:, ix]
+        t11 = t[iy + 1][:, ix + 1]
+        fxr, fyc = fx2[None, :], fy2[:, None]
+        return (1 - fyc) * ((1 - fxr) * t00 + fxr * t01) + fyc * ((1 - fxr) * t10 + fxr * t11)
+    monkeypatch.setattr(ssfm.TemperatureField, "_bilinear", bil)
+
+
+def map_extrapolated(monkeypatch):
+    # no clamp at the map's edge: linear extrapolation outside it
+    def lin_index(coord, origin, spacing, n):
+        u = (coord - origin) / spacing
+        i = torch.floor(u).clamp(0, n - 2)
+        return i.long(), u - i
+    monkeypatch.setattr(ssfm, "_lin_index", lin_index)
+
+
+def deposit_full_weight_at_entrance(monkeypatch):
+    # the trapezoid's half weight dropped at z = 0
+    orig = ssfm.HeatDeposit.add
+
+    def add(self, AF, AS, z, wz):
+        return orig(self, AF, AS, z, 2 * wz if z == 0 else wz)
+    monkeypatch.setattr(ssfm.HeatDeposit, "add", add)
+
+
+def deposit_without_tpa(monkeypatch):
+    # q_dot without the two-photon terms beta_j I_j^2
+    def qdot(self, AF, AS):
+        p = self.p
+        return p.alpha_f * self.cF * AF.abs() ** 2 + p.alpha_sh * self.cS * AS.abs() ** 2
+    monkeypatch.setattr(ssfm.HeatDeposit, "qdot", qdot)
+
+
+def deposit_floor_node(monkeypatch):
+    # floor instead of round: the node below rather than the nearest one
+    orig = ssfm.HeatDeposit.__init__
+
+    def init(self, p, hx, hy, hz, wx, wy):
+        orig(self, p, hx, hy, hz, wx, wy)
+        x = ssfm.axis(p.nx, p.lx)
+        y = ssfm.axis(p.ny, p.ly)
+        self.ix = torch.floor((x + wx / 2) / self.hdx).long()
+        self.iy = torch.floor((y + wy / 2) / self.hdy).long()
+        self.okx = (self.ix >= 0) & (self.ix < hx)
+        self.oky = (self.iy >= 0) & (self.iy < hy)
+    monkeypatch.setattr(ssfm.HeatDeposit, "__init__", init)
+
+
+def stencil_spacings_swapped(monkeypatch):
+    # 1/dy^2 on the x neighbours and 1/dx^2 on the y neighbours
+    orig = heat.jacobi_target
+    monkeypatch.setattr(heat, "jacobi_target",
+                        lambda T, q, kappa, dx, dy, dz: orig(T, q, kappa, dy, dx, dz))
+
+
+def source_without_conductivity(monkeypatch):
+    # q_dot not divided by kappa
+    orig = heat.jacobi_target
+    monkeypatch.setattr(heat, "jacobi_target",
+                        lambda T, q, kappa, dx, dy, dz: orig(T, q, 1.0, dx, dy, dz))
+
+
+# ------------------------------------------------------------------ cases ----
+
+def _attr(obj, name, value):
+    return lambda mp: mp.setattr(obj, name, value)
+
+
+BK = [lambda: P.test_boyd_kleinman_undepleted(2.84, 0.5736),
+      lambda: P.test_boyd_kleinman_undepleted(2.84, -0.5736)]
+
+CASES = {
+    "diffraction sign": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(diffraction_sign)),
+                         [P.test_diffraction_reproduces_gaussian_beam]),
+    "absorption doubled": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(absorption_on_intensity)),
+                           [P.test_beer_lambert_decay_of_both_waves]),
+    "walk-off sign": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(walkoff_sign)),
+                      [P.test_walkoff_is_an_exact_translation,
+                       P.test_walkoff_moves_the_beam_centroid_at_tan_rho]),
+    "walk-off along y": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(walkoff_along_y)),
+                         [P.test_walkoff_is_an_exact_translation]),
+    "no negative frequencies": (no_negative_frequencies,
+                                [P.test_diffraction_reproduces_gaussian_beam]),
+    "kappa_SH with lambda_SH": (kappa_sh_with_sh_wavelength,
+                                [P.test_plane_wave_conversion_follows_tanh_squared,
+                                 P.test_manley_rowe_without_losses]),
+    "TPA without the 1/2": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(tpa_without_half)),
+                            [P.test_two_photon_absorption_closed_form]),
+    "pump coupling without conjugate": (
+        _attr(ssfm.Nonlinear, "rhs", _wrap_rhs(pump_coupling_without_conjugate)),
+        [P.test_manley_rowe_without_losses, P.test_plane_wave_conversion_follows_tanh_squared]),
+    "undepleted drops the SH drive": (
+        _attr(ssfm.Nonlinear, "rhs", _wrap_rhs(undepleted_drops_the_sh_drive)), BK),
+    "phase sign": (_attr(ssfm.Nonlinear, "coefficients", _wrap_coefficients(phase_sign)), BK),
+    "lens with lambda_SH": (_attr(ssfm.Nonlinear, "coefficients",
+                                  _wrap_coefficients(lens_with_sh_wavelength)),
+                            [P.test_uniform_lens_phase_rotates_fields]),
+    "RK4 third stage": (_attr(ssfm.Nonlinear, "rk4", rk4_wrong_third_stage),
+                        [P.test_manley_rowe_without_losses]),
+    "RK4 frozen coefficients": (_attr(ssfm.Nonlinear, "rk4", rk4_frozen_coefficients),
+                                [P.test_phase_mismatched_plane_wave_follows_sinc_squared]),
+    "power without the 1/2": (power_without_half,
+                              [P.test_initial_pump_is_eq5_with_discrete_power]),
+    "pump curvature sign": (pump_curvature_sign,
+                            [P.test_initial_pump_is_eq5_with_discrete_power]),
+    "cumulative left sum": (cumulative_left_sum, [P.test_trilinear_tables_exact_for_affine_maps]),
+    "bilinear transposed": (bilinear_transposed, [P.test_trilinear_tables_exact_for_affine_maps]),
+    "map extrapolated": (map_extrapolated,
+                         [P.test_temperature_map_is_clamped_outside_its_extent]),
+    "deposit full weight at z = 0": (deposit_full_weight_at_entrance,
+                                     [P.test_heat_deposits_balance_absorbed_power]),
+    "deposit without TPA": (deposit_without_tpa, [P.test_heat_deposits_balance_absorbed_power]),
+    "deposit on the node below": (deposit_floor_node,
+                                  [P.test_heat_deposit_lands_on_the_nearest_node]),
+    "stencil spacings swapped": (stencil_spacings_swapped, [P.test_sor_matches_direct_sparse_solve]),
+    "source not divided by kappa": (source_without_conductivity,
+                                    [P.test_sor_matches_direct_sparse_solve,
+                                     P.test_sor_recovers_discrete_eigenmode]),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_planted_mistake_fails_a_pin(name, monkeypatch):
+    plant, pins = CASES[name]
+    plant(monkeypatch)
+    caught = []
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught.append(pin)
+    assert caught, f"no pin caught the planted mistake: {name}"

@@ -11,7 +11,8 @@ or a transposed operand fails at least one of them:
                                       centroid drift tan(rho) z
 * coupling terms (Eq. 1/2, kappa)  -> plane-wave tanh^2 law, Manley-Rowe,
                                       Boyd-Kleinman h(sigma, xi)
-* phase sign and Dk (Eq. 3/4)      -> Boyd-Kleinman at sigma = +-0.57
+* phase sign and Dk (Eq. 3/4)      -> Boyd-Kleinman at sigma = +-0.57,
+                                      plane-wave sinc^2 at Dk L = 3 pi
 * TPA term                         -> closed-form plane-wave decay
 * temperature tables / lens phase  -> exact trilinear of affine maps,
                                       uniform dT == shifted dk0, e^{i psi z}
@@ -178,6 +179,28 @@ def test_plane_wave_conversion_follows_tanh_squared():
     assert abs(eta - math.tanh(gamma_L) ** 2) < 1e-10
 
 
+def test_phase_mismatched_plane_wave_follows_sinc_squared():
+    """Undepleted uniform pump, no losses, Dk L = 3 pi: the SH equation is the
+    quadrature A_SH(L) = i kappa_SH A_F^2 int_0^L e^{i Dk z} dz, so
+    eta = (n_SH / n_F) kappa_SH^2 |A_F|^2 L^2 sinc^2(Dk L / 2).  RK4 on a
+    quadrature is Simpson's rule, and the stage points' z enter through phi,
+    so the rule must hold to 1e-8 at nz = 200."""
+    w = W.plain_focused(n=8, nz=200, undepleted=True)
+    dk = 3 * math.pi / w.L
+    w = w.with_(dk0=dk)
+    a0 = 1e6
+    AF0 = torch.full((8, 8), a0, dtype=torch.complex128)
+    AS0 = torch.zeros_like(AF0)
+    p, (AF, AS) = _uniform_run(w, AF0, AS0)
+    kappa_sh = 2 * math.pi * w.d_eff / (w.n_sh * w.lambda_f)
+    x = dk * w.L / 2
+    ref = (w.n_sh / w.n_f) * (kappa_sh * a0 * w.L * math.sin(x) / x) ** 2
+    eta = float(ssfm.power(AS, p.n_sh, p.dx, p.dy) / ssfm.power(AF0, p.n_f, p.dx, p.dy))
+    assert 1e-5 < ref < 1e-1
+    assert abs(eta / ref - 1) < 1e-8
+    assert float((AF - AF0).abs().max()) < 1e-9 * a0   # the pump stays put
+
+
 def test_manley_rowe_without_losses():
     """P_F + P_SH is conserved up to the RK4 error, which falls as dz^4."""
     def defect(w):
@@ -276,6 +299,29 @@ def test_trilinear_tables_exact_for_affine_maps():
     assert np.max(np.abs(c.numpy() - refc)) < 1e-12
 
 
+def test_temperature_map_is_clamped_outside_its_extent():
+    """A map narrower than the field window: field points beyond its edge take
+    the edge value (reading 7), so an affine map evaluates to the affine
+    function at the coordinates clipped to the map's extent."""
+    w = W.plain_focused(n=16, nz=10)
+    p = _p(w)
+    tx, ty, tz = 5, 4, 3
+    t_lx, t_ly = 0.5 * p.lx, 0.4 * p.ly
+    X = -t_lx / 2 + np.arange(tx) * t_lx / (tx - 1)
+    Y = -t_ly / 2 + np.arange(ty) * t_ly / (ty - 1)
+    Z = np.arange(tz) * p.L / (tz - 1)
+    a, bx, cy, dz = -0.4, 2.3e3, 1.1e3, 25.0
+    dT = a + bx * X[None, None, :] + cy * Y[None, :, None] + dz * Z[:, None, None]
+    temp = ssfm.TemperatureField(p, torch.tensor(dT), t_lx, t_ly, 0.0)
+    x = np.clip(ssfm.axis(p.nx, p.lx).numpy(), -t_lx / 2, t_lx / 2)
+    y = np.clip(ssfm.axis(p.ny, p.ly).numpy(), -t_ly / 2, t_ly / 2)
+    assert np.sum(np.abs(ssfm.axis(p.nx, p.lx).numpy()) > t_lx / 2) >= 4  # points outside
+    for z in (0.0, 0.45 * p.L, p.L):
+        d, _ = temp.at(z)
+        ref = a + bx * x[None, :] + cy * y[:, None] + dz * z
+        assert np.max(np.abs(d.numpy() - ref)) < 1e-12
+
+
 def test_uniform_temperature_equals_shifted_mismatch():
     base = W.plain_focused(n=32, nz=30).with_(ddk_dT=-0.6 * 300, dn_dT=0.0)
     c = 1.7
@@ -368,6 +414,43 @@ def test_heat_deposits_balance_absorbed_power():
         errs.append(abs(float(dep.Q.sum()) / lost - 1))
     assert errs[1] < 1e-3
     assert 3.5 < errs[0] / errs[1] < 5.0
+
+
+def test_heat_deposit_lands_on_the_nearest_node():
+    """One field sample at a time: its q_dot dV (Eq. 8) goes to the heat node
+    nearest to it in x, y and z, found here by brute-force distance; a sample
+    more than half a cell beyond the heat grid deposits nothing."""
+    w = W.plain_focused(n=16, nz=10).with_(alpha_f=3.0)
+    p = _p(w)
+    hx, hy, hz = 7, 5, 4
+    wx, wy = 0.8 * p.lx, 0.6 * p.ly
+    dep = ssfm.HeatDeposit(p, hx, hy, hz, wx, wy)
+    x = ssfm.axis(p.nx, p.lx).numpy()
+    y = ssfm.axis(p.ny, p.ly).numpy()
+    X = -wx / 2 + np.arange(hx) * wx / (hx - 1)
+    Y = -wy / 2 + np.arange(hy) * wy / (hy - 1)
+    Zn = np.arange(hz) * p.L / (hz - 1)
+    a, wz = 1e6, 1e-3
+    q_ref = p.alpha_f * 0.5 * pins.EPS0 * pins.C_LIGHT * p.n_f * a * a * p.dx * p.dy * wz
+    inside_seen = outside_seen = 0
+    for (m, k, z) in ((3, 5, 0.37 * p.L), (8, 8, 0.9 * p.L), (12, 2, 0.1 * p.L),
+                      (0, 7, 0.5 * p.L), (10, 15, 0.62 * p.L), (13, 11, 0.0)):
+        AF = torch.zeros((p.ny, p.nx), dtype=torch.complex128)
+        AF[k, m] = a
+        dep.Q.zero_()
+        dep.add(AF, torch.zeros_like(AF), z, wz)
+        i, j, l = (int(np.argmin(np.abs(X - x[m]))), int(np.argmin(np.abs(Y - y[k]))),
+                   int(np.argmin(np.abs(Zn - z))))
+        inside = (abs(X[i] - x[m]) < 0.5 * wx / (hx - 1)
+                  and abs(Y[j] - y[k]) < 0.5 * wy / (hy - 1))
+        if inside:
+            inside_seen += 1
+            assert abs(float(dep.Q[l, j, i]) / q_ref - 1) < 1e-12
+            assert abs(float(dep.Q.sum()) - float(dep.Q[l, j, i])) == 0.0
+        else:
+            outside_seen += 1
+            assert float(dep.Q.abs().sum()) == 0.0
+    assert inside_seen >= 3 and outside_seen >= 2
 
 
 # ------------------------------------------------------------- gradients ----
