@@ -11,12 +11,8 @@ static cudaError_t row_adj_launch(const void* dl, const void* Y, AdjAcc acc, int
                                   int s, const void* tw, cudaStream_t st) {
     constexpr int T = FftCfg<R, N>::T, NTH = T > 64 ? T : 64;
     using G = RowGeom<R, N, 0, NTH>;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = allow_max_dyn_smem(k_row_adj<R, N, NTH>);
-        if (e != cudaSuccess) return e;
-        attr = true;
-    }
+    static const cudaError_t attr = allow_max_dyn_smem(k_row_adj<R, N, NTH>);  // once, thread-safe
+    if (attr != cudaSuccess) return attr;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, 1);
     k_row_adj<R, N, NTH><<<grid, NTH, G::fields + G::tables, st>>>(
         static_cast<const InstDesc<R>*>(dl), static_cast<const cx<R>*>(Y), acc, ny, nz, s,

@@ -385,19 +385,32 @@ static int tune_key(int pass, int row_bits, int ninst) {
     return pass + (pass == 0 && row_bits ? 2 : 0) + (ninst <= kFewInstances ? 4 : 0);
 }
 
+// A flavour this (precision, length, pass) does not have becomes flavour 0
+// (a forced flavour, or a decision read from a tuner cache of another build).
+static int supported_flavour(bool fp64, int n, int pass, int f) {
+    if (f == 1 && !has_fft_variant(fp64, n)) return 0;
+    if (f == 2 && pass == 0) return 0;
+    if (f >= 3 && !has_col_small(fp64, n)) return 0;
+    return f;
+}
+
 int fft_variant(bool fp64, int n, int pass, int row_bits, int ninst) {
     const int f = forced_variant();
-    if (f >= 0) {
-        if (f == 1 && !has_fft_variant(fp64, n)) return 0;
-        if (f == 2 && pass == 0) return 0;
-        if (f >= 3 && !has_col_small(fp64, n)) return 0;
-        return f;
-    }
+    if (f >= 0) return supported_flavour(fp64, n, pass, f);
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_tune_cache();
     auto it = g_tuned.find(std::make_tuple(fp64, n, tune_key(pass, row_bits, ninst)));
-    return it == g_tuned.end() ? 0 : it->second;
+    return it == g_tuned.end() ? 0 : supported_flavour(fp64, n, pass, it->second);
 }
+
+// The tuner's two timing events, released on every return.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
 
 // Time every candidate flavour of each pass of this group on its own data and
 // keep the fastest for the rest of the process.  After one warm-up launch
@@ -417,9 +430,10 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
             load_tune_cache();
             if (g_tuned.count(std::make_tuple(fp64, n, tune_key(pass, row_bits, ninst)))) continue;
         }
-        cudaEvent_t e0, e1;
-        SHG_CK(cudaEventCreate(&e0));
-        SHG_CK(cudaEventCreate(&e1));
+        EventPair ev;
+        SHG_CK(cudaEventCreate(&ev.e0));
+        SHG_CK(cudaEventCreate(&ev.e1));
+        cudaEvent_t e0 = ev.e0, e1 = ev.e1;
         const int s = nz > 1 ? 1 : 0;
         auto launch = [&](int v) {
             return pass == 0 ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v | row_bits)
@@ -451,8 +465,6 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
                 best_t = best[c];
                 best_v = cand[c];
             }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         std::lock_guard<std::mutex> lk(g_tune_mu);
         const int key = tune_key(pass, row_bits, ninst);
         g_tuned[std::make_tuple(fp64, n, key)] = best_v;
@@ -1214,9 +1226,15 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
         free_entry(ent);
         return SHG_ERR_INVALID_ARG;
     }
-    std::vector<cudaEvent_t> ev(4 * nsteps * ng);
-    for (auto& e : ev) cudaEventCreate(&e);
+    std::vector<cudaEvent_t> ev(4 * nsteps * ng, nullptr);
+    auto release = [&] {
+        for (auto& x : ev)
+            if (x) cudaEventDestroy(x);
+        free_entry(ent);
+    };
     cudaError_t e = cudaSuccess;
+    for (auto& x : ev)
+        if (e == cudaSuccess) e = cudaEventCreate(&x);
     for (int s = 1; s <= nsteps && e == cudaSuccess; ++s) {
         for (int gi = 0; gi < ng && e == cudaSuccess; ++gi) {
             BatchGroup& g = ent->groups[gi];
@@ -1231,7 +1249,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                                              int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps,
                                              row_umap_bit(g.plans));
                 if (r2 != SHG_OK) {
-                    free_entry(ent);
+                    release();
                     return r2;
                 }
                 cudaEventRecord(E[0], st);
@@ -1269,7 +1287,6 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
         }
         *ngroups = ng;
     }
-    for (auto& x : ev) cudaEventDestroy(x);
-    free_entry(ent);
+    release();
     return e == cudaSuccess ? SHG_OK : cuda_fail(e, "shg_pass_times");
 }
