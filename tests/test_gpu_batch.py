@@ -138,6 +138,29 @@ def test_tuner_cache_file_records_and_replays_decisions(tmp_path):
     e1, e2 = json.loads(out1.strip().splitlines()[-1]), json.loads(out2.strip().splitlines()[-1])
     for a, b in zip(e1, e2):
         assert abs(a / b - 1) < 1e-5
+    # decisions that do not apply (the TMA flavour for a row pass, an unknown
+    # length) are read, ignored for what they do not fit, and change nothing
+    cache.write_text("".join(f"{f} {n} {p} {2 if p % 4 != 1 else 4}\n" for f, n, p, v in lines)
+                     + "0 48 1 3\n")
+    r3 = subprocess.run([sys.executable, "-c", script], env=env, cwd=root,
+                        capture_output=True, text=True)
+    assert r3.returncode == 0, r3.stderr[-2000:]
+    e3 = json.loads(r3.stdout.strip().splitlines()[-1])
+    for a, b in zip(e1, e3):
+        assert abs(a / b - 1) < 1e-5
+
+
+def test_pass_times_of_a_mixed_batch():
+    """shg_pass_times on two grid groups (it tunes them first): one entry per
+    group with its sizes, instance count and positive row and column times;
+    a second call gives the same shape of answer."""
+    import paper_2410_04994_gb300 as pkg
+    insts = W.sweep_instances(nz=8, groups=((64, 3), (128, 2)), tgrid=(9, 9, 12))
+    plans = _plans(insts)
+    for _ in range(2):
+        t = pkg.shg_pass_times([p.handle for p in plans], nsteps=3)
+        assert [(g["nx"], g["ny"], g["instances"]) for g in t] == [(64, 64, 3), (128, 128, 2)]
+        assert all(0 < g["row_ms"] < 100 and 0 < g["col_ms"] < 100 for g in t)
 
 
 @pytest.mark.slow
