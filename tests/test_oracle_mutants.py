@@ -257,6 +257,24 @@ def source_without_conductivity(monkeypatch):
                         lambda T, q, kappa, dx, dy, dz: orig(T, q, 1.0, dx, dy, dz))
 
 
+def deposits_never_reset(monkeypatch):
+    # every outer iteration adds its deposits to the previous ones
+    orig = ssfm.HeatDeposit.__init__
+    shared = {}
+
+    def init(self, p, hx, hy, hz, wx, wy):
+        orig(self, p, hx, hy, hz, wx, wy)
+        self.Q = shared.setdefault((hx, hy, hz), self.Q)
+    monkeypatch.setattr(ssfm.HeatDeposit, "__init__", init)
+
+
+def heat_source_sign(monkeypatch):
+    # kappa lap T = +q_dot: the source cools
+    orig = heat.jacobi_target
+    monkeypatch.setattr(heat, "jacobi_target",
+                        lambda T, q, kappa, dx, dy, dz: orig(T, -q, kappa, dx, dy, dz))
+
+
 # ------------------------------------------------------------------ cases ----
 
 def _attr(obj, name, value):
@@ -310,6 +328,8 @@ CASES = {
     "deposit on the node below": (deposit_floor_node,
                                   [P.test_heat_deposit_lands_on_the_nearest_node]),
     "stencil spacings swapped": (stencil_spacings_swapped, [P.test_sor_matches_direct_sparse_solve]),
+    "deposits never reset": (deposits_never_reset, [P.test_thermal_loop_fixed_point_behaviour]),
+    "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
     "source not divided by kappa": (source_without_conductivity,
                                     [P.test_sor_matches_direct_sparse_solve,
                                      P.test_sor_recovers_discrete_eigenmode]),

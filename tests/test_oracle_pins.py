@@ -17,6 +17,8 @@ or a transposed operand fails at least one of them:
 * temperature tables / lens phase  -> exact trilinear of affine maps,
                                       uniform dT == shifted dk0, e^{i psi z}
 * heat solve (Eq. 16)              -> direct sparse solve, discrete eigenmode
+* self-consistent loop (Fig. 2)    -> lossless special case, maximum principle,
+                                      contraction
 * heat source deposits (Eq. 8)     -> energy balance
 * gradients (autograd of the map)  -> central finite differences
 """
@@ -451,6 +453,34 @@ def test_heat_deposit_lands_on_the_nearest_node():
             outside_seen += 1
             assert float(dep.Q.abs().sum()) == 0.0
     assert inside_seen >= 3 and outside_seen >= 2
+
+
+def test_thermal_loop_fixed_point_behaviour():
+    """The self-consistent loop of Fig. 2 on a small grid (100 W, 2 x 1 x 30 mm
+    crystal):
+    - without absorption nothing is deposited: dT stays 0 and every iteration
+      repeats the plain propagation's eta exactly;
+    - with absorption the first iteration starts from q_dot = 0 (the plain
+      eta again);
+    - every solve gives dT >= 0 with zero faces (maximum principle for a
+      non-negative source and Dirichlet faces);
+    - the iteration contracts: the second change is under a fifth of the first."""
+    w = W.thermal_loop(n=16, nz=40, heat=(9, 9, 11), n_outer=3, p1=100.0)
+    lossless = w.with_(alpha_f=0.0, alpha_sh=0.0, beta_f=0.0, beta_sh=0.0)
+    eta_plain = float(ssfm.run(lossless.with_(dT=None))[2])
+    for it in heat.thermal_loop(lossless, 3):
+        assert float(it["dT"].abs().max()) == 0.0
+        assert abs(it["eta"] / eta_plain - 1) < 1e-13
+    h = heat.thermal_loop(w, 3)
+    assert abs(h[0]["eta"] / float(ssfm.run(w.with_(dT=None))[2]) - 1) < 1e-13
+    assert h[0]["change"] == 0.0
+    for it in h[1:]:
+        dT = it["dT"]
+        assert float(dT.min()) >= 0.0 and float(dT.max()) > 0.1
+        faces = (dT[0], dT[-1], dT[:, 0], dT[:, -1], dT[:, :, 0], dT[:, :, -1])
+        assert all(float(f.abs().max()) == 0.0 for f in faces)
+    assert h[1]["change"] > 1.0
+    assert h[2]["change"] < 0.2 * h[1]["change"]
 
 
 # ------------------------------------------------------------- gradients ----
