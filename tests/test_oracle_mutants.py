@@ -121,6 +121,7 @@ def _wrap_coefficients(change):
     orig = ssfm.Nonlinear.coefficients
 
     def coefficients(self, z):
+        self._z = z
         return change(self, *orig(self, z))
     return coefficients
 
@@ -257,6 +258,53 @@ def source_without_conductivity(monkeypatch):
                         lambda T, q, kappa, dx, dy, dz: orig(T, q, 1.0, dx, dy, dz))
 
 
+def sh_diffraction_with_kf(self, p):
+    # the SH diffracts with the pump's wavenumber
+    _, _, K2 = _k(p)
+    self.PS = (self.PS * torch.exp(1j * K2 * p.dz / (2 * p.k_sh))
+               * torch.exp(-1j * K2 * p.dz / (2 * p.k_f)))
+
+
+def sh_intensity_with_nf(monkeypatch):
+    # I_SH = eps0 c n_F |A_SH|^2 / 2
+    orig = ssfm.Nonlinear.__init__
+
+    def init(self, p, temp):
+        orig(self, p, temp)
+        self.cS = self.cF
+    monkeypatch.setattr(ssfm.Nonlinear, "__init__", init)
+
+
+def undepleted_ignored(self, AF, AS, coef, fF, fS):
+    # the undepleted switch has no effect
+    p = self.p
+    if p.undepleted:
+        fF = fF + 1j * p.kappa_f * AS * torch.conj(AF) * torch.conj(torch.exp(1j * coef[0]))
+    return fF, fS
+
+
+def lens_without_offset(self, phi, psiF, psiS):
+    # psi_j from dT alone, without the oven offset T_off
+    t = self.temp.t_off
+    return phi, psiF - self.k0F * self.p.dn_dT * t, psiS - self.k0S * self.p.dn_dT * t
+
+
+def cumulative_without_slope(self, phi, psiF, psiS):
+    # phi = ... + C instead of ... + g C
+    _, c = self.temp.at(self._z)
+    return phi + (1 - self.p.ddk_dT) * c, psiF, psiS
+
+
+def no_deposit_at_exit(monkeypatch):
+    # the trapezoid's last sample, at z = L, left out
+    orig = ssfm.HeatDeposit.add
+
+    def add(self, AF, AS, z, wz):
+        if z != self.p.L:
+            orig(self, AF, AS, z, wz)
+    monkeypatch.setattr(ssfm.HeatDeposit, "add", add)
+
+
 def deposits_never_reset(monkeypatch):
     # every outer iteration adds its deposits to the previous ones
     orig = ssfm.HeatDeposit.__init__
@@ -328,6 +376,18 @@ CASES = {
     "deposit on the node below": (deposit_floor_node,
                                   [P.test_heat_deposit_lands_on_the_nearest_node]),
     "stencil spacings swapped": (stencil_spacings_swapped, [P.test_sor_matches_direct_sparse_solve]),
+    "SH diffraction with k_F": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(sh_diffraction_with_kf)),
+                                BK + [P.test_manley_rowe_without_losses]),
+    "SH intensity with n_F": (sh_intensity_with_nf, [P.test_two_photon_absorption_closed_form]),
+    "undepleted switch ignored": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(undepleted_ignored)),
+                                  [P.test_phase_mismatched_plane_wave_follows_sinc_squared]),
+    "lens without T_off": (_attr(ssfm.Nonlinear, "coefficients",
+                                 _wrap_coefficients(lens_without_offset)),
+                           [P.test_uniform_lens_phase_rotates_fields]),
+    "C without dDk/dT": (_attr(ssfm.Nonlinear, "coefficients",
+                               _wrap_coefficients(cumulative_without_slope)),
+                         [P.test_uniform_temperature_equals_shifted_mismatch]),
+    "no deposit at the exit": (no_deposit_at_exit, [P.test_heat_deposits_balance_absorbed_power]),
     "deposits never reset": (deposits_never_reset, [P.test_thermal_loop_fixed_point_behaviour]),
     "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
     "source not divided by kappa": (source_without_conductivity,
