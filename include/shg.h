@@ -109,7 +109,10 @@ typedef struct shg_plan shg_plan_t;
 /* Create a plan (Sec. 4: the Efields / Tfield / PhaseMatching state of the
  * paper as one object).  Validates the grid, allocates the device state and
  * the twiddle / propagator / phase tables (FP64-computed, rounded once).
- * On error *out is NULL. */
+ * SHG_ERR_INVALID_ARG for 1 <= nz <= 2^26 violated, for any non-finite
+ * double of the three structs, or for a non-positive length, wavelength,
+ * index, waist or (THERMAL) heat-grid extent; SHG_ERR_UNSUPPORTED_GRID for
+ * nx, ny out of range.  On error *out is NULL. */
 shg_status_t shg_plan_create(const shg_grid_t *grid, const shg_crystal_t *crystal,
                              const shg_beams_t *beams, int flags, shg_plan_t **out);
 
@@ -124,7 +127,8 @@ shg_status_t shg_plan_destroy(shg_plan_t *plan);
 shg_status_t shg_set_wait_limit(shg_plan_t *plan, unsigned polls);
 
 /* Replace the beam parameters (Eq. 5/6 inputs, T_off, undepleted switch) and
- * drop any fields set by shg_set_fields.  Grid and crystal are unchanged. */
+ * drop any fields set by shg_set_fields.  Grid and crystal are unchanged.
+ * SHG_ERR_INVALID_ARG for a non-finite value, w0 <= 0 or P1 < 0. */
 shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
 
 /* Temperature map dT (K, relative to the oven) on a node-centred grid

@@ -591,6 +591,24 @@ const char* shg_last_error(void) { return g_last_error.c_str(); }
 
 static void plan_free(shg_plan* p);
 
+// Largest nz: the stage index 4 s + q of the kernels stays far inside int.
+constexpr int kMaxNz = 1 << 26;
+
+static bool finite_beams(const shg_beams_t* b) {
+    return std::isfinite(b->p1) && std::isfinite(b->w0) && std::isfinite(b->z_focus) &&
+           std::isfinite(b->t_oven_offset) && b->w0 > 0 && b->p1 >= 0;
+}
+
+static bool finite_crystal(const shg_crystal_t* c) {
+    const double v[] = {c->L,      c->lambda_f, c->n_f,      c->n_sh,       c->d_eff,
+                        c->alpha_f, c->alpha_sh, c->beta_f,  c->beta_sh,    c->dk0,
+                        c->ddk_dT, c->dn_dT,    c->kappa_th, c->wx,         c->wy,
+                        c->walkoff_f, c->walkoff_sh};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
 shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crystal,
                              const shg_beams_t* beams, int flags, shg_plan_t** out) {
     if (out) *out = nullptr;
@@ -598,9 +616,12 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
     const bool fp64 = (flags & SHG_FLAG_FP64) != 0;
     const int hi = fp64 ? 256 : 1024;
     if (!pow2_in(grid->nx, 8, hi) || !pow2_in(grid->ny, 8, hi)) return SHG_ERR_UNSUPPORTED_GRID;
-    if (grid->nz < 1 || !(grid->lx > 0) || !(grid->ly > 0)) return SHG_ERR_INVALID_ARG;
+    if (grid->nz < 1 || grid->nz > kMaxNz || !(grid->lx > 0) || !(grid->ly > 0) ||
+        !std::isfinite(grid->lx) || !std::isfinite(grid->ly))
+        return SHG_ERR_INVALID_ARG;
+    if (!finite_crystal(crystal) || !finite_beams(beams)) return SHG_ERR_INVALID_ARG;
     if (!(crystal->L > 0) || !(crystal->lambda_f > 0) || !(crystal->n_f > 0) ||
-        !(crystal->n_sh > 0) || !(beams->w0 > 0) || !(beams->p1 >= 0) ||
+        !(crystal->n_sh > 0) ||
         !(std::fabs(crystal->walkoff_f) < 1.5) || !(std::fabs(crystal->walkoff_sh) < 1.5))
         return SHG_ERR_INVALID_ARG;
     if (flags & SHG_FLAG_THERMAL) {
@@ -714,7 +735,7 @@ shg_status_t shg_set_wait_limit(shg_plan_t* p, unsigned polls) {
 }
 
 shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
-    if (!p || !beams || !(beams->w0 > 0) || !(beams->p1 >= 0)) return SHG_ERR_INVALID_ARG;
+    if (!p || !beams || !finite_beams(beams)) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
     p->b = *beams;

@@ -57,6 +57,14 @@ def _w(**kw):
     (dict(L=0.0), 0, 1),
     (dict(hx=2, hy=8, hz=8), 2, 1),
     (dict(hx=8, hy=8, hz=8, kappa_th=0.0), 2, 1),
+    (dict(nz=(1 << 26) + 1), 0, 1),
+    (dict(lx=float("inf")), 0, 1),
+    (dict(d_eff=float("nan")), 0, 1),
+    (dict(dn_dT=float("inf")), 0, 1),
+    (dict(z_focus=float("nan")), 0, 1),
+    (dict(t_off=float("-inf")), 0, 1),
+    (dict(walkoff_sh=1.6), 0, 1),
+    (dict(n_sh=0.0), 0, 1),
 ])
 def test_plan_create_rejects_bad_arguments(pkg, kw, flags, code):
     w = _w(**kw)
