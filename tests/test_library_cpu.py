@@ -82,3 +82,13 @@ def test_null_handles_are_rejected(pkg):
     assert lib.shg_batch_submit(None, 0, None, None) == 1
     assert lib.shg_propagate_adjoint(None, 1.0, None, None, None, None, None) == 1
     assert lib.shg_heat_solve(None, 1, 1e-6, None, None, None) == 1
+    assert lib.shg_thermal_loop(None, 1, 1, 1e-6, None, None, None) == 1
+    assert lib.shg_get_heat(None, None, None, None) == 1
+    assert lib.shg_set_wait_limit(None, 0) == 1
+    assert lib.shg_set_beams(None, None) == 1
+    assert lib.shg_set_temperature(None, None, 2, 2, 2, 0.0, 0.0, None) == 1
+    assert lib.shg_set_temperature_batch(None, 0, None, 2, 2, 2, None, None, None) == 1
+    assert lib.shg_set_fields(None, None, None, None) == 1
+    assert lib.shg_get_fields(None, None, None, None) == 1
+    assert lib.shg_pass_times(None, 0, 1, None, None, 1, None, None) == 1
+    assert lib.shg_field_powers_noalloc(None, 8, 8, 1, 0, 1.0, 1.0, 2.0, 2.0, None, None) == 1
