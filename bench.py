@@ -103,12 +103,12 @@ class Clocks:
 
 # ----------------------------------------------------- plain FP64 GPU form ----
 
-def plain_fp64_gpu_rate(w, nsteps: int) -> float:
-    """Plain FP64 GPU form of the same split step: PyTorch complex128 with
-    torch.fft on the GPU, one instance, unfused elementwise ops.  Returns
-    grid-point-steps/s over `nsteps` z-steps."""
-    dev = "cuda"
-    f64, c128 = torch.float64, torch.complex128
+def plain_form(w, dev: str = "cuda", f64=torch.float64):
+    """The same split step written plainly in PyTorch: complex fields with
+    torch.fft, one instance, unfused elementwise ops (real type f64; complex
+    the matching type).  Returns (A_F(0), A_SH(0), step), step(a, s, z)
+    advancing one z-step from z."""
+    c128 = torch.complex128 if f64 == torch.float64 else torch.complex64
     eps0c = 8.8541878128e-12 * 299792458.0
     nx, ny, dz = w.nx, w.ny, w.L / w.nz
     x = (torch.arange(nx, dtype=f64, device=dev) - nx // 2) * (w.lx / nx)
@@ -180,6 +180,14 @@ def plain_fp64_gpu_rate(w, nsteps: int) -> float:
         s = torch.fft.ifft2(PS * torch.fft.fft2(s))
         return rk4(a, s, z + dz / 2, dz / 2)
 
+    return AF, AS, step
+
+
+def plain_fp64_gpu_rate(w, nsteps: int) -> float:
+    """Plain FP64 GPU form (plain_form on the GPU, complex128).  Returns
+    grid-point-steps/s over `nsteps` z-steps."""
+    AF, AS, step = plain_form(w, "cuda", torch.float64)
+    nx, ny, dz = w.nx, w.ny, w.L / w.nz
     for k in range(3):
         AF, AS = step(AF, AS, k * dz)
     torch.cuda.synchronize()

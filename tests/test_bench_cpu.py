@@ -38,3 +38,27 @@ def test_reference_arm_prints_one_complete_line():
 
 def test_reference_arm_other_ranks_exit_quietly():
     assert _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}) == []
+
+
+def test_plain_comparison_form_is_the_oracle_map():
+    """The plain PyTorch form that the benchmark times as its FP64 GPU
+    comparison (its own code, unfused, torch.fft) computes the oracle's map:
+    run here on the CPU over the full length, its eta matches the oracle's to
+    1e-10 in complex128 and to the FP32 bar in complex64."""
+    import math
+
+    import torch
+
+    import bench
+    import workloads as W
+    from tests.helpers import ETA_TOL, oracle_run
+    w = W.depleted_absorbing(n=32, nz=40, tgrid=(9, 7, 5), p1=400.0).with_(t_off=0.4)
+    eta_ref = oracle_run(w)[0]
+    eps0c = 8.8541878128e-12 * 299792458.0
+    for real, tol in ((torch.float64, 1e-10), (torch.float32, ETA_TOL)):
+        a, s, step = bench.plain_form(w, "cpu", real)
+        for k in range(w.nz):
+            a, s = step(a, s, k * w.L / w.nz)
+        p_sh = 0.5 * eps0c * w.n_sh * float((s.abs() ** 2).sum()) * (w.lx / w.nx) * (w.ly / w.ny)
+        assert math.isfinite(p_sh)
+        assert abs(p_sh / w.p1 / eta_ref - 1) < tol, (real, p_sh / w.p1, eta_ref)
