@@ -92,3 +92,17 @@ def test_null_handles_are_rejected(pkg):
     assert lib.shg_get_fields(None, None, None, None) == 1
     assert lib.shg_pass_times(None, 0, 1, None, None, 1, None, None) == 1
     assert lib.shg_field_powers_noalloc(None, 8, 8, 1, 0, 1.0, 1.0, 2.0, 2.0, None, None) == 1
+
+
+def test_missing_library_fails_loudly(pkg, monkeypatch, tmp_path):
+    """Without libshg.so every entry point raises: there is no CPU or library
+    fallback behind the binding."""
+    import workloads as W
+    monkeypatch.setattr(pkg, "LIB_PATH", str(tmp_path / "absent" / "libshg.so"))
+    monkeypatch.setattr(pkg, "_LIB", None)
+    with pytest.raises(ImportError, match="no fallback"):
+        pkg.load()
+    with pytest.raises(ImportError):
+        pkg.Plan(W.plain_focused(n=8, nz=2))
+    with pytest.raises(ImportError):
+        pkg.shg_status_string(0)
