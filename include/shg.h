@@ -225,8 +225,11 @@ shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
  * shg_batch_submit, with a CUDA event pair around every launch.  For group g
  * (g < *ngroups <= max_groups) it writes out[4g..4g+3] = {nx, ny, average
  * row-pass ms, average column-pass ms} and inst_out[g] = instances in the
- * group.  The plans' fields are advanced (use shg_propagate or
- * shg_batch_submit afterwards for a clean result).  Synchronises `stream`. */
+ * group.  A group not tuned yet in this process is tuned first (outside
+ * the event pairs).  The plans' fields are advanced (use shg_propagate or
+ * shg_batch_submit afterwards for a clean result).  SHG_ERR_INVALID_ARG for
+ * n <= 0, nsteps <= 0, max_groups <= 0, NULL outputs, or more groups than
+ * max_groups.  Synchronises `stream`. */
 shg_status_t shg_pass_times(shg_plan_t *const *plans, int n, int nsteps, double *out,
                             int *inst_out, int max_groups, int *ngroups, shg_stream_t stream);
 
