@@ -159,7 +159,11 @@ def shg_set_beams(plan: int, beams: shg_beams_t) -> None:
 
 
 def shg_set_temperature(plan: int, dT, t_lx: float = 0.0, t_ly: float = 0.0, stream=None) -> None:
-    """dT: contiguous float32 CUDA tensor [tz][ty][tx], or None to clear."""
+    """dT: contiguous float32 CUDA tensor [tz][ty][tx], or None to clear.  A map
+    of the installed shape and extent is copied asynchronously on `stream`:
+    keep dT alive and unchanged until that stream has passed this call (with
+    another stream than the one dT was allocated on, dT.record_stream(stream)
+    keeps PyTorch's allocator from reusing it earlier)."""
     if dT is None:
         _check(_lib().shg_set_temperature(plan, None, 0, 0, 0, 0.0, 0.0, _stream(stream)),
                "shg_set_temperature")
@@ -170,7 +174,10 @@ def shg_set_temperature(plan: int, dT, t_lx: float = 0.0, t_ly: float = 0.0, str
 
 
 def shg_set_temperature_batch(plans: Sequence[int], maps, t_lx, t_ly, stream=None) -> None:
-    """maps: contiguous float32 CUDA tensors [tz][ty][tx] of one shape, one per plan."""
+    """maps: contiguous float32 CUDA tensors [tz][ty][tx] of one shape, one per
+    plan.  They are read asynchronously on `stream`, so they must stay alive
+    and unchanged until that stream has passed this call (as for
+    shg_set_temperature)."""
     n = len(plans)
     if n == 0 or len(maps) != n:
         raise ValueError("one map per plan")
