@@ -136,6 +136,17 @@ def _ptr(t) -> Optional[int]:
     return t.data_ptr()
 
 
+def _map_shape(t):
+    """(tz, ty, tx) of a temperature map; the library reads tz*ty*tx floats
+    from its pointer, so anything but a 3-D float32 tensor is refused here."""
+    import torch
+    if not isinstance(t, torch.Tensor) or t.dim() != 3 or t.dtype != torch.float32:
+        raise ValueError("a temperature map is a 3-D float32 tensor [tz][ty][tx]")
+    if min(t.shape) < 2:
+        raise ValueError("a temperature map has at least 2 nodes per axis")
+    return tuple(t.shape)
+
+
 # ------------------------------------------------- C entry points ----
 
 def shg_plan_create(grid: shg_grid_t, crystal: shg_crystal_t, beams: shg_beams_t,
@@ -168,7 +179,7 @@ def shg_set_temperature(plan: int, dT, t_lx: float = 0.0, t_ly: float = 0.0, str
         _check(_lib().shg_set_temperature(plan, None, 0, 0, 0, 0.0, 0.0, _stream(stream)),
                "shg_set_temperature")
         return
-    tz, ty, tx = dT.shape
+    tz, ty, tx = _map_shape(dT)
     _check(_lib().shg_set_temperature(plan, _ptr(dT), tx, ty, tz, float(t_lx), float(t_ly),
                                       _stream(stream)), "shg_set_temperature")
 
@@ -179,9 +190,12 @@ def shg_set_temperature_batch(plans: Sequence[int], maps, t_lx, t_ly, stream=Non
     and unchanged until that stream has passed this call (as for
     shg_set_temperature)."""
     n = len(plans)
-    if n == 0 or len(maps) != n:
-        raise ValueError("one map per plan")
-    tz, ty, tx = maps[0].shape
+    if n == 0 or len(maps) != n or len(t_lx) != n or len(t_ly) != n:
+        raise ValueError("one map and one extent per plan")
+    shapes = {_map_shape(m) for m in maps}
+    if len(shapes) != 1:
+        raise ValueError(f"the maps of one batch update share one shape, got {sorted(shapes)}")
+    tz, ty, tx = shapes.pop()
     arr = (_P * n)(*plans)
     ptrs = (_P * n)(*[_ptr(m) for m in maps])
     lx = (_D * n)(*[float(v) for v in t_lx])

@@ -106,3 +106,20 @@ def test_missing_library_fails_loudly(pkg, monkeypatch, tmp_path):
         pkg.Plan(W.plain_focused(n=8, nz=2))
     with pytest.raises(ImportError):
         pkg.shg_status_string(0)
+
+
+def test_binding_refuses_maps_the_library_would_misread(pkg):
+    """The library reads tz*ty*tx floats from each map pointer with one shape
+    per batch: a map of another dtype, rank or shape is refused in the
+    binding, before any pointer reaches the library."""
+    import torch
+    good = torch.zeros((4, 3, 5), dtype=torch.float32)
+    bad = [torch.zeros((4, 3, 5), dtype=torch.float16), torch.zeros((4, 3, 5), dtype=torch.float64),
+           torch.zeros((3, 5), dtype=torch.float32), torch.zeros((4, 1, 5), dtype=torch.float32)]
+    for m in bad:
+        with pytest.raises(ValueError, match="temperature map"):
+            pkg.shg_set_temperature(0, m)
+    with pytest.raises(ValueError, match="one shape"):
+        pkg.shg_set_temperature_batch([0, 0], [good, torch.zeros((4, 3, 4))], [0.0, 0.0], [0.0, 0.0])
+    with pytest.raises(ValueError, match="per plan"):
+        pkg.shg_set_temperature_batch([0, 0], [good], [0.0], [0.0])
