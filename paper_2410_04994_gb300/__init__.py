@@ -147,6 +147,17 @@ def _map_shape(t):
     return tuple(t.shape)
 
 
+def _field_check(t, nx: int, ny: int, fp64: bool) -> None:
+    """A field handed to the library is read as ny*nx complex values of the
+    plan's precision: refuse anything else."""
+    import torch
+    if t is None:
+        return
+    want = torch.complex128 if fp64 else torch.complex64
+    if not isinstance(t, torch.Tensor) or t.dtype != want or t.numel() != nx * ny:
+        raise ValueError(f"a field of this plan is a {want} tensor of {ny} x {nx} values")
+
+
 # ------------------------------------------------- C entry points ----
 
 def shg_plan_create(grid: shg_grid_t, crystal: shg_crystal_t, beams: shg_beams_t,
@@ -347,6 +358,8 @@ class Plan:
         shg_set_beams(self.handle, b)
 
     def set_fields(self, a_f=None, a_sh=None, stream=None):
+        for a in (a_f, a_sh):
+            _field_check(a, self.w.nx, self.w.ny, self.fp64)
         shg_set_fields(self.handle, a_f, a_sh, stream)
 
     def propagate(self, stream=None):

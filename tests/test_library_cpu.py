@@ -123,3 +123,15 @@ def test_binding_refuses_maps_the_library_would_misread(pkg):
         pkg.shg_set_temperature_batch([0, 0], [good, torch.zeros((4, 3, 4))], [0.0, 0.0], [0.0, 0.0])
     with pytest.raises(ValueError, match="per plan"):
         pkg.shg_set_temperature_batch([0, 0], [good], [0.0], [0.0])
+
+
+def test_binding_refuses_fields_of_another_size_or_precision(pkg):
+    import torch
+    ok32 = torch.zeros((8, 16), dtype=torch.complex64)
+    pkg._field_check(ok32, 16, 8, False)
+    pkg._field_check(torch.zeros((8, 16), dtype=torch.complex128), 16, 8, True)
+    pkg._field_check(None, 16, 8, False)
+    for t, fp64 in ((ok32, True), (torch.zeros((8, 8), dtype=torch.complex64), False),
+                    (torch.zeros((8, 16, 2), dtype=torch.float32), False)):
+        with pytest.raises(ValueError, match="field of this plan"):
+            pkg._field_check(t, 16, 8, fp64)
