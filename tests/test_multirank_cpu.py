@@ -31,7 +31,7 @@ def _worker(rank, world, port, out):
 def test_sharding_and_aggregation_two_ranks():
     world = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()   # no fork of this multi-threaded process
     out = mgr.dict()
     mp.spawn(_worker, args=(world, port, out), nprocs=world, join=True)
     (v0, t0, p0, pw0), (v1, t1, p1, pw1) = out[0], out[1]
