@@ -139,8 +139,9 @@ shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
  * (uniform temperature T_off).  A map of the shape and extent already
  * installed is rebuilt asynchronously: the copy from dT_dev and the table
  * kernels are enqueued on `stream`, after the plan's last propagation, and
- * the call returns without waiting (later propagations on any stream wait
- * for them); dT_dev must stay unchanged until `stream` has reached them.
+ * the call returns without waiting (later propagations and map updates on
+ * any stream wait for them); dT_dev must stay unchanged until `stream` has
+ * reached them.
  * Any other change synchronises.  FP32 plans without SHG_FLAG_NODE_SAMPLER also
  * keep every map layer bilinearly sampled at every field point (tz*ny*nx*8
  * bytes of device memory; the nodes are sampled in the passes instead when

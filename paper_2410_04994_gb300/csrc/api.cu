@@ -758,6 +758,8 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
         p->tlx == (t_lx > 0 ? t_lx : p->g.lx) && p->tly == (t_ly > 0 ? t_ly : p->g.ly)) {
         const size_t n = size_t(tx) * ty * tz;
         if (p->done_valid) SHG_CK(cudaStreamWaitEvent(s, p->done, 0));
+        // after a rebuild still in flight on another stream (same tables)
+        if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(s, p->ready, 0));
         if (dT_dev != p->tmap)
             SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice,
                                    s));
@@ -852,8 +854,10 @@ shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const fl
         }
     }
     if (fast.empty()) return SHG_OK;
-    for (int k : fast)
+    for (int k : fast) {
         if (plans[k]->done_valid) SHG_CK(cudaStreamWaitEvent(s, plans[k]->done, 0));
+        if (plans[k]->ready_pending) SHG_CK(cudaStreamWaitEvent(s, plans[k]->ready, 0));
+    }
     // (dT, C) tables, one launch per precision
     for (int prec = 0; prec < 2; ++prec) {
         std::vector<TtabJob> jobs;
