@@ -307,8 +307,14 @@ static shg_status_t upload_desc(shg_plan* p) {
     return SHG_OK;
 }
 
+// Wait (host) for the plan's last propagation and for a table rebuild still
+// in flight, before a call rewrites state that device work may be reading.
 static shg_status_t quiesce(shg_plan* p) {
     if (p->last_stream != nullptr || p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    if (p->ready_pending) {
+        SHG_CK(cudaEventSynchronize(p->ready));
+        p->ready_pending = false;
+    }
     return SHG_OK;
 }
 
