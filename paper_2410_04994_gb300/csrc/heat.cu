@@ -203,8 +203,10 @@ extern "C" shg_status_t shg_thermal_loop(shg_plan_t* p, int n_outer, int max_swe
         k_max_abs_diff<<<256, 256, 0, st>>>(p->theat, p->theat_prev, nh, d);
         SHG_CK(cudaGetLastError());
         unsigned long long h = 0;
+        // into pageable host memory: returns once the value has arrived
         SHG_CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, st));
-        if ((r = install_map(p, st)) != SHG_OK) return r;  // synchronises st
+        // stream-ordered on st (same-shape maps after the first iteration)
+        if ((r = install_map(p, st)) != SHG_OK) return r;
         double change;
         memcpy(&change, &h, sizeof(double));
         if ((r = shg_propagate(p, stream)) != SHG_OK) return r;
