@@ -85,6 +85,10 @@ shg_status_t adjoint_checkpoint(shg_plan* p, int s, cudaStream_t st) {
     return SHG_OK;
 }
 
+void adjoint_forward_state(shg_plan* p, bool valid) {
+    if (p->adj) p->adj->have_forward = valid;
+}
+
 // ------------------------------------------------------------ kernels ----
 
 template <class R>

@@ -744,6 +744,7 @@ shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
     if (!p || !beams || !finite_beams(beams)) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
+    adjoint_forward_state(p, false);
     p->b = *beams;
     if (p->custom_init) {
         p->custom_init = false;
@@ -756,6 +757,7 @@ shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
 shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int ty, int tz,
                                  double t_lx, double t_ly, shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;
+    adjoint_forward_state(p, false);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // Fast path: a new map of the shape and extent already installed.  The
     // tables are rebuilt in place, stream-ordered after the last propagation
@@ -861,6 +863,7 @@ shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const fl
     }
     if (fast.empty()) return SHG_OK;
     for (int k : fast) {
+        adjoint_forward_state(plans[k], false);
         if (plans[k]->done_valid) SHG_CK(cudaStreamWaitEvent(s, plans[k]->done, 0));
         if (plans[k]->ready_pending) SHG_CK(cudaStreamWaitEvent(s, plans[k]->ready, 0));
     }
@@ -917,6 +920,7 @@ shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh
     if (!p) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
+    adjoint_forward_state(p, false);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const size_t one = size_t(p->g.nx) * p->g.ny * p->csize;
     if (!p->field0) SHG_CK(cudaMalloc(&p->field0, 2 * one));
@@ -941,6 +945,7 @@ shg_status_t shg_propagate(shg_plan_t* p, shg_stream_t stream) {
     if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(s, p->ready, 0));
     shg_status_t st = plan_forward(p, s);
     if (st != SHG_OK) return st;
+    adjoint_forward_state(p, true);
     SHG_CK(cudaEventRecord(p->done, s));
     p->done_valid = true;
     p->has_result = true;
