@@ -1233,6 +1233,7 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         p->last_stream = st;
         p->has_result = true;
         p->batch_result = true;
+        adjoint_forward_state(p, true);  // the batch wrote its checkpoints too
         p->ready_pending = false;  // the batch waited for it and has completed
         p->done_valid = false;
     }

@@ -188,7 +188,8 @@ shg_status_t adjoint_alloc(shg_plan* p);
 // Enqueue the checkpoint copy of the state entering row pass R(s) (adjoint plans).
 shg_status_t adjoint_checkpoint(shg_plan* p, int s, cudaStream_t st);
 // Whether the checkpoints hold the forward pass of the plan's current inputs:
-// set by every completed shg_propagate, cleared by every change of beams,
+// set by every completed shg_propagate or shg_batch_submit (both write the
+// checkpoints of adjoint plans), cleared by every change of beams,
 // fields or map (no-op for plans without SHG_FLAG_ADJOINT).
 void adjoint_forward_state(shg_plan* p, bool valid);
 
