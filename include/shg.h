@@ -182,12 +182,13 @@ shg_status_t shg_get_fields(shg_plan_t *plan, void *a_f_dev, void *a_sh_dev,
 
 /* Reverse sweep of the exact discrete forward map (conjugate propagator,
  * transposed RK4 with Wirtinger calculus), seeded with d_eta = dJ/deta, using
- * the sqrt(nz) checkpoints of the last shg_propagate (needs SHG_FLAG_ADJOINT).
+ * the sqrt(nz) checkpoints of the last propagation (shg_propagate or
+ * shg_batch_submit; needs SHG_FLAG_ADJOINT).
  * Outputs d_eta * deta/dw0, deta/dz_focus, deta/dT_off (host doubles) and
  * deta/d(dT node) into g_dT_dev[tz][ty][tx] (device float, may be NULL).
  * Grid and window are held fixed.  SHG_ERR_STATE if the plan has no
  * adjoint state, or if its beams, fields or map changed after the last
- * shg_propagate (the checkpoints would belong to other inputs).
+ * propagation (the checkpoints would belong to other inputs).
  * Synchronises `stream`. */
 shg_status_t shg_propagate_adjoint(shg_plan_t *plan, double d_eta, double *g_w0,
                                    double *g_zf, double *g_toven, float *g_dT_dev,
