@@ -197,7 +197,9 @@ shg_status_t shg_propagate_adjoint(shg_plan_t *plan, double d_eta, double *g_w0,
 /* Propagate n independent plans together (a focusing / power / oven sweep):
  * the plans are grouped by grid, and the whole sweep runs as one CUDA-graph
  * launch (captured on first use of this plan set and reused).  Writes
- * eta_host_out[n] and synchronises `stream`. */
+ * eta_host_out[n] and synchronises `stream`.  SHG_ERR_INVALID_ARG for a
+ * NULL or repeated plan (as for shg_set_temperature_batch and
+ * shg_pass_times). */
 shg_status_t shg_batch_submit(shg_plan_t *const *plans, int n, double *eta_host_out,
                               shg_stream_t stream);
 

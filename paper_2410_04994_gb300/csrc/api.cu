@@ -597,6 +597,15 @@ const char* shg_last_error(void) { return g_last_error.c_str(); }
 
 static void plan_free(shg_plan* p);
 
+// Non-null and pairwise distinct: the same plan twice in one call would have
+// two instances write its fields (or rebuild its tables) at once.
+static bool distinct_plans(shg_plan* const* plans, int n) {
+    std::vector<shg_plan*> v(plans, plans + n);
+    std::sort(v.begin(), v.end());
+    if (!v.empty() && v.front() == nullptr) return false;
+    return std::adjacent_find(v.begin(), v.end()) == v.end();
+}
+
 // Largest nz: the stage index 4 s + q of the kernels stays far inside int.
 constexpr int kMaxNz = 1 << 26;
 
@@ -842,7 +851,8 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
 shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const float* const* dT_devs,
                                        int tx, int ty, int tz, const double* t_lx,
                                        const double* t_ly, shg_stream_t stream) {
-    if (!plans || n <= 0 || !dT_devs || !t_lx || !t_ly) return SHG_ERR_INVALID_ARG;
+    if (!plans || n <= 0 || !dT_devs || !t_lx || !t_ly || !distinct_plans(plans, n))
+        return SHG_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // plans whose installed map has this shape and extent are rebuilt together;
     // the others take the single-plan path (which may allocate and synchronise)
@@ -1157,10 +1167,8 @@ void forget_plan_batches(shg_plan* p) {
 
 extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double* eta_host_out,
                                          shg_stream_t stream) {
-    if (!plans || n <= 0) return SHG_ERR_INVALID_ARG;
+    if (!plans || n <= 0 || !distinct_plans(plans, n)) return SHG_ERR_INVALID_ARG;
     std::vector<shg_plan*> key(plans, plans + n);
-    for (auto p : key)
-        if (!p) return SHG_ERR_INVALID_ARG;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g_batch_mu);
     BatchEntry*& ent = g_batches[key];
@@ -1243,7 +1251,8 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
 extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nsteps, double* out,
                                        int* inst_out, int max_groups, int* ngroups,
                                        shg_stream_t stream) {
-    if (!plans || n <= 0 || nsteps <= 0 || !out || !ngroups || max_groups <= 0)
+    if (!plans || n <= 0 || nsteps <= 0 || !out || !ngroups || max_groups <= 0 ||
+        !distinct_plans(plans, n))
         return SHG_ERR_INVALID_ARG;
     std::vector<shg_plan*> key(plans, plans + n);
     for (auto p : key)

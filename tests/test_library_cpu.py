@@ -135,3 +135,20 @@ def test_binding_refuses_fields_of_another_size_or_precision(pkg):
                     (torch.zeros((8, 16, 2), dtype=torch.float32), False)):
         with pytest.raises(ValueError, match="field of this plan"):
             pkg._field_check(t, 16, 8, fp64)
+
+
+def test_the_same_plan_twice_is_refused(pkg):
+    """A plan listed twice in one multi-plan call would have two instances
+    write its fields or tables at once; the call is refused before any plan
+    is touched (the handle here is never dereferenced)."""
+    import ctypes
+    lib = pkg.load()
+    fake = 0x1000
+    arr = (ctypes.c_void_p * 2)(fake, fake)
+    assert lib.shg_batch_submit(arr, 2, None, None) == 1
+    maps = (ctypes.c_void_p * 2)(fake, fake)
+    ext = (ctypes.c_double * 2)(0.0, 0.0)
+    assert lib.shg_set_temperature_batch(arr, 2, maps, 2, 2, 2, ext, ext, None) == 1
+    out = (ctypes.c_double * 8)()
+    ng = ctypes.c_int()
+    assert lib.shg_pass_times(arr, 2, 1, out, None, 2, ctypes.byref(ng), None) == 1
