@@ -175,6 +175,13 @@ def pump_curvature_sign(monkeypatch):
                         lambda p, p1, w0, z_focus: orig(p, p1, w0, -ssfm._t(z_focus)))
 
 
+def focus_at_the_centre(monkeypatch):
+    # the focus taken at L/2 whatever z_focus says
+    orig = ssfm.initial_pump
+    monkeypatch.setattr(ssfm, "initial_pump",
+                        lambda p, p1, w0, z_focus: orig(p, p1, w0, 0.5 * p.L + 0 * ssfm._t(z_focus)))
+
+
 def cumulative_left_sum(monkeypatch):
     # C by the left Riemann sum instead of the trapezoid rule
     def cum(dT, L):
@@ -332,9 +339,19 @@ def _attr(obj, name, value):
 BK = [lambda: P.test_boyd_kleinman_undepleted(2.84, 0.5736),
       lambda: P.test_boyd_kleinman_undepleted(2.84, -0.5736)]
 
+
+def DIFFRACTION():
+    for f in (0.5, 0.3):
+        P.test_diffraction_reproduces_gaussian_beam(f)
+
+
+def PUMP():
+    for f in (0.5, 0.3):
+        P.test_initial_pump_is_eq5_with_discrete_power(f)
+
 CASES = {
     "diffraction sign": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(diffraction_sign)),
-                         [P.test_diffraction_reproduces_gaussian_beam]),
+                         [DIFFRACTION]),
     "absorption doubled": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(absorption_on_intensity)),
                            [P.test_beer_lambert_decay_of_both_waves]),
     "walk-off sign": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(walkoff_sign)),
@@ -343,7 +360,7 @@ CASES = {
     "walk-off along y": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(walkoff_along_y)),
                          [P.test_walkoff_is_an_exact_translation]),
     "no negative frequencies": (no_negative_frequencies,
-                                [P.test_diffraction_reproduces_gaussian_beam]),
+                                [DIFFRACTION]),
     "kappa_SH with lambda_SH": (kappa_sh_with_sh_wavelength,
                                 [P.test_plane_wave_conversion_follows_tanh_squared,
                                  P.test_manley_rowe_without_losses]),
@@ -363,9 +380,10 @@ CASES = {
     "RK4 frozen coefficients": (_attr(ssfm.Nonlinear, "rk4", rk4_frozen_coefficients),
                                 [P.test_phase_mismatched_plane_wave_follows_sinc_squared]),
     "power without the 1/2": (power_without_half,
-                              [P.test_initial_pump_is_eq5_with_discrete_power]),
+                              [PUMP]),
     "pump curvature sign": (pump_curvature_sign,
-                            [P.test_initial_pump_is_eq5_with_discrete_power]),
+                            [PUMP]),
+    "focus at the centre": (focus_at_the_centre, [PUMP, DIFFRACTION]),
     "cumulative left sum": (cumulative_left_sum, [P.test_trilinear_tables_exact_for_affine_maps]),
     "bilinear transposed": (bilinear_transposed, [P.test_trilinear_tables_exact_for_affine_maps]),
     "map extrapolated": (map_extrapolated,

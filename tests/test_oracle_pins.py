@@ -67,8 +67,11 @@ def test_wavenumber_bins_match_plane_waves():
 
 # ----------------------------------------------------------------- init ----
 
-def test_initial_pump_is_eq5_with_discrete_power():
+@pytest.mark.parametrize("focus", [0.5, 0.3])
+def test_initial_pump_is_eq5_with_discrete_power(focus):
+    """Eq. 5 at the entrance for a focus at the centre and off it (f = 0.3 L)."""
     w = W.plain_focused(n=64, nz=10)
+    w = w.with_(z_focus=focus * w.L)
     p = _p(w)
     A = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus).numpy()
     x = ssfm.axis(p.nx, p.lx).numpy()
@@ -92,8 +95,13 @@ def _free_run(w):
     return p, AF0, AF
 
 
-def test_diffraction_reproduces_gaussian_beam():
+@pytest.mark.parametrize("focus", [0.5, 0.3])
+def test_diffraction_reproduces_gaussian_beam(focus):
     w = W.plain_focused(n=128, nz=20, xi=2.84).with_(d_eff=0.0)
+    zf = focus * w.L
+    # a window of ten radii at whichever end the beam is wider
+    lw = 10 * max(W.beam_radius(0.0, w.w0, zf), W.beam_radius(w.L, w.w0, zf))
+    w = w.with_(z_focus=zf, lx=lw, ly=lw)
     p, AF0, AF = _free_run(w)
     x = ssfm.axis(p.nx, p.lx).numpy()
     y = ssfm.axis(p.ny, p.ly).numpy()
