@@ -323,6 +323,29 @@ def deposits_never_reset(monkeypatch):
     monkeypatch.setattr(ssfm.HeatDeposit, "__init__", init)
 
 
+def loop_map_over_the_window(monkeypatch):
+    # the loop installs dT over the field window instead of the crystal
+    def loop(w, n_outer, tol=1e-6, max_sweeps=100000, nsteps=None):
+        p = ssfm.params_from_workload(w)
+        q = torch.zeros((w.hz, w.hy, w.hx), dtype=torch.float64)
+        dT_prev = torch.zeros_like(q)
+        history = []
+        for _ in range(n_outer):
+            dT, sweeps, _ = heat.sor_solve(q, w.kappa_th, w.wx, w.wy, w.L, tol, max_sweeps,
+                                           T0=dT_prev)
+            change = float((dT - dT_prev).abs().max())
+            dep = ssfm.HeatDeposit(p, w.hx, w.hy, w.hz, w.wx, w.wy)
+            temp = ssfm.TemperatureField(p, dT, w.lx, w.ly, w.t_off)
+            AF0 = ssfm.initial_pump(p, w.p1, w.w0, w.z_focus)
+            AF, AS = ssfm.propagate(p, AF0, torch.zeros_like(AF0), temp, dep)
+            eta = float(ssfm.power(AS, p.n_sh, p.dx, p.dy) / w.p1)
+            q = dep.qdot_nodes()
+            history.append(dict(eta=eta, dT=dT, change=change, sweeps=sweeps))
+            dT_prev = dT
+        return history
+    monkeypatch.setattr(heat, "thermal_loop", loop)
+
+
 def heat_source_sign(monkeypatch):
     # kappa lap T = +q_dot: the source cools
     orig = heat.jacobi_target
@@ -407,6 +430,11 @@ CASES = {
                          [P.test_uniform_temperature_equals_shifted_mismatch]),
     "no deposit at the exit": (no_deposit_at_exit, [P.test_heat_deposits_balance_absorbed_power]),
     "deposits never reset": (deposits_never_reset, [P.test_thermal_loop_fixed_point_behaviour]),
+    "loop map over the window": (loop_map_over_the_window,
+                                 [P.test_thermal_loop_fixed_point_behaviour]),
+    "node density without hdz": (_attr(ssfm.HeatDeposit, "qdot_nodes",
+                                       lambda self: self.Q / (self.hdx * self.hdy)),
+                                 [P.test_thermal_loop_fixed_point_behaviour]),
     "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
     "source not divided by kappa": (source_without_conductivity,
                                     [P.test_sor_matches_direct_sparse_solve,

@@ -489,6 +489,11 @@ def test_thermal_loop_fixed_point_behaviour():
         assert all(float(f.abs().max()) == 0.0 for f in faces)
     assert h[1]["change"] > 1.0
     assert h[2]["change"] < 0.2 * h[1]["change"]
+    # each iteration propagates through its solved dT as a map over the
+    # crystal cross-section wx x wy (reading 12), nothing else
+    for it in h[1:]:
+        ref = ssfm.run(w.with_(dT=it["dT"].numpy(), t_lx=w.wx, t_ly=w.wy))[2]
+        assert abs(it["eta"] / float(ref) - 1) < 1e-13
 
 
 # ------------------------------------------------------------- gradients ----
