@@ -435,6 +435,10 @@ CASES = {
     "node density without hdz": (_attr(ssfm.HeatDeposit, "qdot_nodes",
                                        lambda self: self.Q / (self.hdx * self.hdy)),
                                  [P.test_thermal_loop_fixed_point_behaviour]),
+    "cell-centred heat grid": (_attr(heat, "spacings",
+                                     lambda hx, hy, hz, wx, wy, L: (wx / hx, wy / hy, L / hz)),
+                               [P.test_sor_matches_direct_sparse_solve,
+                                P.test_sor_recovers_discrete_eigenmode]),
     "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
     "source not divided by kappa": (source_without_conductivity,
                                     [P.test_sor_matches_direct_sparse_solve,

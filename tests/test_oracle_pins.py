@@ -383,7 +383,7 @@ def test_sor_matches_direct_sparse_solve():
     from scipy.sparse.linalg import spsolve
     hx, hy, hz = 10, 8, 12
     wx, wy, L, kappa = 2e-3, 1e-3, 0.03, 8.4
-    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    dx, dy, dz = wx / (hx - 1), wy / (hy - 1), L / (hz - 1)   # node-centred, faces included
     rng = np.random.default_rng(5)
     q = rng.uniform(0, 1e8, size=(hz, hy, hx))
     T, sweeps, corr = heat.sor_solve(torch.tensor(q), kappa, wx, wy, L, tol=1e-13)
@@ -398,7 +398,7 @@ def test_sor_matches_direct_sparse_solve():
 def test_sor_recovers_discrete_eigenmode():
     hx, hy, hz = 17, 9, 33
     wx, wy, L, kappa = 2e-3, 1e-3, 0.03, 8.4
-    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    dx, dy, dz = wx / (hx - 1), wy / (hy - 1), L / (hz - 1)   # node-centred, faces included
     X = np.arange(hx) * dx
     Y = np.arange(hy) * dy
     Z = np.arange(hz) * dz
