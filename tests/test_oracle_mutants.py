@@ -384,6 +384,9 @@ CASES = {
                          [P.test_walkoff_is_an_exact_translation]),
     "no negative frequencies": (no_negative_frequencies,
                                 [DIFFRACTION]),
+    "axis spacing L/(n-1)": (_attr(ssfm, "axis", lambda n, length: (
+        torch.arange(n, dtype=torch.float64) - n // 2) * (length / (n - 1))),
+                             [P.test_wavenumber_bins_match_plane_waves]),
     "kappa_SH with lambda_SH": (kappa_sh_with_sh_wavelength,
                                 [P.test_plane_wave_conversion_follows_tanh_squared,
                                  P.test_manley_rowe_without_losses]),
