@@ -363,6 +363,24 @@ BK = [lambda: P.test_boyd_kleinman_undepleted(2.84, 0.5736),
       lambda: P.test_boyd_kleinman_undepleted(2.84, -0.5736)]
 
 
+def TPA():
+    for wave in ("sh", "f"):
+        P.test_two_photon_absorption_closed_form(wave)
+
+
+def pump_tpa_with_sh_intensity(self, AF, AS, coef, fF, fS):
+    # the pump's two-photon loss driven by I_SH
+    p = self.p
+    IF = self.cF * AF.abs() ** 2
+    IS = self.cS * AS.abs() ** 2
+    return fF + 0.5 * p.beta_f * IF * AF - 0.5 * p.beta_f * IS * AF, fS
+
+
+def pump_tpa_dropped(self, AF, AS, coef, fF, fS):
+    # beta_F left out of the pump equation
+    return fF + 0.5 * self.p.beta_f * self.cF * AF.abs() ** 2 * AF, fS
+
+
 def DIFFRACTION():
     for f in (0.5, 0.3):
         P.test_diffraction_reproduces_gaussian_beam(f)
@@ -391,7 +409,9 @@ CASES = {
                                 [P.test_plane_wave_conversion_follows_tanh_squared,
                                  P.test_manley_rowe_without_losses]),
     "TPA without the 1/2": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(tpa_without_half)),
-                            [P.test_two_photon_absorption_closed_form]),
+                            [TPA]),
+    "pump TPA with I_SH": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(pump_tpa_with_sh_intensity)), [TPA]),
+    "pump TPA dropped": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(pump_tpa_dropped)), [TPA]),
     "pump coupling without conjugate": (
         _attr(ssfm.Nonlinear, "rhs", _wrap_rhs(pump_coupling_without_conjugate)),
         [P.test_manley_rowe_without_losses, P.test_plane_wave_conversion_follows_tanh_squared]),
@@ -422,7 +442,7 @@ CASES = {
     "stencil spacings swapped": (stencil_spacings_swapped, [P.test_sor_matches_direct_sparse_solve]),
     "SH diffraction with k_F": (_attr(ssfm.Linear, "__init__", _wrap_linear_init(sh_diffraction_with_kf)),
                                 BK + [P.test_manley_rowe_without_losses]),
-    "SH intensity with n_F": (sh_intensity_with_nf, [P.test_two_photon_absorption_closed_form]),
+    "SH intensity with n_F": (sh_intensity_with_nf, [TPA]),
     "undepleted switch ignored": (_attr(ssfm.Nonlinear, "rhs", _wrap_rhs(undepleted_ignored)),
                                   [P.test_phase_mismatched_plane_wave_follows_sinc_squared]),
     "lens without T_off": (_attr(ssfm.Nonlinear, "coefficients",

@@ -13,7 +13,7 @@ or a transposed operand fails at least one of them:
                                       Boyd-Kleinman h(sigma, xi)
 * phase sign and Dk (Eq. 3/4)      -> Boyd-Kleinman at sigma = +-0.57,
                                       plane-wave sinc^2 at Dk L = 3 pi
-* TPA term                         -> closed-form plane-wave decay
+* TPA terms                        -> closed-form plane-wave decay of each wave
 * temperature tables / lens phase  -> exact trilinear of affine maps,
                                       uniform dT == shifted dk0, e^{i psi z}
 * heat solve (Eq. 16)              -> direct sparse solve, discrete eigenmode
@@ -264,20 +264,28 @@ def test_paper_optimum_focusing_from_bk_quadrature():
     assert abs(pins.bk_h(0.0, 2.84) - math.atan(2.84) ** 2 / 2.84) < 1e-10
 
 
-def test_two_photon_absorption_closed_form():
-    """Uniform SH only, alpha_SH and beta_SH: second-order convergence to
-    I0 e^{-a z} / (1 + b I0 (1 - e^{-a z}) / a)."""
+@pytest.mark.parametrize("wave", ["sh", "f"])
+def test_two_photon_absorption_closed_form(wave):
+    """One uniform wave alone (no coupling) with alpha_j and beta_j:
+    second-order convergence to I0 e^{-a z} / (1 + b I0 (1 - e^{-a z}) / a)."""
     errs = []
     for nz in (50, 100):
-        w = W.plain_focused(n=8, nz=nz).with_(alpha_sh=20.0, beta_sh=2e-12)
+        w = W.plain_focused(n=8, nz=nz).with_(d_eff=0.0)
+        if wave == "sh":
+            w = w.with_(alpha_sh=20.0, beta_sh=2e-12)
+        else:
+            w = w.with_(alpha_f=20.0, beta_f=2e-12)
         p = _p(w)
         a = 3e7
-        AF0 = torch.zeros((8, 8), dtype=torch.complex128)
-        AS0 = torch.full((8, 8), a, dtype=torch.complex128)
+        full = torch.full((8, 8), a, dtype=torch.complex128)
+        none = torch.zeros_like(full)
+        AF0, AS0 = (none, full) if wave == "sh" else (full, none)
         p, (AF, AS) = _uniform_run(w, AF0, AS0)
-        I0 = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * p.n_sh * a * a
-        I = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * p.n_sh * float(AS[0, 0].abs() ** 2)
-        ref = pins.tpa_plane_wave(I0, p.alpha_sh, p.beta_sh, p.L)
+        n, A, alpha, beta = ((p.n_sh, AS, p.alpha_sh, p.beta_sh) if wave == "sh"
+                             else (p.n_f, AF, p.alpha_f, p.beta_f))
+        I0 = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * n * a * a
+        I = 0.5 * ssfm.EPS0 * ssfm.C_LIGHT * n * float(A[0, 0].abs() ** 2)
+        ref = pins.tpa_plane_wave(I0, alpha, beta, p.L)
         assert ref < 0.5 * I0   # strong absorption regime
         errs.append(abs(I / ref - 1))
     assert errs[1] < 1e-5
