@@ -141,7 +141,8 @@ shg_status_t shg_set_beams(shg_plan_t *plan, const shg_beams_t *beams);
  * kernels are enqueued on `stream`, after the plan's last propagation, and
  * the call returns without waiting (later propagations and map updates on
  * any stream wait for them); dT_dev must stay unchanged until `stream` has
- * reached them.
+ * reached them.  SHG_ERR_INVALID_ARG (tx, ty or tz < 2, a non-finite
+ * extent) leaves the installed map and the adjoint checkpoints untouched.
  * Any other change synchronises.  FP32 plans without SHG_FLAG_NODE_SAMPLER also
  * keep every map layer bilinearly sampled at every field point (tz*ny*nx*8
  * bytes of device memory; the nodes are sampled in the passes instead when
@@ -155,7 +156,11 @@ shg_status_t shg_set_temperature(shg_plan_t *plan, const float *dT_dev, int tx, 
  * launches for all of them (stream-ordered, no host synchronisation, as the
  * single-plan fast path); the others are set one by one.  The host arrays
  * may be reused once the call returns; the maps must stay unchanged until
- * `stream` has reached the rebuild. */
+ * `stream` has reached the rebuild.  Every argument of every plan (non-NULL
+ * plan and map, tx, ty, tz >= 2, finite extents) is checked before any plan
+ * changes, so SHG_ERR_INVALID_ARG leaves all maps as they were.  A CUDA
+ * failure part-way (SHG_ERR_CUDA / SHG_ERR_OOM) can leave the plans before
+ * the failing one with the new map and the rest with the old one. */
 shg_status_t shg_set_temperature_batch(shg_plan_t *const *plans, int n, const float *const *dT_devs,
                                        int tx, int ty, int tz, const double *t_lx,
                                        const double *t_ly, shg_stream_t stream);

@@ -2,8 +2,9 @@
 
 TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline and reference legs of ``bench.py`` may import this package.  It shares no code
-with the CUDA path: plain PyTorch CPU ops in float64 / complex128, one library
-FFT (``torch.fft``) as a step, no blocking, fusion or reordering.
+with the CUDA path: plain PyTorch CPU ops in float64 / complex128 and the
+oracle's own radix-2 DFT (``oracle/fft.c``, no library FFT), with no blocking,
+fusion or reordering.
 
 The discrete map it computes (all SI units):
 
@@ -50,6 +51,8 @@ from dataclasses import dataclass
 from typing import Optional
 
 import torch
+
+from . import fft as dft
 
 F64 = torch.float64
 C128 = torch.complex128
@@ -140,8 +143,11 @@ def axis(n: int, length: float) -> torch.Tensor:
 
 
 def wavenumbers(n: int, length: float) -> torch.Tensor:
-    """K = 2 pi fftfreq(n, dx): the angular spatial frequencies of the DFT bins."""
-    return 2.0 * math.pi * torch.fft.fftfreq(n, d=length / n, dtype=F64)
+    """Angular spatial frequency of DFT bin b: K_b = 2 pi m_b / length with
+    m_b = b for b < n/2 and b - n above (the bin's signed frequency index)."""
+    b = torch.arange(n, dtype=F64)
+    m = torch.where(b < (n + 1) // 2, b, b - n)
+    return 2.0 * math.pi * m / length
 
 
 def power(A: torch.Tensor, n_j: float, dx: float, dy: float) -> torch.Tensor:
@@ -306,8 +312,8 @@ class Linear:
         self.PS = self.PS * torch.exp(-1j * math.tan(p.walkoff_sh) * Kx[None, :] * dz)
 
     def __call__(self, AF, AS):
-        AF = torch.fft.ifft2(self.PF * torch.fft.fft2(AF))
-        AS = torch.fft.ifft2(self.PS * torch.fft.fft2(AS))
+        AF = dft.ifft2(self.PF * dft.fft2(AF))
+        AS = dft.ifft2(self.PS * dft.fft2(AS))
         return AF, AS
 
 

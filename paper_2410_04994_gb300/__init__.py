@@ -286,9 +286,30 @@ def shg_pass_times(plans: Sequence[int], nsteps: int = 4, stream=None, max_group
 def shg_field_powers_noalloc(fields, nx: int, ny: int, n_inst: int, lx: float, ly: float,
                              n_f: float, n_sh: float, powers, stream=None) -> None:
     """P_F, P_SH of caller-held fields into a caller-held float64 CUDA tensor
-    [n_inst, 2]; the library allocates nothing (see include/shg.h)."""
+    [n_inst, 2]; the library allocates nothing (see include/shg.h).
+
+    The library reads n_inst * 2 * ny * nx complex values from `fields` and
+    writes 2 * n_inst doubles to `powers`, so any tensor it would read or
+    write past its end, or reinterpret as another type, is refused here
+    (ValueError) before the call."""
     import torch
-    fp64 = 1 if fields.dtype in (torch.complex128, torch.float64) else 0
+    if not isinstance(fields, torch.Tensor) or fields.dtype not in (torch.complex64,
+                                                                   torch.complex128):
+        raise ValueError("fields is a complex64 or complex128 tensor")
+    if not isinstance(powers, torch.Tensor) or powers.dtype != torch.float64:
+        raise ValueError("powers is a float64 tensor")
+    n_inst, nx, ny = int(n_inst), int(nx), int(ny)
+    if n_inst < 1 or nx < 1 or ny < 1 or fields.numel() != n_inst * 2 * nx * ny:
+        raise ValueError(f"fields holds {fields.numel()} values, not n_inst x 2 x ny x nx = "
+                         f"{n_inst} x 2 x {ny} x {nx}")
+    if powers.numel() < 2 * n_inst:
+        raise ValueError(f"powers holds {powers.numel()} values, fewer than 2 x n_inst")
+    for t in (fields, powers):
+        if not t.is_cuda or not t.is_contiguous():
+            raise ValueError("fields and powers are contiguous CUDA tensors")
+        if t.device.index != torch.cuda.current_device():
+            raise ValueError("fields and powers live on the current CUDA device")
+    fp64 = 1 if fields.dtype == torch.complex128 else 0
     _check(_lib().shg_field_powers_noalloc(_ptr(fields), nx, ny, n_inst, fp64, float(lx),
                                            float(ly), float(n_f), float(n_sh), _ptr(powers),
                                            _stream(stream)), "shg_field_powers_noalloc")

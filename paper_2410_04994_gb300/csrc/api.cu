@@ -482,11 +482,16 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
                              const InitDesc* idescs, int ninst, const void* tw,
                              const std::vector<shg_plan*>& plans, cudaStream_t st,
-                             const void* tmaps) {
+                             const void* tmaps, int* status_arr) {
     const bool custom = plans[0]->custom_init;
-    for (shg_plan* p : plans) {
-        const cudaError_t e0 = cudaMemsetAsync(p->status, 0, sizeof(int), st);
+    if (status_arr) {
+        const cudaError_t e0 = cudaMemsetAsync(status_arr, 0, ninst * sizeof(int), st);
         if (e0 != cudaSuccess) return cuda_fail(e0, "memset status");
+    } else {
+        for (shg_plan* p : plans) {
+            const cudaError_t e0 = cudaMemsetAsync(p->status, 0, sizeof(int), st);
+            if (e0 != cudaSuccess) return cuda_fail(e0, "memset status");
+        }
     }
     cudaError_t e = custom ? launch_copy_init(fp64, idescs, ninst, descs, nx, ny, st)
                            : launch_init(fp64, idescs, nullptr, ninst, descs, nx, ny, st);
@@ -766,6 +771,11 @@ shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
 shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int ty, int tz,
                                  double t_lx, double t_ly, shg_stream_t stream) {
     if (!p) return SHG_ERR_INVALID_ARG;
+    // every argument is checked before anything of the plan changes: a refused
+    // call leaves the map, the tables and the adjoint checkpoints as they were
+    if (dT_dev != nullptr &&
+        (tx < 2 || ty < 2 || tz < 2 || !std::isfinite(t_lx) || !std::isfinite(t_ly)))
+        return SHG_ERR_INVALID_ARG;
     adjoint_forward_state(p, false);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // Fast path: a new map of the shape and extent already installed.  The
@@ -808,7 +818,6 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
         }
         return upload_desc(p);
     }
-    if (tx < 2 || ty < 2 || tz < 2) return SHG_ERR_INVALID_ARG;
     const size_t n = size_t(tx) * ty * tz;
     if (p->ttab == nullptr || p->tx != tx || p->ty != ty || p->tz != tz) {
         if (p->ttab) cudaFree(p->ttab);
@@ -853,13 +862,18 @@ shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const fl
                                        const double* t_ly, shg_stream_t stream) {
     if (!plans || n <= 0 || !dT_devs || !t_lx || !t_ly || !distinct_plans(plans, n))
         return SHG_ERR_INVALID_ARG;
+    // all arguments of all plans are checked before any plan changes, so a
+    // refused call leaves every plan's map as it was
+    if (tx < 2 || ty < 2 || tz < 2) return SHG_ERR_INVALID_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!plans[k] || !dT_devs[k] || !std::isfinite(t_lx[k]) || !std::isfinite(t_ly[k]))
+            return SHG_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     // plans whose installed map has this shape and extent are rebuilt together;
     // the others take the single-plan path (which may allocate and synchronise)
     std::vector<int> fast;
     for (int k = 0; k < n; ++k) {
         shg_plan* p = plans[k];
-        if (!p || !dT_devs[k]) return SHG_ERR_INVALID_ARG;
         const bool same = p->ttab != nullptr && p->tx == tx && p->ty == ty && p->tz == tz &&
                           p->tlx == (t_lx[k] > 0 ? t_lx[k] : p->g.lx) &&
                           p->tly == (t_ly[k] > 0 ? t_ly[k] : p->g.ly);
@@ -968,8 +982,9 @@ shg_status_t shg_efficiency(shg_plan_t* p, double* eta, double* p_f, double* p_s
     if (!p) return SHG_ERR_INVALID_ARG;
     if (!p->has_result) return SHG_ERR_STATE;
     SHG_CK(cudaStreamSynchronize(p->last_stream));
-    int kst = 0;
-    SHG_CK(cudaMemcpy(&kst, p->status, sizeof(int), cudaMemcpyDeviceToHost));
+    int kst = p->batch_kst;  // a batch reports kernel errors per instance on the host
+    if (!p->batch_result)
+        SHG_CK(cudaMemcpy(&kst, p->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (kst != 0) return shg_status_t(kst);
     if (!p->batch_result)
         SHG_CK(cudaMemcpy(p->pw_host, p->pw, 2 * sizeof(double), cudaMemcpyDeviceToHost));
@@ -1008,7 +1023,11 @@ struct BatchGroup {
     void* descs = nullptr;      // device InstDesc[n]
     InitDesc* idescs = nullptr; // device InitDesc[n]
     double* pw = nullptr;       // device [n][2]
+    int* status = nullptr;      // device [n]: the instances' status words during a batch
     void* tmaps = nullptr;      // device CUtensorMap[n], or nullptr (cp.async column pass)
+    size_t off = 0;             // first instance of the group in the entry's staging arrays
+    unsigned char* hdesc = nullptr;  // pinned staging of the descriptors [n]
+    InitDesc* hinit = nullptr;       // pinned staging of the init descriptors [n]
 };
 
 struct BatchEntry {
@@ -1017,7 +1036,10 @@ struct BatchEntry {
     cudaStream_t cap = nullptr;
     std::vector<cudaStream_t> side;
     std::vector<cudaEvent_t> ev;
-    double* pw_host = nullptr;  // pinned [n][2]
+    double* pw_host = nullptr;  // pinned [n][2], the caller's order
+    double* pw_stage = nullptr; // pinned [n][2], group order (one copy per group)
+    int* st_stage = nullptr;    // pinned [n], group order
+    cudaEvent_t uploaded = nullptr;  // after the last descriptor upload from the staging
     int n = 0;
     bool valid = false;
 };
@@ -1026,17 +1048,25 @@ static std::mutex g_batch_mu;
 static std::map<std::vector<shg_plan*>, BatchEntry*> g_batches;
 
 static void free_entry(BatchEntry* b) {
+    // the staging buffers may still be read by an upload in flight
+    if (b->uploaded) cudaEventSynchronize(b->uploaded);
     for (auto& g : b->groups) {
         if (g.descs) cudaFree(g.descs);
         if (g.idescs) cudaFree(g.idescs);
         if (g.pw) cudaFree(g.pw);
+        if (g.status) cudaFree(g.status);
         if (g.tmaps) cudaFree(g.tmaps);
+        if (g.hdesc) cudaFreeHost(g.hdesc);
+        if (g.hinit) cudaFreeHost(g.hinit);
     }
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
     if (b->cap) cudaStreamDestroy(b->cap);
     for (auto s : b->side) cudaStreamDestroy(s);
     for (auto e : b->ev) cudaEventDestroy(e);
     if (b->pw_host) cudaFreeHost(b->pw_host);
+    if (b->pw_stage) cudaFreeHost(b->pw_stage);
+    if (b->st_stage) cudaFreeHost(b->st_stage);
+    if (b->uploaded) cudaEventDestroy(b->uploaded);
     delete b;
 }
 
@@ -1063,7 +1093,10 @@ static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry*
         const int n = int(g.plans.size());
         if ((e = cudaMalloc(&g.descs, n * desc_bytes(g.fp64))) != cudaSuccess ||
             (e = cudaMalloc((void**)&g.idescs, n * sizeof(InitDesc))) != cudaSuccess ||
-            (e = cudaMalloc((void**)&g.pw, n * 2 * sizeof(double))) != cudaSuccess) {
+            (e = cudaMalloc((void**)&g.pw, n * 2 * sizeof(double))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&g.status, n * sizeof(int))) != cudaSuccess ||
+            (e = cudaMallocHost((void**)&g.hdesc, n * desc_bytes(g.fp64))) != cudaSuccess ||
+            (e = cudaMallocHost((void**)&g.hinit, n * sizeof(InitDesc))) != cudaSuccess) {
             free_entry(b);
             return cuda_fail(e, "batch alloc");
         }
@@ -1080,7 +1113,15 @@ static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry*
             }
         }
     }
+    size_t off = 0;
+    for (auto& g : b->groups) {
+        g.off = off;
+        off += g.plans.size();
+    }
     if ((e = cudaMallocHost((void**)&b->pw_host, b->n * 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&b->pw_stage, b->n * 2 * sizeof(double))) != cudaSuccess ||
+        (e = cudaMallocHost((void**)&b->st_stage, b->n * sizeof(int))) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->uploaded, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking)) != cudaSuccess) {
         free_entry(b);
         return cuda_fail(e, "batch setup");
@@ -1106,24 +1147,30 @@ static shg_status_t build_entry(const std::vector<shg_plan*>& plans, BatchEntry*
     return SHG_OK;
 }
 
-// Upload the current descriptors of every plan of the entry.
+// Upload the current descriptors of every plan of the entry, from pinned
+// staging buffers owned by the entry (so the copies need no host wait; the
+// next refresh reuses the staging only after the previous submit has
+// synchronised its stream).  Inside a batch every instance reports kernel
+// errors into its slot of the group's status array, which one copy reads.
 static shg_status_t refresh_entry(BatchEntry* b, cudaStream_t st) {
     for (auto& g : b->groups) {
         const int n = int(g.plans.size());
         const size_t db = desc_bytes(g.fp64);
-        std::vector<unsigned char> hd(n * db);
-        std::vector<InitDesc> hi(n);
         for (int k = 0; k < n; ++k) {
-            fill_desc_any(g.plans[k], hd.data() + k * db);
-            fill_init(g.plans[k], &hi[k]);
-            hi[k].pw = g.pw + 2 * k;
+            unsigned char* d = g.hdesc + k * db;
+            fill_desc_any(g.plans[k], d);
+            if (g.fp64)
+                reinterpret_cast<InstDesc<double>*>(d)->status = g.status + k;
+            else
+                reinterpret_cast<InstDesc<float>*>(d)->status = g.status + k;
+            fill_init(g.plans[k], &g.hinit[k]);
+            g.hinit[k].pw = g.pw + 2 * k;
         }
-        SHG_CK(cudaMemcpyAsync(g.descs, hd.data(), hd.size(), cudaMemcpyHostToDevice, st));
-        SHG_CK(cudaMemcpyAsync(g.idescs, hi.data(), n * sizeof(InitDesc), cudaMemcpyHostToDevice,
+        SHG_CK(cudaMemcpyAsync(g.descs, g.hdesc, n * db, cudaMemcpyHostToDevice, st));
+        SHG_CK(cudaMemcpyAsync(g.idescs, g.hinit, n * sizeof(InitDesc), cudaMemcpyHostToDevice,
                                st));
     }
-    // the host vectors above go out of scope: make the copies complete first
-    SHG_CK(cudaStreamSynchronize(st));
+    SHG_CK(cudaEventRecord(b->uploaded, st));
     return SHG_OK;
 }
 
@@ -1139,7 +1186,8 @@ static shg_status_t enqueue_batch(BatchEntry* b, cudaStream_t st) {
         cudaStream_t s = b->side[i];
         SHG_CK(cudaStreamWaitEvent(s, fork, 0));
         shg_status_t r = enqueue_forward(g.fp64, g.nx, g.ny, g.nz, g.descs, g.idescs,
-                                         int(g.plans.size()), g.plans[0]->tw, g.plans, s, g.tmaps);
+                                         int(g.plans.size()), g.plans[0]->tw, g.plans, s, g.tmaps,
+                                         g.status);
         if (r != SHG_OK) return r;
         SHG_CK(cudaEventRecord(b->ev[i], s));
         SHG_CK(cudaStreamWaitEvent(st, b->ev[i], 0));
@@ -1192,7 +1240,7 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
         }
     }
     for (auto p : key) {
-        if (p->has_result) cudaStreamSynchronize(p->last_stream);
+        if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
         if (p->ready_pending) SHG_CK(cudaStreamWaitEvent(st, p->ready, 0));
     }
     if ((r = refresh_entry(ent, st)) != SHG_OK) return r;
@@ -1219,16 +1267,35 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
     } else {
         if ((r = enqueue_batch(ent, st)) != SHG_OK) return r;
     }
-    // gather the powers
-    for (auto& g : ent->groups)
-        for (size_t k = 0; k < g.plans.size(); ++k)
-            SHG_CK(cudaMemcpyAsync(ent->pw_host + 2 * g.index[k], g.pw + 2 * k,
-                                   2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    // gather the powers and the status words: one copy of each per group
+    for (auto& g : ent->groups) {
+        const size_t m = g.plans.size();
+        SHG_CK(cudaMemcpyAsync(ent->pw_stage + 2 * g.off, g.pw, 2 * m * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+        SHG_CK(cudaMemcpyAsync(ent->st_stage + g.off, g.status, m * sizeof(int),
+                               cudaMemcpyDeviceToHost, st));
+    }
     SHG_CK(cudaStreamSynchronize(st));
-    for (auto p : key) {
-        int kst = 0;
-        SHG_CK(cudaMemcpy(&kst, p->status, sizeof(int), cudaMemcpyDeviceToHost));
-        if (kst != 0) return shg_status_t(kst);
+    int first_err = 0;
+    for (auto& g : ent->groups)
+        for (size_t k = 0; k < g.plans.size(); ++k) {
+            const int i = g.index[k];
+            ent->pw_host[2 * i] = ent->pw_stage[2 * (g.off + k)];
+            ent->pw_host[2 * i + 1] = ent->pw_stage[2 * (g.off + k) + 1];
+            const int kst = ent->st_stage[g.off + k];
+            g.plans[k]->batch_kst = kst;
+            if (kst != 0 && first_err == 0) first_err = kst;
+        }
+    if (first_err != 0) {
+        for (auto p : key) {
+            adjoint_forward_state(p, false);  // the checkpoints of a failed sweep are unusable
+            p->last_stream = st;
+            p->has_result = true;
+            p->batch_result = true;
+            p->ready_pending = false;
+            p->done_valid = false;
+        }
+        return shg_status_t(first_err);
     }
     bool finite = true;
     for (int i = 0; i < n; ++i) {

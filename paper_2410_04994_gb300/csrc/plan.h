@@ -65,6 +65,7 @@ struct shg_plan {
     double pw_host[2] = {0, 0};
     bool has_result = false;
     bool batch_result = false;  // pw_host holds the last batch's powers
+    int batch_kst = 0;          // status word of this instance in the last batch
     cudaStream_t last_stream = nullptr;
     // Stream ordering without host synchronisation: `done` is recorded after
     // each propagation (its kernels read the map tables), `ready` after the
@@ -179,7 +180,7 @@ struct PdlScope {
 shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* descs,
                              const InitDesc* idescs, int ninst, const void* tw,
                              const std::vector<shg_plan*>& plans, cudaStream_t st,
-                             const void* tmaps = nullptr);
+                             const void* tmaps = nullptr, int* status_arr = nullptr);
 
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);

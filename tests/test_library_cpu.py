@@ -152,3 +152,48 @@ def test_the_same_plan_twice_is_refused(pkg):
     out = (ctypes.c_double * 8)()
     ng = ctypes.c_int()
     assert lib.shg_pass_times(arr, 2, 1, out, None, 2, ctypes.byref(ng), None) == 1
+
+
+@pytest.mark.parametrize("case", ["real_fields", "short_fields", "long_fields", "f32_powers",
+                                  "short_powers", "cpu_tensors", "bad_n_inst"])
+def test_noalloc_binding_refuses_mismatched_tensors(pkg, case):
+    """shg_field_powers_noalloc reads n_inst*2*ny*nx complex values and writes
+    2*n_inst doubles: the binding refuses, before any library call, every
+    tensor that the kernels would read or write past its end or reinterpret
+    as another type."""
+    import torch
+    nx, ny, n = 8, 8, 3
+    fields = torch.zeros((n, 2, ny, nx), dtype=torch.complex64)
+    powers = torch.zeros((n, 2), dtype=torch.float64)
+    kw = dict(n_inst=n)
+    if case == "real_fields":
+        fields = torch.zeros((n, 2, ny, nx, 2), dtype=torch.float64)
+    elif case == "short_fields":
+        fields = fields[:2]
+    elif case == "long_fields":
+        kw["n_inst"] = 2
+        powers = powers[:2]
+    elif case == "f32_powers":
+        powers = powers.float()
+    elif case == "short_powers":
+        powers = powers[:2]
+    elif case == "bad_n_inst":
+        kw["n_inst"] = 0
+    with pytest.raises(ValueError):
+        pkg.shg_field_powers_noalloc(fields, nx, ny, kw["n_inst"], 1e-3, 1e-3, 2.14, 2.18,
+                                     powers)
+
+
+def test_refused_temperature_update_keeps_the_map(pkg):
+    """Arguments are checked before the plan changes: a refused
+    shg_set_temperature / shg_set_temperature_batch returns
+    SHG_ERR_INVALID_ARG with no device work (no GPU needed to reach it)."""
+    lib = pkg.load()
+    # a NULL plan, and a non-NULL map with too few nodes, are refused first
+    assert lib.shg_set_temperature(None, None, 0, 0, 0, 0.0, 0.0, None) == 1
+    arr = (ctypes.c_void_p * 1)(1)   # never dereferenced: the shape check comes first
+    maps = (ctypes.c_void_p * 1)(1)
+    ext = (ctypes.c_double * 1)(0.0)
+    assert lib.shg_set_temperature_batch(arr, 1, maps, 1, 4, 4, ext, ext, None) == 1
+    bad = (ctypes.c_double * 1)(float("nan"))
+    assert lib.shg_set_temperature_batch(arr, 1, maps, 4, 4, 4, bad, ext, None) == 1

@@ -43,15 +43,51 @@ def _p(w):
 
 # ------------------------------------------------------------------ FFT ----
 
-@pytest.mark.parametrize("shape", [(8, 8), (16, 8)])
+@pytest.mark.parametrize("shape", [(8, 8), (16, 8), (2, 4), (1, 1)])
 def test_fft_step_matches_brute_force_dft(shape):
+    """The oracle's own radix-2 DFT (oracle/fft.c) against the O(N^4) sum of
+    the DFT's definition, and its inverse back to the input."""
+    from oracle import fft as dft
     rng = np.random.default_rng(3)
     a = rng.normal(size=shape) + 1j * rng.normal(size=shape)
     ref = pins.brute_dft2(a)
-    got = torch.fft.fft2(torch.tensor(a)).numpy()
+    got = dft.fft2(torch.tensor(a)).numpy()
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
-    back = torch.fft.ifft2(torch.tensor(got)).numpy()
+    back = dft.ifft2(torch.tensor(got)).numpy()
     assert np.max(np.abs(back - a)) < 1e-13
+
+
+@pytest.mark.parametrize("shape", [(128, 256), (2, 1024), (1024, 4)])
+def test_fft_matches_a_library_fft_at_every_stage_count(shape):
+    """Large lengths (up to the 10 stages of 1024) against numpy's FFT, a
+    library routine that shares nothing with the oracle's code."""
+    from oracle import fft as dft
+    rng = np.random.default_rng(4)
+    a = rng.normal(size=shape) + 1j * rng.normal(size=shape)
+    got = dft.fft2(torch.tensor(a)).numpy()
+    ref = np.fft.fft2(a)
+    assert np.max(np.abs(got - ref)) < 1e-13 * np.max(np.abs(ref))
+    assert np.max(np.abs(dft.ifft2(torch.tensor(a)).numpy() - np.fft.ifft2(a))) < 1e-15 * np.abs(a).sum()
+
+
+def test_fft_gradient_is_the_adjoint_map():
+    """The DFT's vector-Jacobian products (used by the oracle's autograd
+    gradients) against numerical differentiation."""
+    from oracle import fft as dft
+    x = torch.randn(4, 8, dtype=torch.complex128, requires_grad=True)
+    assert torch.autograd.gradcheck(lambda t: dft.fft2(t), (x,))
+    assert torch.autograd.gradcheck(lambda t: dft.ifft2(t * t), (x,))
+
+
+def test_oracle_uses_no_library_fft():
+    """The oracle's sources call no library FFT (torch.fft, numpy.fft, scipy)."""
+    import glob
+    import re
+    root = os.path.join(os.path.dirname(os.path.dirname(__file__)), "oracle")
+    for f in glob.glob(os.path.join(root, "*.py")) + glob.glob(os.path.join(root, "*.c")):
+        code = open(f).read()
+        assert not re.search(r"torch\.fft|np\.fft|numpy\.fft|scipy\.fft|fftpack|fftw", code,
+                             re.I), f
 
 
 def test_wavenumber_bins_match_plane_waves():
