@@ -101,61 +101,97 @@ class Clocks:
                 "samples": len(sm)}
 
 
-# ----------------------------------------------------- plain FP64 GPU form ----
+# --------------------------------------------- plain GPU forms (comparisons) ----
 
-def plain_form(w, dev: str = "cuda", f64=torch.float64):
-    """The same split step written plainly in PyTorch: complex fields with
-    torch.fft, one instance, unfused elementwise ops (real type f64; complex
-    the matching type).  Returns (A_F(0), A_SH(0), step), step(a, s, z)
-    advancing one z-step from z."""
-    c128 = torch.complex128 if f64 == torch.float64 else torch.complex64
+def plain_group_form(ws, dev: str = "cuda", real=torch.float64):
+    """The same split step written plainly in PyTorch for B instances of one
+    grid: complex fields [B, ny, nx], torch.fft over the last two axes (cuFFT
+    on the GPU) and unfused elementwise operations, in the real type `real`
+    (complex the matching type).  This is the design the paper describes
+    (Sec. 4: cuFFT plus separate elementwise kernels), batched.
+    Returns (A_F(0), A_SH(0), step); step(a, s, z) advances one z-step from z
+    (a float, or a 0-d float64 tensor on `dev` so that a CUDA graph can
+    replay the step)."""
+    cdt = torch.complex128 if real == torch.float64 else torch.complex64
+    f64 = torch.float64
+    w = ws[0]
+    for v in ws:
+        assert (v.nx, v.ny, v.nz, v.L, v.lambda_f, v.n_f, v.n_sh, v.d_eff) == \
+            (w.nx, w.ny, w.nz, w.L, w.lambda_f, w.n_f, w.n_sh, w.d_eff)
+        assert (v.alpha_f, v.alpha_sh, v.beta_f, v.beta_sh, v.dk0, v.ddk_dT, v.dn_dT) == \
+            (w.alpha_f, w.alpha_sh, w.beta_f, w.beta_sh, w.dk0, w.ddk_dT, w.dn_dT)
+    B = len(ws)
     eps0c = 8.8541878128e-12 * 299792458.0
     nx, ny, dz = w.nx, w.ny, w.L / w.nz
-    x = (torch.arange(nx, dtype=f64, device=dev) - nx // 2) * (w.lx / nx)
-    y = (torch.arange(ny, dtype=f64, device=dev) - ny // 2) * (w.ly / ny)
+
+    def col(vals, dt=f64):
+        return torch.tensor([float(v) for v in vals], dtype=dt, device=dev)
+
+    lx, ly = col(v.lx for v in ws), col(v.ly for v in ws)
+    x = (torch.arange(nx, dtype=f64, device=dev) - nx // 2)[None, :] * (lx / nx)[:, None]
+    y = (torch.arange(ny, dtype=f64, device=dev) - ny // 2)[None, :] * (ly / ny)[:, None]
     kF = 2 * math.pi * w.n_f / w.lambda_f
     kS = 2 * math.pi * w.n_sh / (w.lambda_f / 2)
-    zr = w.w0 ** 2 * kF / 2
-    q = complex(1.0, -w.z_focus / zr)
-    r2 = (x[None, :] ** 2 + y[:, None] ** 2).to(c128)
-    AF = torch.exp(-r2 / (w.w0 ** 2 * q)) / q
-    AF = AF * math.sqrt(w.p1 / float(0.5 * eps0c * w.n_f * (AF.abs() ** 2).sum()
-                                     * (w.lx / nx) * (w.ly / ny)))
+    w0 = col(v.w0 for v in ws)[:, None, None]
+    zr = w0 ** 2 * kF / 2
+    q = torch.complex(torch.ones_like(zr), -col(v.z_focus for v in ws)[:, None, None] / zr)
+    r2 = (x[:, None, :] ** 2 + y[:, :, None] ** 2).to(torch.complex128)
+    AF = torch.exp(-r2 / (w0 ** 2 * q)) / q
+    dxdy = (lx / nx) * (ly / ny)
+    pw = 0.5 * eps0c * w.n_f * (AF.abs() ** 2).sum(dim=(1, 2)) * dxdy
+    AF = (AF * torch.sqrt(col(v.p1 for v in ws) / pw)[:, None, None]).to(cdt)
     AS = torch.zeros_like(AF)
-    Kx = 2 * math.pi * torch.fft.fftfreq(nx, d=w.lx / nx, dtype=f64, device=dev)
-    Ky = 2 * math.pi * torch.fft.fftfreq(ny, d=w.ly / ny, dtype=f64, device=dev)
-    K2 = Kx[None, :] ** 2 + Ky[:, None] ** 2
-    PF = torch.exp(-1j * K2 * dz / (2 * kF)) * math.exp(-w.alpha_f * dz / 2)
-    PS = torch.exp(-1j * K2 * dz / (2 * kS)) * math.exp(-w.alpha_sh * dz / 2)
-    dT = torch.as_tensor(w.dT, dtype=f64, device=dev)
-    tz, ty, tx = dT.shape
+
+    def freq(n, length):
+        b = torch.arange(n, dtype=f64, device=dev)
+        m = torch.where(b < (n + 1) // 2, b, b - n)
+        return 2 * math.pi * m[None, :] / length[:, None]
+
+    Kx, Ky = freq(nx, lx), freq(ny, ly)
+    K2 = Kx[:, None, :] ** 2 + Ky[:, :, None] ** 2
+    PF = (torch.exp(-1j * K2 * dz / (2 * kF)) * math.exp(-w.alpha_f * dz / 2)).to(cdt)
+    PS = (torch.exp(-1j * K2 * dz / (2 * kS)) * math.exp(-w.alpha_sh * dz / 2)).to(cdt)
+    dT = torch.stack([torch.as_tensor(v.dT, dtype=f64) for v in ws]).to(dev)
+    _, tz, ty, tx = dT.shape
     dZ = w.L / (tz - 1)
-    C = torch.cumsum(torch.cat([torch.zeros_like(dT[:1]), 0.5 * dZ * (dT[1:] + dT[:-1])]), 0)
+    C = torch.cumsum(torch.cat([torch.zeros_like(dT[:, :1]),
+                                0.5 * dZ * (dT[:, 1:] + dT[:, :-1])], 1), 1)
+    dT, C = dT.to(real), C.to(real)
 
-    def cell(coord, lo, n, length):
-        u = ((coord - lo) / (length / (n - 1))).clamp(0, n - 1)
+    def cell(coord, length, n):
+        u = ((coord + length[:, None] / 2) / (length[:, None] / (n - 1))).clamp(0, n - 1)
         i = torch.floor(u).clamp(max=n - 2)
-        return i.long(), u - i
+        return i.long(), (u - i).to(real)
 
-    ix, fx = cell(x, -w.t_lx / 2, tx, w.t_lx)
-    iy, fy = cell(y, -w.t_ly / 2, ty, w.t_ly)
+    ix, fx = cell(x, col(v.t_lx for v in ws), tx)
+    iy, fy = cell(y, col(v.t_ly for v in ws), ty)
+    bidx = torch.arange(B, device=dev)[:, None, None]
+    fxr, fyc = fx[:, None, :], fy[:, :, None]
 
     def bil(t2):
-        a = t2[iy][:, ix]; b = t2[iy][:, ix + 1]; c = t2[iy + 1][:, ix]; d = t2[iy + 1][:, ix + 1]
-        return (1 - fy[:, None]) * ((1 - fx) * a + fx * b) + fy[:, None] * ((1 - fx) * c + fx * d)
+        a = t2[bidx, iy[:, :, None], ix[:, None, :]]
+        b = t2[bidx, iy[:, :, None], ix[:, None, :] + 1]
+        c = t2[bidx, iy[:, :, None] + 1, ix[:, None, :]]
+        d = t2[bidx, iy[:, :, None] + 1, ix[:, None, :] + 1]
+        return (1 - fyc) * ((1 - fxr) * a + fxr * b) + fyc * ((1 - fxr) * c + fxr * d)
 
     cF, cS = 0.5 * eps0c * w.n_f, 0.5 * eps0c * w.n_sh
     kapF = 2 * math.pi * w.d_eff / (w.n_f * w.lambda_f)
     kapS = 2 * math.pi * w.d_eff / (w.n_sh * w.lambda_f)
     k0F, k0S = 2 * math.pi / w.lambda_f, 4 * math.pi / w.lambda_f
+    toff = col([v.t_off for v in ws], real)[:, None, None]
 
     def coef(z):
-        u = min(max(z / dZ, 0.0), tz - 1.0)
-        l = min(int(u), tz - 2)
-        t = u - l
-        d = (1 - t) * bil(dT[l]) + t * bil(dT[l + 1]) + w.t_off
-        c = (1 - t) * bil(C[l]) + t * bil(C[l + 1])
-        phi = (w.dk0 + w.ddk_dT * w.t_off) * z + w.ddk_dT * c
+        zt = torch.as_tensor(z, dtype=f64, device=dev)
+        u = (zt / dZ).clamp(0.0, tz - 1.0)
+        l = torch.floor(u).clamp(max=tz - 2)
+        t = (u - l).to(real)
+        li = l.long().reshape(1)
+        d0, d1 = dT.index_select(1, li)[:, 0], dT.index_select(1, li + 1)[:, 0]
+        c0, c1 = C.index_select(1, li)[:, 0], C.index_select(1, li + 1)[:, 0]
+        d = (1 - t) * bil(d0) + t * bil(d1) + toff
+        c = (1 - t) * bil(c0) + t * bil(c1)
+        phi = (w.dk0 + w.ddk_dT * toff) * zt.to(real) + w.ddk_dT * c
         return torch.exp(1j * phi), k0F * w.dn_dT * d, k0S * w.dn_dT * d
 
     def rhs(a, s, cf):
@@ -183,20 +219,57 @@ def plain_form(w, dev: str = "cuda", f64=torch.float64):
     return AF, AS, step
 
 
-def plain_gpu_rate(w, nsteps: int, real=torch.float64) -> float:
-    """plain_form on the GPU (complex128 by default; complex64 is the paper's
-    own design: cuFFT plus unfused elementwise steps in FP32).  Returns
-    grid-point-steps/s over `nsteps` z-steps."""
-    AF, AS, step = plain_form(w, "cuda", real)
-    nx, ny, dz = w.nx, w.ny, w.L / w.nz
-    for k in range(3):
-        AF, AS = step(AF, AS, k * dz)
+def plain_form(w, dev: str = "cuda", real=torch.float64):
+    """plain_group_form for one instance, fields [ny, nx]."""
+    AF, AS, step = plain_group_form([w], dev, real)
+
+    def step1(a, s, z):
+        a2, s2 = step(a[None], s[None], z)
+        return a2[0], s2[0]
+
+    return AF[0], AS[0], step1
+
+
+def plain_gpu_rate(ws, nsteps: int, real=torch.float64):
+    """plain_group_form on the GPU with one z-step captured in a CUDA graph
+    and replayed (so the timing is of the kernels, not of Python dispatch).
+    Returns (grid-point-steps/s over `nsteps` z-steps, how it ran)."""
+    AF, AS, step = plain_group_form(ws, "cuda", real)
+    nx, ny, dz = ws[0].nx, ws[0].ny, ws[0].L / ws[0].nz
+    zt = torch.zeros((), dtype=torch.float64, device="cuda")
+    a_buf, s_buf = AF.clone(), AS.clone()
+
+    def body():
+        a, s = step(a_buf, s_buf, zt)
+        a_buf.copy_(a)
+        s_buf.copy_(s)
+
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        for _ in range(3):
+            body()
+    torch.cuda.current_stream().wait_stream(side)
+    how = "one z-step captured in a CUDA graph, replayed"
+    try:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            body()
+        run = graph.replay
+    except Exception as e:  # capture refused: time the same step eagerly
+        how = f"eager (graph capture failed: {type(e).__name__})"
+        run = body
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    run()
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
+    e0.record(stream)
     for k in range(nsteps):
-        AF, AS = step(AF, AS, (3 + k) * dz)
+        zt.fill_(k * dz)
+        run()
+    e1.record(stream)
     torch.cuda.synchronize()
-    return nx * ny * nsteps / (time.perf_counter() - t0)
+    return len(ws) * nx * ny * nsteps / (e0.elapsed_time(e1) * 1e-3), how
 
 
 # ------------------------------------------------------------------ oracle ----
@@ -216,6 +289,39 @@ def oracle_sample_rate(instances, nsteps: int):
     return pts / dt, dt
 
 
+def oracle_threads(n: int = 0) -> int:
+    """Set (n > 0) and return the oracle's thread count: PyTorch's CPU ops
+    and the OpenMP loop of its C DFT use the same number."""
+    from oracle import fft as oracle_fft
+    if n > 0:
+        torch.set_num_threads(n)
+        oracle_fft.set_threads(n)
+    else:
+        oracle_fft.set_threads(torch.get_num_threads())
+    return torch.get_num_threads()
+
+
+def oracle_baseline(sample, nsteps: int, single_steps: int):
+    """Best of three timed runs on all host threads, plus one run on one
+    thread (per-core context)."""
+    cores = oracle_threads()
+    runs = [oracle_sample_rate(sample, nsteps) for _ in range(3)]
+    rate = max(r for r, _ in runs)
+    out = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "nproc": os.cpu_count(),
+           "sample": f"best of 3 runs of {nsteps} z-steps of one instance per grid size "
+                     f"({', '.join(f'{w.nx}^2' for w in sample)}), "
+                     f"{sum(dt for _, dt in runs):.1f} s of CPU work"}
+    if single_steps > 0:
+        oracle_threads(1)
+        r1, dt1 = oracle_sample_rate(sample, single_steps)
+        oracle_threads(cores)
+        out["single_core"] = {"value": r1, "unit": UNIT,
+                              "sample": f"{single_steps} z-steps per instance, 1 thread, "
+                                        f"{dt1:.1f} s"}
+    return out
+
+
 def sample_instances(insts):
     """First instance of every grid size of the sweep."""
     seen, out = set(), []
@@ -232,6 +338,7 @@ def run_reference(args, rank):
     insts = W.sweep_instances(seed=1)
     sample = sample_instances(insts)
     nsteps = args.ref_zsteps
+    cores = oracle_threads()
     for _ in range(args.warmup):
         oracle_sample_rate(sample, nsteps)
     rates, times = [], []
@@ -248,7 +355,7 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "sweep_384_mixed_nz2000", "sample": desc},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT,
-                             "cores": torch.get_num_threads(), "sample": desc},
+                             "cores": cores, "sample": desc},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -273,6 +380,170 @@ def aggregate_rate(point_steps_local: float, seconds_local: float, world: int, d
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     torch.distributed.all_reduce(n, op=torch.distributed.ReduceOp.SUM)
     return float(n) / float(t), float(t)
+
+
+# ------------------------------------------------------------ every config ----
+
+GOLDEN = os.path.join(ROOT, "tests", "golden")
+
+
+def golden(name):
+    """Stored oracle values (written by tests/golden/make_golden.py, which
+    calls only the FP64 oracle), or None if that file is absent."""
+    path = os.path.join(GOLDEN, name)
+    if not os.path.exists(path):
+        return None
+    if path.endswith(".json"):
+        return json.load(open(path))
+    return dict(np.load(path))
+
+
+def _rel(a, b):
+    return abs(a / b - 1) if b else abs(a)
+
+
+def _event_ms(fn, reps, stream):
+    """CUDA-event time of fn() (which may synchronise) on `stream`, per call."""
+    out = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out.append(e0.elapsed_time(e1))
+    return out
+
+
+def _pass_roof(pkg, plan, w, stream, fp32_peak, fp64_peak, l2_gbs, hbm_gbs, thermal):
+    """Row and column launch times of one plan (CUDA events) and their
+    fractions of the binding roofs."""
+    t = min((pkg.shg_pass_times([plan.handle], nsteps=10, stream=stream)[0] for _ in range(3)),
+            key=lambda g: g["row_ms"] + g["col_ms"])
+    npts = w.nx * w.ny
+    fp64 = getattr(w, "precision", "f32") == "f64"
+    peak = fp64_peak if fp64 else fp32_peak
+    row_flops = row_flops_per_point(w.nx, thermal) * npts
+    col_bytes = col_bytes_per_point() * (2 if fp64 else 1) * npts
+    return {"row_ms": t["row_ms"], "col_ms": t["col_ms"],
+            "row_alu_frac": row_flops / (t["row_ms"] * 1e-3) / (peak * 1e12),
+            "row_alu_peak_tflops": peak,
+            "col_gbs": col_bytes / (t["col_ms"] * 1e-3) / 1e9,
+            "col_hbm_frac": col_bytes / (t["col_ms"] * 1e-3) / 1e9 / hbm_gbs,
+            "col_l2_frac": col_bytes / (t["col_ms"] * 1e-3) / 1e9 / l2_gbs}
+
+
+def time_configs(pkg, stream, mp, hbm_gbs):
+    """Every workload at full size, timed through the C ABI with CUDA events
+    on `stream`, with its error against stored FP64-oracle values."""
+    fp32, fp64, l2 = mp["fp32_peak_tflops"], mp["fp64_tflops"], mp["l2_read_gbs"]
+    out = {}
+    cfg_eta = golden("configs_eta.json") or {}
+
+    # plain: 32^2, nz = 100, FP64, single instance
+    w = W.plain_focused()
+    plan = pkg.Plan(w)
+    run = lambda: (plan.propagate(stream), plan.efficiency())  # noqa: E731
+    run()
+    ms = statistics.median(_event_ms(run, 20, stream))
+    eta = plan.efficiency()[0]
+    e = {"workload": "plain_32x32_nz100_fp64", "value": w.point_steps / (ms * 1e-3),
+         "unit": UNIT, "ms_per_propagation": ms, "dtype": "f64"}
+    if "plain" in cfg_eta:
+        e["eta_rel_err_vs_oracle"] = _rel(eta, cfg_eta["plain"]["eta"])
+    e["passes"] = _pass_roof(pkg, plan, w, stream, fp32, fp64, l2, hbm_gbs, False)
+    out["plain"] = e
+    del plan
+
+    # depleted: 128^2, nz = 1000, FP32, seeded map, single instance
+    w = W.depleted_absorbing()
+    plan = pkg.Plan(w)
+    plan.set_temperature(torch.as_tensor(w.dT), w.t_lx, w.t_ly)
+    run = lambda: (plan.propagate(stream), plan.efficiency())  # noqa: E731
+    run()
+    ms = statistics.median(_event_ms(run, 10, stream))
+    eta = plan.efficiency()[0]
+    e = {"workload": "depleted_128x128_nz1000", "value": w.point_steps / (ms * 1e-3),
+         "unit": UNIT, "ms_per_propagation": ms, "us_per_z_step": 1e3 * ms / w.nz,
+         "dtype": "f32"}
+    if "depleted" in cfg_eta:
+        e["eta_rel_err_vs_oracle"] = _rel(eta, cfg_eta["depleted"]["eta"])
+    e["passes"] = _pass_roof(pkg, plan, w, stream, fp32, fp64, l2, hbm_gbs, True)
+    out["depleted"] = e
+    del plan
+
+    # adjoint: 256^2, nz = 2000, FP32, forward + reverse sweep
+    w = W.adjoint_case()
+    plan = pkg.Plan(w, adjoint=True)
+    dT = torch.as_tensor(w.dT).cuda()
+    plan.set_temperature(dT, w.t_lx, w.t_ly)
+    g_dT = torch.empty_like(dT)
+    fwd = lambda: (plan.propagate(stream), plan.efficiency())  # noqa: E731
+    bwd = lambda: pkg.shg_propagate_adjoint(plan.handle, 1.0, g_dT, stream)  # noqa: E731
+    fwd()
+    bwd()
+    f_ms = statistics.median(_event_ms(fwd, 3, stream))
+    b_ms = statistics.median(_event_ms(lambda: (fwd(), bwd()), 3, stream)) - f_ms
+    eta = plan.efficiency()[0]
+    gw, gz, gt = bwd()
+    e = {"workload": "adjoint_256x256_nz2000", "value": w.point_steps / (f_ms * 1e-3),
+         "unit": UNIT, "forward_ms": f_ms, "backward_ms": b_ms,
+         "forward_plus_backward_point_steps_per_s": w.point_steps / ((f_ms + b_ms) * 1e-3),
+         "dtype": "f32"}
+    fd = golden("adjoint_fd_256_nz2000.json")
+    if fd is not None:
+        e["eta_rel_err_vs_oracle"] = _rel(eta, fd["eta"])
+        gT = g_dT.double().cpu().numpy()
+        scale_t = float(np.abs(gT).sum())   # 1 K applied to every node
+        errs = {"w0": _rel(gw, fd["d_w0"]["value"]), "z_focus": _rel(gz, fd["d_zf"]["value"]),
+                "t_off": abs(gt - fd["d_toff"]["value"]) / max(abs(fd["d_toff"]["value"]),
+                                                               scale_t)}
+        rng = np.random.default_rng(fd["d_map_directions"][0]["seed"])
+        for d in fd["d_map_directions"]:
+            v = rng.normal(size=gT.shape)
+            got = float((gT * v).sum())
+            errs[f"map_direction_{d['index']}"] = abs(got - d["value"]) / max(
+                abs(d["value"]), float(np.abs(gT * v).sum()) * 1e-2)
+        e["gradient_rel_err_vs_oracle_fd"] = errs
+    e["passes"] = _pass_roof(pkg, plan, w, stream, fp32, fp64, l2, hbm_gbs, True)
+    out["adjoint"] = e
+    del plan
+
+    # thermal: 1024^2, nz = 8000, 6 outer iterations with heat solves
+    w = W.thermal_loop()
+    plan = pkg.Plan(w, thermal=True)
+    res = {}
+
+    def loop():
+        res["etas"], res["changes"] = pkg.shg_thermal_loop(plan.handle, w.n_outer, 200000, 1e-6,
+                                                           stream)
+    ms = statistics.median(_event_ms(loop, 1, stream))
+    e = {"workload": "thermal_1024x1024_nz8000_x6", "value": w.n_outer * w.point_steps /
+         (ms * 1e-3), "unit": UNIT, "ms_per_loop": ms, "etas": res["etas"],
+         "changes_K": res["changes"], "dtype": "f32"}
+    tp = golden("thermal_pass_1024_nz8000.npz")
+    if tp is not None:
+        e["first_pass_eta_rel_err_vs_oracle"] = _rel(res["etas"][0], float(tp["eta"]))
+    # heat solves alone: a cold start (dT = 0 with the first pass's deposits)
+    # and a warm start (from that solution after the second pass)
+    plan2 = pkg.Plan(w, thermal=True)
+    plan2.propagate(stream)
+    plan2.efficiency()
+    sw = {}
+    cold = _event_ms(lambda: sw.__setitem__("cold", pkg.shg_heat_solve(plan2.handle, 200000,
+                                                                       1e-6, stream)), 1, stream)
+    plan2.propagate(stream)
+    plan2.efficiency()
+    warm = _event_ms(lambda: sw.__setitem__("warm", pkg.shg_heat_solve(plan2.handle, 200000,
+                                                                       1e-6, stream)), 1, stream)
+    e["heat_solve"] = {"cold_ms": cold[0], "cold_sweeps": sw["cold"][1],
+                       "warm_ms": warm[0], "warm_sweeps": sw["warm"][1],
+                       "grid": f"{w.hx}x{w.hy}x{w.hz}"}
+    e["passes"] = _pass_roof(pkg, plan, w, stream, fp32, fp64, l2, hbm_gbs, True)
+    out["thermal"] = e
+    del plan, plan2
+    return out
 
 
 # --------------------------------------------------------------- our path ----
@@ -376,12 +647,25 @@ def run_ours(args, rank, world):
                            "d2h_bytes_per_step": d2h},
                       gpu_launches=kernels_per_step * args.steps)
 
-    # ---- per-kernel launch times (CUDA events on the launching stream)
+    # ---- measured ceilings of this device (timed kernels; no setting changes)
     pk = peaks()
+    mpk = pkg.shg_measure_peaks(stream)
+    fp32_peak = max(mpk["fp32_tflops"], mpk["fp32_scalar_tflops"])
+    mp = dict(mpk, fp32_peak_tflops=fp32_peak)
+
+    # ---- per-kernel launch times (CUDA events on the launching stream)
     pkg.shg_pass_times(handles, nsteps=2, stream=stream)
     runs = [pkg.shg_pass_times(handles, nsteps=10, stream=stream) for _ in range(3)]
     times = [dict(g, row_ms=min(r[i]["row_ms"] for r in runs), col_ms=min(r[i]["col_ms"] for r in runs))
              for i, g in enumerate(runs[0])]
+    for g in times:
+        npts = g["nx"] * g["ny"] * g["instances"]
+        g["row_alu_frac"] = (row_flops_per_point(g["nx"], True) * npts / (g["row_ms"] * 1e-3)
+                             / (fp32_peak * 1e12))
+        gbs = col_bytes_per_point() * npts / (g["col_ms"] * 1e-3) / 1e9
+        g["col_gbs"] = gbs
+        g["col_hbm_frac"] = gbs / pk["hbm_gbs"]
+        g["col_l2_frac"] = gbs / mpk["l2_read_gbs"]
     best = None
     for g in times:
         npts = g["nx"] * g["ny"] * g["instances"]
@@ -393,11 +677,13 @@ def run_ours(args, rank, world):
     _, kind, g, t_ms, npts = best
     if kind == "row":
         flops = row_flops_per_point(g["nx"], True) * npts
-        peak = N_SM * FP32_LANES_PER_SM * 2 * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
         achieved = flops / (t_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "kernel": f"k_row_pass<float,{g['nx']}>", "achieved": achieved,
-                "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x sm_max_mhz",
+                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+                "peak_source": "measured: FP32 FMA throughput kernel (shg_measure_peaks), "
+                               "burst, timed alone like the pass",
+                "derived_peak_at_sm_max": N_SM * FP32_LANES_PER_SM * 2
+                * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
                 "algorithmic_per_point": row_flops_per_point(g["nx"], True),
                 "points_per_launch": npts, "launch_ms": t_ms, "traffic": None}
     else:
@@ -417,36 +703,54 @@ def run_ours(args, rank, world):
     if rank == 0:
         result["roofline"] = roof
         result["pass_times_ms"] = times
+        result["measured_peaks"] = dict(mp, hbm_gbs=pk["hbm_gbs"],
+                                        how="shg_measure_peaks on this GPU during this run; "
+                                            "HBM from MEASURED_PEAKS.json")
 
-    # ---- comparisons (rank 0, N = 1): plain FP64 GPU form, oracle, eta check
+    # ---- comparisons (rank 0, N = 1): plain GPU forms, oracle, eta check, every config
     if rank == 0 and world == 1 and not args.skip_baselines:
-        w256 = [w for w in insts if w.nx == 256][0]
-        plain = plain_gpu_rate(w256, 50)
-        result["plain_fp64_gpu"] = {"value": plain, "unit": UNIT,
-                                    "sample": "one 256^2 instance, 50 z-steps, complex128 torch"
-                                              " + torch.fft, unfused",
-                                    "speedup_of_fused_fp32": value / plain}
+        g256 = [w for w in insts if w.nx == 256]
+        fused_256 = [g for g in times if g["nx"] == 256]
         try:
-            p32 = plain_gpu_rate(w256, 200, torch.float32)
-            result["plain_fp32_gpu"] = {"value": p32, "unit": UNIT,
-                                        "sample": "one 256^2 instance, 200 z-steps, complex64 torch"
-                                                  " + torch.fft (cuFFT), unfused: the paper's design",
-                                        "speedup_of_fused_fp32": value / p32}
+            plain, how = plain_gpu_rate(g256[:1], 50)
+            result["plain_fp64_gpu"] = {
+                "value": plain, "unit": UNIT,
+                "sample": f"one 256^2 instance, 50 z-steps, complex128 torch + torch.fft, "
+                          f"unfused; {how}",
+                "speedup_of_fused_fp32": value / plain}
         except Exception as e:  # a comparison only: never lose the measured line for it
+            result["plain_fp64_gpu"] = {"error": f"{type(e).__name__}: {e}"[:200]}
+        try:
+            p32, how = plain_gpu_rate(g256, 50, torch.float32)
+            ent = {"value": p32, "unit": UNIT,
+                   "sample": f"all {len(g256)} 256^2 instances of the sweep batched, 50 z-steps, "
+                             f"complex64 torch + torch.fft (cuFFT) with unfused elementwise "
+                             f"steps (the paper's design); {how}",
+                   "speedup_of_fused_fp32": value / p32}
+            if fused_256:
+                f = fused_256[0]
+                rate = f["nx"] * f["ny"] * f["instances"] / ((f["row_ms"] + f["col_ms"]) * 1e-3)
+                ent["fused_same_group"] = rate
+                ent["speedup_of_fused_same_group"] = rate / p32
+            result["plain_fp32_gpu"] = ent
+        except Exception as e:
             result["plain_fp32_gpu"] = {"error": f"{type(e).__name__}: {e}"[:200]}
         sample = sample_instances(insts)
-        nref = 3 * args.ref_zsteps  # about 10-15 s of CPU work
-        rate, dt = oracle_sample_rate(sample, nref)
-        result["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": torch.get_num_threads(),
-                                  "kind": "oracle",
-                                  "sample": f"{nref} z-steps of one instance per grid "
-                                            f"size ({dt:.1f} s of CPU work)"}
-        # eta against the FP64 oracle on a full-length instance
-        from oracle import ssfm
+        result["cpu_baseline"] = oracle_baseline(sample, args.ref_zsteps // 2 + 10, 10)
+        # eta of the first instance against the FP64 oracle at full length
+        cfg_eta = golden("configs_eta.json") or {}
         w0 = insts[0]
-        _, _, eta_ref = ssfm.run(w0)
-        result["eta_rel_err_vs_oracle"] = {"instance": w0.name,
-                                           "value": abs(etas[0] / float(eta_ref) - 1)}
+        if args.nz == 2000 and not args.groups and w0.name in cfg_eta.get("sweep", {}):
+            eta_ref = cfg_eta["sweep"][w0.name]["eta"]
+            src_ref = "stored FP64-oracle value (tests/golden/configs_eta.json)"
+        else:
+            from oracle import ssfm
+            eta_ref = float(ssfm.run(w0)[2])
+            src_ref = "FP64 oracle run live"
+        result["eta_rel_err_vs_oracle"] = {"instance": w0.name, "value": _rel(etas[0], eta_ref),
+                                           "oracle": src_ref}
+        if not args.skip_configs:
+            result["configs"] = time_configs(pkg, stream, mp, pk["hbm_gbs"])
     if rank == 0:
         print(json.dumps(result), flush=True)
 
@@ -458,7 +762,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--ref-zsteps", type=int, default=100)
-    ap.add_argument("--skip-baselines", action="store_true")
+    ap.add_argument("--skip-baselines", action="store_true",
+                    help="only the sweep line (no comparisons, no other configs)")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="no timing of the other workloads")
     ap.add_argument("--nz", type=int, default=2000,
                     help="z-steps per instance (2000 is the benchmarked workload; smaller "
                          "values are for profiling captures)")

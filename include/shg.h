@@ -185,6 +185,26 @@ shg_status_t shg_efficiency(shg_plan_t *plan, double *eta, double *p_f, double *
 shg_status_t shg_get_fields(shg_plan_t *plan, void *a_f_dev, void *a_sh_dev,
                             shg_stream_t stream);
 
+/* Power monitor (Manley-Rowe balance along the crystal).  With every > 0,
+ * each later propagation of the plan (single or batched) records the
+ * discrete powers P_F(z_s), P_SH(z_s) = (1/2) eps0 c n_j sum |A_j|^2 dx dy
+ * (Eq. 17's powers) at z_s = s dz for s = 0, every, 2 every, ... and at
+ * s = nz, summed in double precision inside the row pass at the point where
+ * the state is exactly at z_s.  Without losses (alpha = beta = 0) the total
+ * P_F + P_SH is conserved by Eqs. (1)-(2) (Manley-Rowe), so its drift is the
+ * split-step rounding error; with losses it traces the absorbed power.
+ * every = 0 turns it off.  Allocates nz/every + 2 pairs of doubles; drops
+ * the plan's captured graphs and the result of the last propagation.
+ * SHG_ERR_INVALID_ARG for every < 0. */
+shg_status_t shg_set_monitor(shg_plan_t *plan, int every);
+
+/* The monitor's samples of the last propagation: z (m), P_F and P_SH (W)
+ * for up to max_samples samples (host arrays, any may be NULL);
+ * *n_samples = the number recorded.  SHG_ERR_STATE without a monitor or a
+ * propagation since it was set.  Synchronises the last propagation's stream. */
+shg_status_t shg_get_monitor(shg_plan_t *plan, double *z_out, double *p_f_out, double *p_sh_out,
+                             int max_samples, int *n_samples);
+
 /* Reverse sweep of the exact discrete forward map (conjugate propagator,
  * transposed RK4 with Wirtinger calculus), seeded with d_eta = dJ/deta, using
  * the sqrt(nz) checkpoints of the last propagation (shg_propagate or
@@ -244,6 +264,23 @@ shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
  * max_groups.  Synchronises `stream`. */
 shg_status_t shg_pass_times(shg_plan_t *const *plans, int n, int nsteps, double *out,
                             int *inst_out, int max_groups, int *ngroups, shg_stream_t stream);
+
+/* Measurement aid (Sec. 4.3 reports speed-ups only; a roofline needs the
+ * device's own ceilings).  Times, with CUDA events on `stream`, best of 5
+ * launches after a warm-up:
+ *   fp32_tflops: packed two-lane FP32 FMAs (fma.rn.f32x2), 8 independent
+ *                chains per thread, 8 CTAs of 256 threads per SM, in TFLOP/s
+ *                (an FMA counts 2 flops);
+ *   fp32_scalar_tflops: the same with scalar FMAs;
+ *   fp64_tflops: scalar double-precision FMAs, 8 chains per thread;
+ *   l2_read_gbs: 16 re-reads of a 32 MiB buffer (resident in L2) with
+ *                16-byte L2-only loads, in GB/s.
+ * Any output may be NULL (not all).  Allocates and frees its buffers on
+ * `stream` (stream-ordered allocator); changes no clock or device setting.
+ * Synchronises `stream`. */
+shg_status_t shg_measure_peaks(double *fp32_tflops, double *l2_read_gbs,
+                               double *fp32_scalar_tflops, double *fp64_tflops,
+                               shg_stream_t stream);
 
 /* Powers P_F, P_SH = (1/2) eps0 c n_j sum |A_j|^2 dx dy of fields the caller
  * already holds, written to memory the caller already holds, with no device

@@ -16,6 +16,9 @@
  */
 #include <math.h>
 #include <stdlib.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 static const double kPi = 3.14159265358979323846;
 
@@ -70,4 +73,16 @@ int oracle_dft_rows(double *data, long count, long n, int sign)
     }
     free(tw);
     return 0;
+}
+
+/* Threads of the row loop (no effect without OpenMP); returns the count used. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -64,8 +64,15 @@ def _load():
             lib.oracle_dft_rows.argtypes = [ctypes.c_void_p, ctypes.c_long, ctypes.c_long,
                                             ctypes.c_int]
             lib.oracle_dft_rows.restype = ctypes.c_int
+            lib.oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.oracle_set_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
+
+
+def set_threads(n: int) -> int:
+    """Threads of the DFT's row loop (n <= 0 only queries); returns the count."""
+    return int(_load().oracle_set_threads(int(n)))
 
 
 def _rows(x: torch.Tensor, sign: int) -> torch.Tensor:

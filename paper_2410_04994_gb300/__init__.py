@@ -84,6 +84,9 @@ _SIGS = {
     "shg_get_heat": [_P, _P, _P, _P],
     "shg_pass_times": [ctypes.POINTER(_P), _I, _I, _DP, _IP, _I, _IP, _P],
     "shg_field_powers_noalloc": [_P, _I, _I, _I, _I, _D, _D, _D, _D, _P, _P],
+    "shg_measure_peaks": [_DP, _DP, _DP, _DP, _P],
+    "shg_set_monitor": [_P, _I],
+    "shg_get_monitor": [_P, _DP, _DP, _DP, _I, _IP],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
 
@@ -313,6 +316,30 @@ def shg_field_powers_noalloc(fields, nx: int, ny: int, n_inst: int, lx: float, l
     _check(_lib().shg_field_powers_noalloc(_ptr(fields), nx, ny, n_inst, fp64, float(lx),
                                            float(ly), float(n_f), float(n_sh), _ptr(powers),
                                            _stream(stream)), "shg_field_powers_noalloc")
+
+
+def shg_set_monitor(plan: int, every: int) -> None:
+    _check(_lib().shg_set_monitor(plan, int(every)), "shg_set_monitor")
+
+
+def shg_get_monitor(plan: int):
+    """(z, P_F, P_SH) lists of the power monitor's samples of the last
+    propagation (see include/shg.h)."""
+    n = _I()
+    _check(_lib().shg_get_monitor(plan, None, None, None, 0, ctypes.byref(n)), "shg_get_monitor")
+    z, pf, psh = (_D * n.value)(), (_D * n.value)(), (_D * n.value)()
+    _check(_lib().shg_get_monitor(plan, z, pf, psh, n.value, ctypes.byref(n)), "shg_get_monitor")
+    return list(z), list(pf), list(psh)
+
+
+def shg_measure_peaks(stream=None):
+    """Measured FP32 FMA throughput (packed and scalar), FP64 FMA throughput
+    (TFLOP/s) and L2 read bandwidth (GB/s) of the current device."""
+    f, l2, fs, f64 = _D(), _D(), _D(), _D()
+    _check(_lib().shg_measure_peaks(ctypes.byref(f), ctypes.byref(l2), ctypes.byref(fs),
+                                    ctypes.byref(f64), _stream(stream)), "shg_measure_peaks")
+    return {"fp32_tflops": f.value, "fp32_scalar_tflops": fs.value, "fp64_tflops": f64.value,
+            "l2_read_gbs": l2.value}
 
 
 def shg_status_string(status: int) -> str:

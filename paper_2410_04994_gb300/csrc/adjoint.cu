@@ -246,6 +246,7 @@ template <class R> static void fill_adj_descs(shg_plan* p, std::vector<unsigned 
     else
         fill_desc_f32(p, &d);
     d.Q = nullptr;
+    d.mon = nullptr;  // the recomputed segments are not a forward pass to monitor
     InstDesc<R> dw = d, dl = d;
     dw.field = static_cast<cx<R>*>(p->adj->work);
     dl.field = static_cast<cx<R>*>(p->adj->lam);

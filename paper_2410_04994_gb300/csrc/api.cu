@@ -252,6 +252,9 @@ template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void
     d->undepleted = p->b.undepleted ? 1 : 0;
     d->status = p->status;
     d->wait_polls = p->wait_polls;
+    d->mon = p->mon;
+    d->mon_every = p->mon_every > 0 ? p->mon_every : 1;
+    d->mon_last = p->mon_slots - 1;
     if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
         d->Q = p->Q;
         d->hix = p->hix;
@@ -493,6 +496,12 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
             if (e0 != cudaSuccess) return cuda_fail(e0, "memset status");
         }
     }
+    for (shg_plan* p : plans) {
+        if (p->mon) {
+            const cudaError_t e0 = cudaMemsetAsync(p->mon, 0, 2 * p->mon_slots * sizeof(double), st);
+            if (e0 != cudaSuccess) return cuda_fail(e0, "memset monitor");
+        }
+    }
     cudaError_t e = custom ? launch_copy_init(fp64, idescs, ninst, descs, nx, ny, st)
                            : launch_init(fp64, idescs, nullptr, ninst, descs, nx, ny, st);
     if (e != cudaSuccess) return cuda_fail(e, "init");
@@ -732,7 +741,7 @@ static void plan_free(shg_plan* p) {
     void* bufs[] = {p->field, p->field0, p->px,  p->py,  p->pxc,  p->pyc,   p->eph,
                     p->tw,    p->ttab,   p->umap, p->tmap, p->desc, p->idesc, p->red, p->pw,
                     p->Q,     p->hix,    p->hiy, p->hlz,  p->theat, p->theat_prev, p->theat_f,
-                    p->hred,  p->status, p->cmap_dev};
+                    p->hred,  p->status, p->cmap_dev, p->mon};
     for (void* b : bufs)
         if (b) cudaFree(b);
     delete p;
@@ -1005,6 +1014,56 @@ shg_status_t shg_get_fields(shg_plan_t* p, void* a_f_dev, void* a_sh_dev, shg_st
     if (a_f_dev) SHG_CK(cudaMemcpyAsync(a_f_dev, f, one, cudaMemcpyDeviceToDevice, s));
     if (a_sh_dev) SHG_CK(cudaMemcpyAsync(a_sh_dev, f + one, one, cudaMemcpyDeviceToDevice, s));
     return SHG_OK;
+}
+
+shg_status_t shg_set_monitor(shg_plan_t* p, int every) {
+    if (!p || every < 0) return SHG_ERR_INVALID_ARG;
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    if (p->mon) {
+        cudaFree(p->mon);
+        p->mon = nullptr;
+    }
+    p->mon_every = 0;
+    p->mon_slots = 0;
+    if (every > 0) {
+        const int nz = p->g.nz;
+        const int slots = nz / every + 1 + (nz % every != 0 ? 1 : 0);
+        SHG_CK(cudaMalloc((void**)&p->mon, 2 * size_t(slots) * sizeof(double)));
+        SHG_CK(cudaMemset(p->mon, 0, 2 * size_t(slots) * sizeof(double)));
+        p->mon_every = every;
+        p->mon_slots = slots;
+    }
+    // captured graphs hold the old monitor buffer (its memset node)
+    p->gvalid = false;
+    forget_plan_batches(p);
+    p->has_result = false;
+    return upload_desc(p);
+}
+
+shg_status_t shg_get_monitor(shg_plan_t* p, double* z_out, double* p_f_out, double* p_sh_out,
+                             int max_samples, int* n_samples) {
+    if (!p || max_samples < 0) return SHG_ERR_INVALID_ARG;
+    if (!p->mon || !p->has_result) return SHG_ERR_STATE;
+    SHG_CK(cudaStreamSynchronize(p->last_stream));
+    std::vector<double> h(2 * size_t(p->mon_slots));
+    SHG_CK(cudaMemcpy(h.data(), p->mon, h.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    const double dxdy = (p->g.lx / p->g.nx) * (p->g.ly / p->g.ny);
+    const double cF = 0.5 * kEps0 * kCLight * p->c.n_f * dxdy;
+    const double cS = 0.5 * kEps0 * kCLight * p->c.n_sh * dxdy;
+    const double dz = p->c.L / p->g.nz;
+    const int n = std::min(max_samples, p->mon_slots);
+    bool finite = true;
+    for (int m = 0; m < n; ++m) {
+        const bool last = (m == p->mon_slots - 1);
+        const int s = last ? p->g.nz : m * p->mon_every;
+        if (z_out) z_out[m] = s * dz;
+        if (p_f_out) p_f_out[m] = cF * h[2 * m];
+        if (p_sh_out) p_sh_out[m] = cS * h[2 * m + 1];
+        finite &= std::isfinite(h[2 * m]) && std::isfinite(h[2 * m + 1]);
+    }
+    if (n_samples) *n_samples = p->mon_slots;
+    return finite ? SHG_OK : SHG_ERR_NONFINITE;
 }
 
 }  // extern "C"

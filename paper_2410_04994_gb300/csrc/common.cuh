@@ -108,6 +108,11 @@ template <class R> struct InstDesc {
     R dxdy;
     int* status;           // set to a non-zero shg_status_t by a kernel that gave up
     unsigned wait_polls;   // bound on the polls of a device-side wait (0: give up at once)
+    // power monitor: sum |A_F|^2, sum |A_SH|^2 (times eps0 c n_j dx dy / 2 on the
+    // host) at z_s for s % mon_every == 0 and at s = nz, into mon[2 * slot]
+    double* mon;           // [2 * n_slots] or nullptr
+    int mon_every;         // sampling interval in steps (>= 1)
+    int mon_last;          // slot of s = nz when nz % mon_every != 0
 };
 
 // Asynchronous global -> shared copies (LDGSTS), so that a whole tile is in

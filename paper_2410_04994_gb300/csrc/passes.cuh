@@ -205,6 +205,13 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             atomicAdd(&bins[lr * d.hx + i], float(q * w_dep));
         }
     };
+    // Power monitor: this thread's share of sum |A_F|^2, sum |A_SH|^2 at z_s.
+    const bool mon = d.mon != nullptr && (s % d.mon_every == 0 || s == nz);
+    R monF = R(0), monS = R(0);
+    auto monitor = [&](const C& aF, const C& aS) {
+        monF += aF.x * aF.x + aF.y * aF.y;
+        monS += aS.x * aS.x + aS.y * aS.y;
+    };
     // One point: N_b(s-1) [z_s - dz/2 -> z_s], deposit at z_s, N_a(s).
     auto point = [&](int xi, C& aF, C& aS, auto& ts) {
         const Coef<R> cz = coef_at(d, zsh[2], thermal, ts);  // z_s, shared by both halves
@@ -214,6 +221,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             rk4(d, aF, aS, c0, cm, cz, h);
         }
         if (l_dep >= 0 && j_dep >= 0) deposit(xi, aF, aS);
+        if (mon) monitor(aF, aS);
         if (s < nz) {
             const Coef<R> cm = coef_at(d, zsh[3], thermal, ts);
             const Coef<R> c1 = coef_at(d, zsh[4], thermal, ts);
@@ -232,13 +240,19 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
                 const Coef2 cm = cq(1);
                 rk4_2(dsh, F, S, c0, cm, z2, h);
             }
-            if (l_dep >= 0 && j_dep >= 0) {
+            if ((l_dep >= 0 && j_dep >= 0) || mon) {
                 up2(F.r, aF0.x, aF1.x);
                 up2(F.i, aF0.y, aF1.y);
                 up2(S.r, aS0.x, aS1.x);
                 up2(S.i, aS0.y, aS1.y);
-                deposit(xa, aF0, aS0);
-                deposit(xb, aF1, aS1);
+                if (l_dep >= 0 && j_dep >= 0) {
+                    deposit(xa, aF0, aS0);
+                    deposit(xb, aF1, aS1);
+                }
+                if (mon) {
+                    monitor(aF0, aS0);
+                    monitor(aF1, aS1);
+                }
             }
             if (s < nz) {
                 const Coef2 cm = cq(3);
@@ -302,6 +316,19 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
         }
     }
     __syncthreads();  // the transforms read points that other threads advanced
+    if (mon) {
+        // per-warp FP64 sums, one atomic pair per warp
+        double vF = double(monF), vS = double(monS);
+        for (int o = 16; o > 0; o >>= 1) {
+            vF += __shfl_xor_sync(0xffffffffu, vF, o);
+            vS += __shfl_xor_sync(0xffffffffu, vS, o);
+        }
+        if ((threadIdx.x & 31) == 0) {
+            const int slot = (s % d.mon_every == 0) ? s / d.mon_every : d.mon_last;
+            atomicAdd(&d.mon[2 * slot], vF);
+            atomicAdd(&d.mon[2 * slot + 1], vS);
+        }
+    }
     if (dep) {
         __syncthreads();
         const int y0 = blockIdx.x * ROWS;

@@ -88,6 +88,8 @@ struct shg_plan {
     void* cmap_dev = nullptr;
     bool has_cmap = false;
     int* status = nullptr;     // device status word written by kernels that give up
+    double* mon = nullptr;     // power monitor slots [2 * mon_slots] (shg_set_monitor)
+    int mon_every = 0, mon_slots = 0;
     unsigned wait_polls = 1u << 20;  // bound on each device-side wait (shg_set_wait_limit)
 
     // forward graph

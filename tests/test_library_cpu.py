@@ -197,3 +197,10 @@ def test_refused_temperature_update_keeps_the_map(pkg):
     assert lib.shg_set_temperature_batch(arr, 1, maps, 1, 4, 4, ext, ext, None) == 1
     bad = (ctypes.c_double * 1)(float("nan"))
     assert lib.shg_set_temperature_batch(arr, 1, maps, 4, 4, 4, bad, ext, None) == 1
+
+
+def test_monitor_calls_refuse_bad_arguments(pkg):
+    lib = pkg.load()
+    assert lib.shg_set_monitor(None, 1) == 1
+    assert lib.shg_get_monitor(None, None, None, None, 0, None) == 1
+    assert lib.shg_measure_peaks(None, None, None, None, None) == 1
