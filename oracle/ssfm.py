@@ -357,8 +357,19 @@ class HeatDeposit:
         self.Q.index_put_((ll, jj, ii), q[mask].detach(), accumulate=True)
 
     def qdot_nodes(self) -> torch.Tensor:
-        """Node source density q_dot = Q / (hdx hdy hdz)."""
-        return self.Q / (self.hdx * self.hdy * self.hdz)
+        """Node source density q_dot = Q / V, V the volume of the node's cell:
+        hdx hdy hdz, halved once for every face the node lies on (a face
+        node's cell lies half outside the crystal, and only samples inside
+        are binned to it).  Nodes on faces held at T_oven are not solved
+        for, so there the factor has no effect."""
+        hz, hy, hx = self.shape
+        vol = torch.full(self.shape, self.hdx * self.hdy * self.hdz, dtype=F64)
+        for axis, n in ((0, hz), (1, hy), (2, hx)):
+            for end in (0, n - 1):
+                sl = [slice(None)] * 3
+                sl[axis] = end
+                vol[tuple(sl)] *= 0.5
+        return self.Q / vol
 
 
 # ---------------------------------------------------------- propagate ----

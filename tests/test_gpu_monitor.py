@@ -54,22 +54,24 @@ def test_monitor_matches_oracle_powers(precision, tol):
     for (rf, rs), gf, gs in zip(ref, pf, psh):
         assert abs(gf - rf) <= tol * w.p1, (gf, rf)
         assert abs(gs - rs) <= tol * w.p1, (gs, rs)
-    # the last sample is the propagation's own result
-    assert abs(pf[-1] / p_f - 1) < 1e-9 and abs(psh[-1] - p_sh) <= 1e-9 * w.p1
+    # the last sample is the propagation's own result (its FP64 reduction; the
+    # monitor adds up to 16 points per thread in the field precision first)
+    same = 1e-12 if precision == "f64" else 1e-6
+    assert abs(pf[-1] / p_f - 1) < same and abs(psh[-1] - p_sh) <= same * w.p1
     # absorption only removes power
     tot = [a + b for a, b in zip(pf, psh)]
     assert all(b < a for a, b in zip(tot, tot[1:]))
 
 
 def test_manley_rowe_drift_without_losses_fp32():
-    """Lossless depleted SHG at 128 x 128, nz = 400: P_F + P_SH stays at P1
-    to 1e-5 at every sample while the SH grows to a sizeable fraction."""
+    """Lossless depleted SHG at 128 x 128, nz = 400, 200 W (strong conversion,
+    then back-conversion of the focused beams): P_F + P_SH stays at P1 to
+    1e-5 at every sample while the SH power rises to a sizeable fraction."""
     w = W.plain_focused(n=128, nz=400, p1=200.0, precision="f32")
     plan, (eta, _, _), z, pf, psh = _gpu_monitor(w, 20)
-    assert eta > 0.05
     for a, b in zip(pf, psh):
         assert abs((a + b) / w.p1 - 1) < 1e-5, (a + b) / w.p1 - 1
-    assert psh[0] == 0.0 and psh[-1] > psh[len(psh) // 2] > 0
+    assert psh[0] == 0.0 and max(psh) > 0.2 * w.p1
 
 
 def test_monitor_in_a_batch_and_off_again():

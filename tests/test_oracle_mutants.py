@@ -255,14 +255,16 @@ def stencil_spacings_swapped(monkeypatch):
     # 1/dy^2 on the x neighbours and 1/dx^2 on the y neighbours
     orig = heat.jacobi_target
     monkeypatch.setattr(heat, "jacobi_target",
-                        lambda T, q, kappa, dx, dy, dz: orig(T, q, kappa, dy, dx, dz))
+                        lambda T, q, kappa, dx, dy, dz, bc=heat.DIRICHLET:
+                        orig(T, q, kappa, dy, dx, dz, bc))
 
 
 def source_without_conductivity(monkeypatch):
     # q_dot not divided by kappa
     orig = heat.jacobi_target
     monkeypatch.setattr(heat, "jacobi_target",
-                        lambda T, q, kappa, dx, dy, dz: orig(T, q, 1.0, dx, dy, dz))
+                        lambda T, q, kappa, dx, dy, dz, bc=heat.DIRICHLET:
+                        orig(T, q, 1.0, dx, dy, dz, bc))
 
 
 def sh_diffraction_with_kf(self, p):
@@ -350,7 +352,47 @@ def heat_source_sign(monkeypatch):
     # kappa lap T = +q_dot: the source cools
     orig = heat.jacobi_target
     monkeypatch.setattr(heat, "jacobi_target",
-                        lambda T, q, kappa, dx, dy, dz: orig(T, -q, kappa, dx, dy, dz))
+                        lambda T, q, kappa, dx, dy, dz, bc=heat.DIRICHLET:
+                        orig(T, -q, kappa, dx, dy, dz, bc))
+
+
+def ghost_without_doubling(monkeypatch):
+    # the convective face's ghost node taken as 0 instead of T_inner - ...
+    def nsum(T, axis):
+        n = T.shape[axis]
+        S = torch.zeros_like(T)
+        sl = lambda a, b: tuple(slice(a, b) if k == axis else slice(None) for k in range(3))  # noqa: E731
+        S[sl(1, n - 1)] = T[sl(2, n)] + T[sl(0, n - 2)]
+        S[sl(0, 1)] = T[sl(1, 2)]
+        S[sl(n - 1, n)] = T[sl(n - 2, n - 1)]
+        return S
+    monkeypatch.setattr(heat, "_neighbour_sum", nsum)
+
+
+def convection_heats(monkeypatch):
+    # -kappa dT/dn = -h (T - T_inf): the sign of Eq. (10) flipped
+    orig = heat._face_terms
+    monkeypatch.setattr(heat, "_face_terms", lambda *a: tuple(-x for x in orig(*a)))
+
+
+def convection_without_spacing(monkeypatch):
+    # the ghost node's offset without the spacing d (h / kappa instead of d h / kappa)
+    def terms(shape, dx, dy, dz, kappa, bc):
+        diag = torch.zeros(shape, dtype=torch.float64)
+        for k, (axis, d) in enumerate(((2, dx), (2, dx), (1, dy), (1, dy), (0, dz), (0, dz))):
+            if not bc.convective(k):
+                continue
+            layer = [slice(None)] * 3
+            layer[axis] = 0 if k % 2 == 0 else shape[axis] - 1
+            diag[tuple(layer)] += 2.0 * (1.0 / d ** 2) * bc.h_of(k) / kappa
+        return diag, diag * bc.t_inf
+    monkeypatch.setattr(heat, "_face_terms", terms)
+
+
+def face_cells_full_volume(monkeypatch):
+    # a face node's source density over a whole cell instead of its half cell
+    monkeypatch.setattr(ssfm.HeatDeposit, "qdot_nodes",
+                        lambda self: self.Q / (self.hdx * self.hdy * self.hdz))
 
 
 # ------------------------------------------------------------------ cases ----
@@ -463,6 +505,14 @@ CASES = {
                                [P.test_sor_matches_direct_sparse_solve,
                                 P.test_sor_recovers_discrete_eigenmode]),
     "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
+    "convective ghost not doubled": (ghost_without_doubling,
+                                     [P.test_all_convective_faces_balance_the_source_exactly]),
+    "convection heats": (convection_heats,
+                         [P.test_all_convective_faces_balance_the_source_exactly]),
+    "convective offset without spacing": (convection_without_spacing,
+                                          [P.test_all_convective_faces_balance_the_source_exactly]),
+    "face cells of full volume": (face_cells_full_volume,
+                                  [P.test_loop_with_convective_faces_conserves_energy]),
     "source not divided by kappa": (source_without_conductivity,
                                     [P.test_sor_matches_direct_sparse_solve,
                                      P.test_sor_recovers_discrete_eigenmode]),

@@ -454,6 +454,130 @@ def test_sor_recovers_discrete_eigenmode():
     assert np.max(np.abs(T.numpy() - 3.0 * mode)) < 1e-9
 
 
+def _slab_profile(coord, length, q, kappa, h, t_inf):
+    """Steady 1-D profile of kappa T'' + q = 0 with T(0) = 0 and the
+    convective end -kappa T'(length) = h (T(length) - t_inf): a quadratic,
+    T = -q s^2 / (2 kappa) + A s."""
+    A = (q * length + h * q * length ** 2 / (2 * kappa) + h * t_inf) / (kappa + h * length)
+    return -q * coord ** 2 / (2 * kappa) + A * coord
+
+
+@pytest.mark.parametrize("axis", ["z", "y"])
+def test_convective_face_slab_closed_form(axis):
+    """Eq. (10) on one face, Eq. (9) on the opposite one, insulated sides
+    (h = 0) and a uniform source: the solution is the quadratic slab profile,
+    and the ghost-node scheme is exact for quadratics, so the discrete
+    solution equals it at the nodes.  axis z: oven at the entrance face,
+    convection at the exit face; axis y: the bottom-oven configuration of
+    Sec. 4.2 reduced to one dimension."""
+    hx, hy, hz = 5, 6, 17
+    wx, wy, L, kappa, q0 = 2e-3, 1e-3, 0.03, 8.4, 3e5
+    if axis == "z":
+        faces, hs, length, h = ("C", "C", "C", "C", "D", "C"), (0, 0, 0, 0, 0, 350.0), L, 350.0
+    else:
+        faces, hs, length, h = ("C", "C", "D", "C", "C", "C"), (0, 0, 0, 800.0, 0, 0), wy, 800.0
+    bc = heat.HeatBC(faces, hs, -3.0)
+    q = torch.full((hz, hy, hx), q0, dtype=torch.float64)
+    T, sweeps, _ = heat.sor_solve(q, kappa, wx, wy, L, tol=1e-13, max_sweeps=200000, bc=bc)
+    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    if axis == "z":
+        ref = _slab_profile(np.arange(hz) * dz, L, q0, kappa, h, -3.0)[:, None, None]
+    else:
+        ref = _slab_profile(np.arange(hy) * dy, wy, q0, kappa, h, -3.0)[None, :, None]
+    ref = np.broadcast_to(ref, T.shape)
+    assert np.max(np.abs(T.numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+    assert np.max(np.abs(ref)) > 0.1
+
+
+def test_all_convective_faces_balance_the_source_exactly():
+    """With every face convective (no oven), summing the node equations over
+    the node cells (halved on each face) telescopes to the discrete energy
+    balance sum q_i V_i = sum over face nodes of h (T_i - T_inf) A_i, A_i the
+    face cell's area; it holds to the solver's tolerance for any source, and
+    covers the edges and corners where two or three faces meet."""
+    hx, hy, hz = 7, 6, 9
+    wx, wy, L, kappa, h, t_inf = 2e-3, 1e-3, 0.03, 8.4, 2e3, 0.7
+    bc = heat.HeatBC(("C",) * 6, h, t_inf)
+    rng = np.random.default_rng(8)
+    q = rng.uniform(0, 1e7, size=(hz, hy, hx))
+    T, _, _ = heat.sor_solve(torch.tensor(q), kappa, wx, wy, L, tol=1e-14, max_sweeps=500000,
+                             bc=bc)
+    T = T.numpy()
+    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    wgt = [np.ones(n) for n in (hz, hy, hx)]
+    for w_ in wgt:
+        w_[0] = w_[-1] = 0.5
+    V = dx * dy * dz * wgt[0][:, None, None] * wgt[1][None, :, None] * wgt[2][None, None, :]
+    gen = float((q * V).sum())
+    out = 0.0
+    for axis, (d, n) in enumerate(((dz, hz), (dy, hy), (dx, hx))):
+        others = [k for k in range(3) if k != axis]
+        area = dx * dy * dz / d
+        for end in (0, n - 1):
+            sl = [slice(None)] * 3
+            sl[axis] = end
+            wf = np.ones_like(T[tuple(sl)])
+            shape2 = [T.shape[k] for k in others]
+            wf = wgt[others[0]][:, None] * wgt[others[1]][None, :]
+            out += float((h * (T[tuple(sl)] - t_inf) * area * wf.reshape(shape2)).sum())
+    assert abs(out / gen - 1) < 1e-9, (out, gen)
+
+
+def test_convective_sor_matches_direct_sparse_solve():
+    """A mixed configuration (oven on y- and z-, convection elsewhere, with
+    different h per face) against scipy's sparse direct solve of the same
+    node equations."""
+    import scipy.sparse as sp
+    from scipy.sparse.linalg import spsolve
+    hx, hy, hz = 6, 5, 7
+    wx, wy, L, kappa = 2e-3, 1e-3, 0.03, 8.4
+    hs = (400.0, 900.0, 0.0, 1500.0, 0.0, 250.0)
+    bc = heat.HeatBC(("C", "C", "D", "C", "D", "C"), hs, 1.5)
+    dx, dy, dz = heat.spacings(hx, hy, hz, wx, wy, L)
+    rng = np.random.default_rng(9)
+    q = rng.uniform(0, 1e7, size=(hz, hy, hx))
+    T, _, _ = heat.sor_solve(torch.tensor(q), kappa, wx, wy, L, tol=1e-14, max_sweeps=500000,
+                             bc=bc)
+    unknown = heat.unknown_mask((hz, hy, hx), bc).numpy()
+    idx = -np.ones((hz, hy, hx), dtype=int)
+    idx[unknown] = np.arange(int(unknown.sum()))
+    rows, cols, vals, rhs = [], [], [], []
+    dims = (hz, hy, hx)
+    sp_of = (dz, dy, dx)
+    face = {(2, 0): 0, (2, 1): 1, (1, 0): 2, (1, 1): 3, (0, 0): 4, (0, 1): 5}
+    for node in zip(*np.nonzero(unknown)):
+        r = idx[node]
+        b = -q[node] / kappa
+        diag = 0.0
+        for axis in range(3):
+            a = 1.0 / sp_of[axis] ** 2
+            diag -= 2 * a
+            for step, side in ((-1, 0), (1, 1)):
+                nb = list(node)
+                nb[axis] += step
+                if 0 <= nb[axis] < dims[axis]:
+                    target = [tuple(nb)]
+                else:
+                    # ghost beyond a convective face: 2 x the inner neighbour,
+                    # and -2 d (h / kappa) (T - T_inf)
+                    hk = hs[face[(axis, side)]]
+                    inner = list(node)
+                    inner[axis] -= step
+                    target = [tuple(inner)]
+                    diag -= 2 * a * sp_of[axis] * hk / kappa
+                    b -= 2 * a * sp_of[axis] * hk / kappa * 1.5
+                for t in target:
+                    if idx[t] >= 0:
+                        rows.append(r); cols.append(idx[t]); vals.append(a)
+        rows.append(r); cols.append(r); vals.append(diag)
+        rhs.append(b)
+    A = sp.csr_matrix((vals, (rows, cols)), shape=(len(rhs), len(rhs)))
+    sol = spsolve(A.tocsc(), np.array(rhs))
+    ref = np.zeros((hz, hy, hx))
+    ref[unknown] = sol
+    assert np.max(np.abs(T.numpy() - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
 def test_heat_deposits_balance_absorbed_power():
     """P_in - P_out = sum of deposited q_dot dV, to the trapezoid rule's O(dz^2)."""
     errs = []
@@ -538,6 +662,34 @@ def test_thermal_loop_fixed_point_behaviour():
     for it in h[1:]:
         ref = ssfm.run(w.with_(dT=it["dT"].numpy(), t_lx=w.wx, t_ly=w.wy))[2]
         assert abs(it["eta"] / float(ref) - 1) < 1e-13
+
+
+def test_loop_with_convective_faces_conserves_energy():
+    """Every face convective (no oven): in steady state all the heat the beams
+    deposit (Eq. 8) leaves through the faces by convection (Eq. 10).  The
+    second iteration's dT, solved from the first pass's deposits, carries
+    exactly that heat out; this holds only if a face node's source density
+    uses its half-size cell (the entrance and exit facets receive deposits)."""
+    w = W.thermal_loop(n=16, nz=40, heat=(9, 9, 11), n_outer=2, p1=100.0)
+    w = w.with_(heat_faces=("C",) * 6, h_conv=4e3, t_inf=0.0)
+    hist = heat.thermal_loop(w, 2, tol=1e-13, max_sweeps=500000)
+    deposited = float(hist[0]["Q"].sum())
+    assert deposited > 0.01 * w.p1
+    T = hist[1]["dT"].numpy()
+    hx, hy, hz = w.hx, w.hy, w.hz
+    dx, dy, dz = heat.spacings(hx, hy, hz, w.wx, w.wy, w.L)
+    wgt = [np.ones(n) for n in (hz, hy, hx)]
+    for w_ in wgt:
+        w_[0] = w_[-1] = 0.5
+    out = 0.0
+    for axis, d in enumerate((dz, dy, dx)):
+        others = [k for k in range(3) if k != axis]
+        for end in (0, T.shape[axis] - 1):
+            sl = [slice(None)] * 3
+            sl[axis] = end
+            wf = wgt[others[0]][:, None] * wgt[others[1]][None, :]
+            out += float((w.h_conv * T[tuple(sl)] * (dx * dy * dz / d) * wf).sum())
+    assert abs(out / deposited - 1) < 1e-8, (out, deposited)
 
 
 # ------------------------------------------------------------- gradients ----

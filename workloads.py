@@ -113,6 +113,12 @@ class Workload:
     hy: int = 0
     hz: int = 0
     n_outer: int = 0
+    # heat boundary of each face x-, x+, y-, y+, z-, z+: "D" held at the oven
+    # temperature (Eq. 9) or "C" convective (Eq. 10) with coefficient h_conv
+    # (W/(m^2 K); one value or six) toward the ambient T_oven + t_inf (K)
+    heat_faces: tuple = ("D",) * 6
+    h_conv: object = 0.0
+    t_inf: float = 0.0
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -222,6 +228,22 @@ def thermal_loop(n: int = 1024, nz: int = 8000, xi: float = 2.84, p1: float = 10
     return _lossy(Workload(name=f"thermal_{n}x{n}_nz{nz}", nx=n, ny=n, nz=nz, lx=lw,
                            ly=lw, p1=p1, w0=w0, z_focus=L_CRYSTAL / 2, hx=hx, hy=hy,
                            hz=hz, n_outer=n_outer, t_lx=CRYSTAL_WX, t_ly=CRYSTAL_WY))
+
+
+# Oven arrangements of Sec. 4.2 (Tfield::setOvenSurrounded / setBottomOvens):
+# the faces held at the oven temperature, the rest cooled by convection.
+OVENS = {
+    "all": ("D",) * 6,
+    "surrounded": ("D", "D", "D", "D", "C", "C"),   # side faces in the oven, end facets in air
+    "bottom": ("C", "C", "D", "C", "C", "C"),       # one oven under the y- face
+}
+
+
+def with_oven(w: Workload, oven: str, h_conv=10.0, t_inf: float = 0.0) -> Workload:
+    """The workload with one of the paper's oven arrangements (h_conv and the
+    ambient temperature are not given in the paper: free convection in air is
+    of order 10 W/(m^2 K))."""
+    return w.with_(heat_faces=OVENS[oven], h_conv=h_conv, t_inf=t_inf)
 
 
 # The five workloads at full size, in the order they are quoted.
