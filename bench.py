@@ -525,24 +525,30 @@ def time_configs(pkg, stream, mp, hbm_gbs):
     tp = golden("thermal_pass_1024_nz8000.npz")
     if tp is not None:
         e["first_pass_eta_rel_err_vs_oracle"] = _rel(res["etas"][0], float(tp["eta"]))
-    # heat solves alone: a cold start (dT = 0 with the first pass's deposits)
-    # and a warm start (from that solution after the second pass)
-    plan2 = pkg.Plan(w, thermal=True)
-    plan2.propagate(stream)
-    plan2.efficiency()
-    sw = {}
-    cold = _event_ms(lambda: sw.__setitem__("cold", pkg.shg_heat_solve(plan2.handle, 200000,
-                                                                       1e-6, stream)), 1, stream)
-    plan2.propagate(stream)
-    plan2.efficiency()
-    warm = _event_ms(lambda: sw.__setitem__("warm", pkg.shg_heat_solve(plan2.handle, 200000,
-                                                                       1e-6, stream)), 1, stream)
-    e["heat_solve"] = {"cold_ms": cold[0], "cold_sweeps": sw["cold"][1],
-                       "warm_ms": warm[0], "warm_sweeps": sw["warm"][1],
-                       "grid": f"{w.hx}x{w.hy}x{w.hz}"}
+    # heat solves alone, each method on the same deposits: a cold start
+    # (dT = 0 with the first pass's deposits) and a warm start (from that
+    # solution after the second pass)
+    hs = {"grid": f"{w.hx}x{w.hy}x{w.hz}", "tol_K": 1e-6}
+    for name, method in (("direct", pkg.SHG_HEAT_DIRECT), ("sor", pkg.SHG_HEAT_SOR)):
+        plan2 = pkg.Plan(w, thermal=True)
+        pkg.shg_set_heat_method(plan2.handle, method)
+        plan2.propagate(stream)
+        plan2.efficiency()
+        sw = {}
+        cold = _event_ms(lambda: sw.__setitem__("cold", pkg.shg_heat_solve(
+            plan2.handle, 200000, 1e-6, stream)), 1, stream)
+        plan2.propagate(stream)
+        plan2.efficiency()
+        warm = _event_ms(lambda: sw.__setitem__("warm", pkg.shg_heat_solve(
+            plan2.handle, 200000, 1e-6, stream)), 1, stream)
+        hs[name] = {"cold_ms": cold[0], "cold_iterations": sw["cold"][1],
+                    "warm_ms": warm[0], "warm_iterations": sw["warm"][1]}
+        del plan2
+    hs["cold_speedup_direct_over_sor"] = hs["sor"]["cold_ms"] / hs["direct"]["cold_ms"]
+    e["heat_solve"] = hs
     e["passes"] = _pass_roof(pkg, plan, w, stream, fp32, fp64, l2, hbm_gbs, True)
     out["thermal"] = e
-    del plan, plan2
+    del plan
     return out
 
 

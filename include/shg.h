@@ -228,16 +228,47 @@ shg_status_t shg_propagate_adjoint(shg_plan_t *plan, double d_eta, double *g_w0,
 shg_status_t shg_batch_submit(shg_plan_t *const *plans, int n, double *eta_host_out,
                               shg_stream_t stream);
 
-/* Solve kappa lap dT = -q_dot (Eq. 7/16, Dirichlet dT = 0 on all faces) on
- * the heat grid by red-black SOR (double precision, warm-started from the
- * previous solution) from the q_dot deposited by the last THERMAL
- * propagation, until the largest Jacobi correction is below tol (K) or
- * max_sweeps sweeps.  The correction is checked every 8 sweeps, so up to 7
- * sweeps may follow the first converged one.  Installs dT as the plan's
- * temperature map.  Returns the final correction and sweep count.
- * Synchronises `stream`. */
+/* Solve kappa lap dT = -q_dot (Eq. 7/16 with the faces of
+ * shg_set_heat_boundary) on the heat grid, warm-started from the previous
+ * solution, from the q_dot deposited by the last THERMAL propagation, until
+ * the largest Jacobi correction is below tol (K) or max_sweeps sweeps
+ * (SOR) or refinement passes (direct; see shg_set_heat_method).  The SOR
+ * checks the correction every 8 sweeps, so up to 7 sweeps may follow the
+ * first converged one.  Installs dT as the plan's temperature map.  Returns
+ * the final correction and the sweep or pass count.  Synchronises `stream`. */
 shg_status_t shg_heat_solve(shg_plan_t *plan, int max_sweeps, double tol, double *resid,
                             int *sweeps, shg_stream_t stream);
+
+/* Boundary of each face of the heat grid, in the order x-, x+, y-, y+, z-, z+
+ * (kinds[6]): SHG_FACE_OVEN holds the face at T_oven (dT = 0, Eq. 9);
+ * SHG_FACE_CONVECTIVE cools it by free convection, -kappa dT/dn = h (T - T_inf)
+ * (Eq. 10), with h[k] >= 0 (W/(m^2 K); h may be NULL for 0) and the ambient
+ * temperature T_inf = T_oven + t_inf.  A convective face node is an unknown
+ * whose stencil uses a ghost node beyond the face eliminated by the central
+ * difference of Eq. (10); its source density uses its half-size cell.  A node
+ * on an oven face is held even where it also lies on a convective face.
+ * The paper's arrangements: all faces in the oven, the four side faces in
+ * the oven with the end facets in air (setOvenSurrounded), or one oven under
+ * the y- face (setBottomOvens).  Default: all oven-held.  Resets the solved
+ * dT to 0.  SHG_ERR_INVALID_ARG for another kind, a negative or non-finite h,
+ * every face convective with h = 0 (no steady state), or convective faces
+ * with the SOR method; SHG_ERR_STATE without SHG_FLAG_THERMAL. */
+enum { SHG_FACE_OVEN = 0, SHG_FACE_CONVECTIVE = 1 };
+shg_status_t shg_set_heat_boundary(shg_plan_t *plan, const int *kinds, const double *h,
+                                   double t_inf);
+
+/* Method of shg_heat_solve and shg_thermal_loop:
+ *   SHG_HEAT_DIRECT (default): the operator of Eq. (16) is a Kronecker sum of
+ *     three 1-D operators, so it is solved directly: FP32 transforms to the
+ *     eigenbases of the x and y operators (computed once per boundary by
+ *     Jacobi rotations on the host), one tridiagonal solve along z per
+ *     transverse mode, transforms back, repeated as FP64 iterative refinement
+ *     of dT until the largest Jacobi correction is below tol (max_sweeps
+ *     bounds the refinement passes, at most 50; the solves report passes).
+ *   SHG_HEAT_SOR: red-black SOR in FP64 (every face oven-held only).
+ * Both converge to the same discrete solution. */
+enum { SHG_HEAT_DIRECT = 0, SHG_HEAT_SOR = 1 };
+shg_status_t shg_set_heat_method(shg_plan_t *plan, int method);
 
 /* The self-consistent loop of Fig. 2 with n_outer fixed iterations:
  * q_dot = 0 -> dT -> (Dk, lens) -> propagate (depositing q_dot) -> ...

@@ -43,6 +43,15 @@ Readings of the paper (where it is silent, garbled or inconsistent):
    is removed; beta_F and psi_F stay.
 9. Heat source samples (Eq. 8) are taken at z_s = s dz, s = 0..nz, with
    trapezoid weights in z, and box-summed into the nearest heat node.
+10. Dk(T) of Eq. (4) (optional, ``Params.qpm``): with the oven at T_oven the
+   local temperature is T = T_oven + T_off + dT, and
+   Dk(T) = (4 pi / lambda_F)(n_SH(T) - n_F(T)) - 2 pi / Lambda(T),
+   Lambda(T) = Lambda(25 C)(1 + a (T - 25) + b (T - 25)^2), n_j(T) a
+   polynomial in (T - 25 C) (the paper gives no index data).  With
+   T_ref = T_oven + T_off: phi = Dk(T_ref) z + C'(x,y,z), C' the trapezoid
+   cumulative integral of Dk(T_ref + dT) - Dk(T_ref) on the map nodes,
+   interpolated like C.  dk0 and dDk/dT are not used then; the lens phase
+   (reading 6) keeps dn/dT.
 """
 from __future__ import annotations
 
@@ -68,6 +77,24 @@ def _t(v) -> torch.Tensor:
 
 
 @dataclass
+class QPM:
+    """Temperature model of the phase mismatch, Eq. (4) with Lambda(T)."""
+    t_oven: float               # oven temperature (deg C)
+    lambda25: float             # grating period Lambda(25 C) (m)
+    a_lambda: float = 2.2e-6    # thermal expansion of the period (1/K), the paper's MgO:sPPLT
+    b_lambda: float = -5.9e-9   # (1/K^2)
+    n_f_t: tuple = (0.0,)       # n_F(T) = sum_k n_f_t[k] (T - 25)^k
+    n_sh_t: tuple = (0.0,)
+
+    def dk(self, lambda_f: float, T):
+        u = T - 25.0
+        nF = sum(c * u ** k for k, c in enumerate(self.n_f_t))
+        nS = sum(c * u ** k for k, c in enumerate(self.n_sh_t))
+        lam = self.lambda25 * (1.0 + self.a_lambda * u + self.b_lambda * u * u)
+        return 4.0 * math.pi / lambda_f * (nS - nF) - 2.0 * math.pi / lam
+
+
+@dataclass
 class Params:
     """Physical inputs of one instance (crystal, beams, grid)."""
     nx: int
@@ -90,6 +117,7 @@ class Params:
     undepleted: bool = False
     walkoff_f: float = 0.0      # spatial walk-off angles rho_j (rad) toward +x
     walkoff_sh: float = 0.0
+    qpm: Optional[QPM] = None   # Eq. (4) phase mismatch instead of dk0 + dDk/dT dT
 
     @property
     def lambda_sh(self) -> float:
@@ -132,7 +160,14 @@ def params_from_workload(w) -> Params:
                   alpha_f=w.alpha_f, alpha_sh=w.alpha_sh, beta_f=w.beta_f,
                   beta_sh=w.beta_sh, dk0=w.dk0, ddk_dT=w.ddk_dT, dn_dT=w.dn_dT,
                   undepleted=bool(w.undepleted), walkoff_f=getattr(w, "walkoff_f", 0.0),
-                  walkoff_sh=getattr(w, "walkoff_sh", 0.0))
+                  walkoff_sh=getattr(w, "walkoff_sh", 0.0), qpm=_qpm_of(w))
+
+
+def _qpm_of(w) -> Optional["QPM"]:
+    q = getattr(w, "qpm", None)
+    if q is None:
+        return None
+    return QPM(q.t_oven, q.lambda25, q.a_lambda, q.b_lambda, tuple(q.n_f_t), tuple(q.n_sh_t))
 
 
 # ---------------------------------------------------------------- grid ----
@@ -211,7 +246,13 @@ class TemperatureField:
         self.L = p.L
         tz, ty, tx = self.dT.shape
         self.tz = tz
-        self.C = cumulative_dT(self.dT, p.L)
+        if p.qpm is None:
+            self.C = cumulative_dT(self.dT, p.L)
+        else:
+            # reading 10: the integrand is Dk(T_ref + dT) - Dk(T_ref) at every node
+            t_ref = p.qpm.t_oven + self.t_off
+            self.C = cumulative_dT(p.qpm.dk(p.lambda_f, t_ref + self.dT)
+                                   - p.qpm.dk(p.lambda_f, t_ref), p.L)
         t_lx = t_lx or p.lx
         t_ly = t_ly or p.ly
         x = axis(p.nx, p.lx)
@@ -260,8 +301,11 @@ class Nonlinear:
         p = self.p
         d, c = self.temp.at(z)
         t_off = self.temp.t_off
-        g = p.ddk_dT
-        phi = (p.dk0 + g * t_off) * z + g * c
+        if p.qpm is None:
+            g = p.ddk_dT
+            phi = (p.dk0 + g * t_off) * z + g * c
+        else:
+            phi = p.qpm.dk(p.lambda_f, p.qpm.t_oven + t_off) * z + c
         dT_eff = d + t_off
         psiF = self.k0F * p.dn_dT * dT_eff
         psiS = self.k0S * p.dn_dT * dT_eff

@@ -31,6 +31,11 @@ SHG_FLAG_THERMAL = 2
 SHG_FLAG_ADJOINT = 4
 SHG_FLAG_NODE_SAMPLER = 8
 
+SHG_FACE_OVEN = 0
+SHG_FACE_CONVECTIVE = 1
+SHG_HEAT_DIRECT = 0
+SHG_HEAT_SOR = 1
+
 
 class shg_grid_t(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
@@ -86,6 +91,8 @@ _SIGS = {
     "shg_field_powers_noalloc": [_P, _I, _I, _I, _I, _D, _D, _D, _D, _P, _P],
     "shg_measure_peaks": [_DP, _DP, _DP, _DP, _P],
     "shg_set_monitor": [_P, _I],
+    "shg_set_heat_boundary": [_P, _IP, _DP, _D],
+    "shg_set_heat_method": [_P, _I],
     "shg_get_monitor": [_P, _DP, _DP, _DP, _I, _IP],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
@@ -318,6 +325,24 @@ def shg_field_powers_noalloc(fields, nx: int, ny: int, n_inst: int, lx: float, l
                                            _stream(stream)), "shg_field_powers_noalloc")
 
 
+def shg_set_heat_boundary(plan: int, kinds, h=None, t_inf: float = 0.0) -> None:
+    """kinds: six of SHG_FACE_OVEN / SHG_FACE_CONVECTIVE ("D" / "C" accepted) for
+    the faces x-, x+, y-, y+, z-, z+; h: one coefficient or six (W/(m^2 K))."""
+    if len(kinds) != 6:
+        raise ValueError("six faces: x-, x+, y-, y+, z-, z+")
+    code = {"D": SHG_FACE_OVEN, "C": SHG_FACE_CONVECTIVE}
+    k = (_I * 6)(*[code.get(v, v) if isinstance(v, str) else int(v) for v in kinds])
+    hv = [float(h or 0.0)] * 6 if not isinstance(h, (list, tuple)) else [float(v) for v in h]
+    if len(hv) != 6:
+        raise ValueError("one heat transfer coefficient or six")
+    _check(_lib().shg_set_heat_boundary(plan, k, (_D * 6)(*hv), float(t_inf)),
+           "shg_set_heat_boundary")
+
+
+def shg_set_heat_method(plan: int, method: int) -> None:
+    _check(_lib().shg_set_heat_method(plan, int(method)), "shg_set_heat_method")
+
+
 def shg_set_monitor(plan: int, every: int) -> None:
     _check(_lib().shg_set_monitor(plan, int(every)), "shg_set_monitor")
 
@@ -378,6 +403,10 @@ class Plan:
         self.fp64 = bool(flags & SHG_FLAG_FP64)
         self.handle = shg_plan_create(*structs_from(w), flags)
         self._dT = None
+        faces = tuple(getattr(w, "heat_faces", ("D",) * 6))
+        if (flags & SHG_FLAG_THERMAL) and any(f != "D" for f in faces):
+            shg_set_heat_boundary(self.handle, faces, getattr(w, "h_conv", 0.0),
+                                  getattr(w, "t_inf", 0.0))
 
     def __del__(self):
         h = getattr(self, "handle", None)

@@ -734,6 +734,7 @@ static void plan_free(shg_plan* p) {
     if (!p) return;
     shg::forget_plan_batches(p);
     shg::free_adjoint(p);
+    shg::free_heat_direct(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->done) cudaEventDestroy(p->done);

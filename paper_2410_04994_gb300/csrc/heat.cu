@@ -1,15 +1,18 @@
-// Steady heat solve (Eq. 7 discretised as Eq. 16, Dirichlet T = T_oven on all
-// faces, Eq. 9) by red-black successive over-relaxation, and the
-// self-consistent loop of Fig. 2.
+// Steady heat solve (Eq. 7 discretised as Eq. 16) and the self-consistent
+// loop of Fig. 2.  Two methods: the direct separable solve of heat_direct.cu
+// (default; any mix of oven-held (Eq. 9) and convective (Eq. 10) faces) and
+// red-black successive over-relaxation (below; every face held at T_oven).
 //
 // The iteration runs in double precision: in FP32 the Jacobi correction of a
 // solution of a few kelvin bottoms out near 1e-6 K (rounding of the stencil
 // sums), which would make a 1e-6 K stopping test unreachable.
 //
 // Unknown: dT = T - T_oven on the node grid [hz][hy][hx] spanning the crystal
-// [-wx/2, wx/2] x [-wy/2, wy/2] x [0, L], zero on the faces.  Source: the heat
-// deposited by the last THERMAL propagation, q_dot = Q / (dx dy dz) at each
-// node (Q = sum of q_dot dV of the field samples binned to the node).
+// [-wx/2, wx/2] x [-wy/2, wy/2] x [0, L], zero on oven-held faces.  Source: the
+// heat deposited by the last THERMAL propagation, q_dot = Q / V at each node
+// (Q = sum of q_dot dV of the field samples binned to the node, V = dx dy dz,
+// halved for each face the node lies on; for the SOR, whose faces are all
+// oven-held, only interior nodes matter).
 // SOR factor omega = 2 / (1 + sqrt(1 - rho_J^2)) with rho_J the Jacobi
 // spectral radius of the anisotropic stencil.  Convergence: the largest Jacobi
 // correction over the interior, checked after every kCheckEvery full (red +
@@ -152,9 +155,64 @@ static shg_status_t install_map(shg_plan* p, cudaStream_t st) {
                                reinterpret_cast<shg_stream_t>(st));
 }
 
+// The plan's heat solve with its method; max_sweeps bounds the SOR sweeps or
+// the refinement passes of the direct solve (at most 50 of those).
+static shg_status_t solve(shg_plan* p, int max_sweeps, double tol, double* resid, int* sweeps,
+                          cudaStream_t st) {
+    if (p->heat_method == SHG_HEAT_SOR)
+        return sor(p, max_sweeps, tol, resid, sweeps, st);
+    return heat_direct_solve(p, std::min(max_sweeps, 50), tol, resid, sweeps, st);
+}
+
+static bool all_oven(const shg_plan* p) {
+    for (int k = 0; k < 6; ++k)
+        if (p->heat_face[k]) return false;
+    return true;
+}
+
 }  // namespace shg
 
 using namespace shg;
+
+extern "C" shg_status_t shg_set_heat_boundary(shg_plan_t* p, const int* kinds, const double* h,
+                                              double t_inf) {
+    if (!p || !kinds || !std::isfinite(t_inf)) return SHG_ERR_INVALID_ARG;
+    if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
+    bool any_sink = false;
+    for (int k = 0; k < 6; ++k) {
+        if (kinds[k] != SHG_FACE_OVEN && kinds[k] != SHG_FACE_CONVECTIVE) return SHG_ERR_INVALID_ARG;
+        const double hk = (kinds[k] == SHG_FACE_CONVECTIVE) ? (h ? h[k] : 0.0) : 0.0;
+        if (!std::isfinite(hk) || hk < 0) return SHG_ERR_INVALID_ARG;
+        any_sink |= kinds[k] == SHG_FACE_OVEN || hk > 0;
+    }
+    // every face insulated: no steady state exists
+    if (!any_sink) return SHG_ERR_INVALID_ARG;
+    if (p->heat_method == SHG_HEAT_SOR) {
+        for (int k = 0; k < 6; ++k)
+            if (kinds[k] != SHG_FACE_OVEN) return SHG_ERR_INVALID_ARG;
+    }
+    if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    for (int k = 0; k < 6; ++k) {
+        p->heat_face[k] = kinds[k];
+        p->heat_h[k] = kinds[k] == SHG_FACE_CONVECTIVE ? (h ? h[k] : 0.0) : 0.0;
+    }
+    p->heat_tinf = t_inf;
+    free_heat_direct(p);  // rebuilt for the new boundary at the next direct solve
+    // the previous solution belongs to the old boundary (nodes now held at the
+    // oven may be non-zero): the next solve starts from dT = 0
+    const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;
+    SHG_CK(cudaMemset(p->theat, 0, nh * sizeof(double)));
+    SHG_CK(cudaMemset(p->theat_prev, 0, nh * sizeof(double)));
+    return SHG_OK;
+}
+
+extern "C" shg_status_t shg_set_heat_method(shg_plan_t* p, int method) {
+    if (!p || (method != SHG_HEAT_DIRECT && method != SHG_HEAT_SOR)) return SHG_ERR_INVALID_ARG;
+    if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
+    if (method == SHG_HEAT_SOR && !all_oven(p)) return SHG_ERR_INVALID_ARG;
+    p->heat_method = method;
+    return SHG_OK;
+}
 
 extern "C" shg_status_t shg_heat_solve(shg_plan_t* p, int max_sweeps, double tol, double* resid,
                                        int* sweeps, shg_stream_t stream) {
@@ -162,7 +220,7 @@ extern "C" shg_status_t shg_heat_solve(shg_plan_t* p, int max_sweeps, double tol
     if (!(p->flags & SHG_FLAG_THERMAL) || !p->Q) return SHG_ERR_STATE;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     if (p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
-    shg_status_t r = sor(p, max_sweeps, tol, resid, sweeps, st);
+    shg_status_t r = solve(p, max_sweeps, tol, resid, sweeps, st);
     if (r != SHG_OK) return r;
     return install_map(p, st);
 }
@@ -196,7 +254,7 @@ extern "C" shg_status_t shg_thermal_loop(shg_plan_t* p, int n_outer, int max_swe
     for (int it = 0; it < n_outer; ++it) {
         SHG_CK(cudaMemcpyAsync(p->theat_prev, p->theat, nh * sizeof(double),
                                cudaMemcpyDeviceToDevice, st));
-        shg_status_t r = sor(p, max_sweeps, tol, nullptr, nullptr, st);
+        shg_status_t r = solve(p, max_sweeps, tol, nullptr, nullptr, st);
         if (r != SHG_OK) return r;
         auto* d = reinterpret_cast<unsigned long long*>(p->hred);
         SHG_CK(cudaMemsetAsync(d, 0, sizeof(*d), st));

@@ -29,8 +29,9 @@ struct InitDesc {
     const void* f0;         // custom initial fields [2][ny][nx] or nullptr
 };
 
-struct Adjoint;  // adjoint.cu
-struct Heat;     // heat.cu
+struct Adjoint;     // adjoint.cu
+struct Heat;        // heat.cu
+struct HeatDirect;  // heat_direct.cu
 
 }  // namespace shg
 
@@ -82,6 +83,11 @@ struct shg_plan {
     double* theat_prev = nullptr;
     float* theat_f = nullptr; // dT rounded to float, as installed as the map
     double* hred = nullptr;   // reduction scratch of the heat solve
+    int heat_face[6] = {0, 0, 0, 0, 0, 0};  // x-, x+, y-, y+, z-, z+: 0 oven (Eq. 9), 1 convective (Eq. 10)
+    double heat_h[6] = {0, 0, 0, 0, 0, 0};  // heat transfer coefficient of each convective face
+    double heat_tinf = 0;                    // T_inf - T_oven (K)
+    int heat_method = 0;                     // SHG_HEAT_DIRECT or SHG_HEAT_SOR
+    shg::HeatDirect* hdir = nullptr;         // eigenbases and work buffers of the direct solve
 
     // tensor map of `field` for the TMA column pass (FP32, supported lengths)
     CUtensorMap cmap;
@@ -187,6 +193,10 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);
 void free_adjoint(shg_plan* p);
+void free_heat_direct(shg_plan* p);
+shg_status_t heat_direct_setup(shg_plan* p);
+shg_status_t heat_direct_solve(shg_plan* p, int max_iters, double tol, double* resid, int* iters,
+                               cudaStream_t st);
 shg_status_t adjoint_alloc(shg_plan* p);
 // Enqueue the checkpoint copy of the state entering row pass R(s) (adjoint plans).
 shg_status_t adjoint_checkpoint(shg_plan* p, int s, cudaStream_t st);

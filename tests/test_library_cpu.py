@@ -204,3 +204,10 @@ def test_monitor_calls_refuse_bad_arguments(pkg):
     assert lib.shg_set_monitor(None, 1) == 1
     assert lib.shg_get_monitor(None, None, None, None, 0, None) == 1
     assert lib.shg_measure_peaks(None, None, None, None, None) == 1
+
+
+def test_heat_calls_refuse_null_plans(pkg):
+    lib = pkg.load()
+    kinds = (ctypes.c_int * 6)(0, 0, 0, 0, 0, 0)
+    assert lib.shg_set_heat_boundary(None, kinds, None, 0.0) == 1
+    assert lib.shg_set_heat_method(None, 0) == 1

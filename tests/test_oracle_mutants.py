@@ -395,6 +395,62 @@ def face_cells_full_volume(monkeypatch):
                         lambda self: self.Q / (self.hdx * self.hdy * self.hdz))
 
 
+def _qpm_dk(mutate):
+    def dk(self, lambda_f, T):
+        u = T - 25.0
+        nF = sum(c * u ** k for k, c in enumerate(self.n_f_t))
+        nS = sum(c * u ** k for k, c in enumerate(self.n_sh_t))
+        return mutate(self, lambda_f, T, u, nF, nS)
+    return dk
+
+
+def grating_b_sign(self, lambda_f, T, u, nF, nS):
+    # Lambda(T) with the quadratic term's sign flipped
+    lam = self.lambda25 * (1.0 + self.a_lambda * u - self.b_lambda * u * u)
+    return 4.0 * math.pi / lambda_f * (nS - nF) - 2.0 * math.pi / lam
+
+
+def grating_about_the_oven(self, lambda_f, T, u, nF, nS):
+    # the grating expanded about the oven temperature instead of 25 C
+    v = T - self.t_oven
+    lam = self.lambda25 * (1.0 + self.a_lambda * v + self.b_lambda * v * v)
+    return 4.0 * math.pi / lambda_f * (nS - nF) - 2.0 * math.pi / lam
+
+
+def material_term_2pi(self, lambda_f, T, u, nF, nS):
+    # 2 pi / lambda_F instead of 4 pi / lambda_F on the index difference
+    lam = self.lambda25 * (1.0 + self.a_lambda * u + self.b_lambda * u * u)
+    return 2.0 * math.pi / lambda_f * (nS - nF) - 2.0 * math.pi / lam
+
+
+def eq4_without_offset(monkeypatch):
+    # the local temperature of Eq. (4) taken without the oven offset
+    orig = ssfm.Nonlinear.coefficients
+
+    def coefficients(self, z):
+        p = self.p
+        if p.qpm is None:
+            return orig(self, z)
+        d, c = self.temp.at(z)
+        t_off = self.temp.t_off
+        phi = p.qpm.dk(p.lambda_f, p.qpm.t_oven) * z + c
+        dT_eff = d + t_off
+        return phi, self.k0F * p.dn_dT * dT_eff, self.k0S * p.dn_dT * dT_eff
+    monkeypatch.setattr(ssfm.Nonlinear, "coefficients", coefficients)
+
+
+def eq4_integrand_not_relative(monkeypatch):
+    # C' integrates Dk(T_ref + dT) instead of Dk(T_ref + dT) - Dk(T_ref)
+    orig = ssfm.TemperatureField.__init__
+
+    def init(self, p, dT, t_lx, t_ly, t_off=0.0):
+        orig(self, p, dT, t_lx, t_ly, t_off)
+        if p.qpm is not None:
+            t_ref = p.qpm.t_oven + self.t_off
+            self.C = ssfm.cumulative_dT(p.qpm.dk(p.lambda_f, t_ref + self.dT), p.L)
+    monkeypatch.setattr(ssfm.TemperatureField, "__init__", init)
+
+
 # ------------------------------------------------------------------ cases ----
 
 def _attr(obj, name, value):
@@ -505,6 +561,16 @@ CASES = {
                                [P.test_sor_matches_direct_sparse_solve,
                                 P.test_sor_recovers_discrete_eigenmode]),
     "heat source sign": (heat_source_sign, [P.test_thermal_loop_fixed_point_behaviour]),
+    "grating b sign": (_attr(ssfm.QPM, "dk", _qpm_dk(grating_b_sign)),
+                       [P.test_eq4_zero_crossing_at_the_constructed_phase_matching_temperature]),
+    "grating about the oven": (_attr(ssfm.QPM, "dk", _qpm_dk(grating_about_the_oven)),
+                               [P.test_eq4_zero_crossing_at_the_constructed_phase_matching_temperature]),
+    "material term 2 pi": (_attr(ssfm.QPM, "dk", _qpm_dk(material_term_2pi)),
+                           [P.test_eq4_with_linear_indices_and_rigid_grating_is_the_linearised_model]),
+    "Eq. 4 without the offset": (eq4_without_offset,
+                                 [P.test_eq4_with_linear_indices_and_rigid_grating_is_the_linearised_model]),
+    "Eq. 4 integrand absolute": (eq4_integrand_not_relative,
+                                 [P.test_eq4_with_linear_indices_and_rigid_grating_is_the_linearised_model]),
     "convective ghost not doubled": (ghost_without_doubling,
                                      [P.test_all_convective_faces_balance_the_source_exactly]),
     "convection heats": (convection_heats,

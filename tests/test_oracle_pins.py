@@ -692,6 +692,59 @@ def test_loop_with_convective_faces_conserves_energy():
     assert abs(out / deposited - 1) < 1e-8, (out, deposited)
 
 
+# ------------------------------------------------- Eq. (4) phase mismatch ----
+
+def _eq4_case():
+    w = W.depleted_absorbing(n=32, nz=60, tgrid=(8, 8, 12), p1=300.0)
+    return w.with_(ddk_dT=0.0, dk0=0.0, t_off=1.5)
+
+
+def test_eq4_with_linear_indices_and_rigid_grating_is_the_linearised_model():
+    """With n_j(T) linear in T and a rigid grating (a = b = 0), Eq. (4) is
+    exactly Dk(T_oven) + g (T - T_oven), g = (4 pi / lambda_F) (n_SH' - n_F').
+    With the period chosen for phase matching at T_oven (Dk(T_oven) = 0), the
+    Eq. (4) run must reproduce the linearised run (dk0 = 0, dDk/dT = g) with
+    the same map and oven offset, to rounding."""
+    w = _eq4_case()
+    lam = w.lambda_f
+    nF0, sF, nS0, sS, t_oven = 2.14, 3e-5, 2.18, 9e-5, 48.0
+    dn = (nS0 - nF0) + (sS - sF) * (t_oven - 25.0)
+    period = lam / (2.0 * dn)              # 2 pi / period = (4 pi / lambda) dn
+    g = 4.0 * math.pi / lam * (sS - sF)
+    q = W.Qpm(t_oven=t_oven, lambda25=period, a_lambda=0.0, b_lambda=0.0,
+              n_f_t=(nF0, sF), n_sh_t=(nS0, sS))
+    AF, AS, eta = ssfm.run(w.with_(qpm=q))
+    AF2, AS2, eta2 = ssfm.run(w.with_(ddk_dT=g))
+    # rounding: Dk(T_ref + dT) - Dk(T_ref) cancels two terms of ~5e5 / m
+    assert abs(float(eta) / float(eta2) - 1) < 1e-10
+    assert float((AS - AS2).norm() / AS2.norm()) < 1e-9
+    # and the slope matters at this size: without it the result differs
+    assert abs(float(ssfm.run(w)[2]) / float(eta2) - 1) > 1e-3
+
+
+def test_eq4_zero_crossing_at_the_constructed_phase_matching_temperature():
+    """The paper's grating expansion (a_Lambda, b_Lambda of MgO:sPPLT) and
+    temperature-dependent indices; the period at 25 C is chosen so that the
+    quasi-phase-matching condition 2 pi / Lambda(T_pm) = (4 pi / lambda_F)
+    (n_SH - n_F)(T_pm) holds at T_pm = 60 C.  At T_oven + T_off = T_pm the
+    uniform-temperature run equals the phase-matched run (Dk = 0) to rounding;
+    3 K away it does not."""
+    w = _eq4_case().with_(dT=None, dn_dT=0.0)
+    lam = w.lambda_f
+    a, b, t_pm = 2.2e-6, -5.9e-9, 60.0
+    nF, nS = (2.14, 2e-5, 3e-8), (2.18, 7e-5, -4e-8)
+    u = t_pm - 25.0
+    dn = sum(c * u ** k for k, c in enumerate(nS)) - sum(c * u ** k for k, c in enumerate(nF))
+    lam25 = lam / (2.0 * dn) / (1.0 + a * u + b * u * u)
+    q = W.Qpm(t_oven=55.0, lambda25=lam25, a_lambda=a, b_lambda=b, n_f_t=nF, n_sh_t=nS)
+    AF, AS, eta = ssfm.run(w.with_(qpm=q, t_off=5.0))
+    AF0, AS0, eta0 = ssfm.run(w.with_(t_off=0.0))        # dk0 = 0: phase matched
+    assert abs(float(eta) / float(eta0) - 1) < 1e-10
+    assert float((AS - AS0).norm() / AS0.norm()) < 1e-9
+    eta_off = float(ssfm.run(w.with_(qpm=q, t_off=8.0))[2])
+    assert eta_off < (1 - 1e-3) * float(eta0)
+
+
 # ------------------------------------------------------------- gradients ----
 
 def _grad_case():

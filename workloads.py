@@ -69,6 +69,21 @@ def window_for_beam(w0: float, z_focus: float, lambda_f: float = LAMBDA_F,
     return 10.0 * beam_radius(0.0, w0, z_focus, lambda_f, n_f)
 
 
+@dataclass(frozen=True)
+class Qpm:
+    """Inputs of the phase-matching model of Eq. (4): oven temperature (deg C),
+    grating period at 25 C (m), its thermal-expansion coefficients (the
+    paper's MgO:sPPLT values by default) and polynomial coefficients of the
+    refractive indices in (T - 25 C), n_j(T) = sum_k c_k (T - 25)^k (the
+    paper gives no index data, so these are the caller's)."""
+    t_oven: float
+    lambda25: float
+    a_lambda: float = 2.2e-6
+    b_lambda: float = -5.9e-9
+    n_f_t: tuple = (0.0,)
+    n_sh_t: tuple = (0.0,)
+
+
 @dataclass
 class Workload:
     """One SSFM instance: grid, crystal, beam and an optional temperature map."""
@@ -119,6 +134,8 @@ class Workload:
     heat_faces: tuple = ("D",) * 6
     h_conv: object = 0.0
     t_inf: float = 0.0
+    # phase-matching model of Eq. (4), or None for dk0 + dDk/dT dT
+    qpm: Optional[Qpm] = None
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
