@@ -205,6 +205,32 @@ shg_status_t shg_set_monitor(shg_plan_t *plan, int every);
 shg_status_t shg_get_monitor(shg_plan_t *plan, double *z_out, double *p_f_out, double *p_sh_out,
                              int max_samples, int *n_samples);
 
+/* Temperature model of the phase mismatch, Eq. (4):
+ *   Dk(T) = (4 pi / lambda_F) (n_SH(T) - n_F(T)) - 2 pi / Lambda(T),
+ *   Lambda(T) = Lambda(25 C) (1 + a_Lambda (T - 25) + b_Lambda (T - 25)^2)
+ * (the paper's MgO:sPPLT expansion is a_Lambda = 2.2e-6 /K, b_Lambda =
+ * -5.9e-9 /K^2), with n_j(T) = sum_k n_j[k] (T - 25 C)^k supplied by the
+ * caller (the paper gives no index data).  The local temperature is
+ * T = t_oven + T_off + dT(x,y,z). */
+typedef struct {
+    double t_oven;            /* oven temperature (deg C) */
+    double lambda25;          /* grating period Lambda(25 C) (m), > 0 */
+    double a_lambda, b_lambda;
+    double n_f[4], n_sh[4];   /* index polynomials in (T - 25 C) */
+} shg_qpm_t;
+
+/* Use Eq. (4) for the phase (model != NULL) instead of the linearised
+ * dk0 + dDk/dT (dT + T_off), or return to the latter (NULL).  With the model,
+ * phi = Dk(T_ref) z + C'(x,y,z), T_ref = t_oven + T_off, where C' is the
+ * trapezoid cumulative integral along z of Dk(T_ref + dT) - Dk(T_ref) on the
+ * map's nodes (in double precision), interpolated like the map; the crystal's
+ * dk0 and dDk/dT are then unused (the thermal lens keeps dn/dT).  The map
+ * tables depend on T_off, so shg_set_beams rebuilds them.  The adjoint
+ * differentiates the same map (the node gradients carry dDk/dT at each node's
+ * temperature).  SHG_ERR_INVALID_ARG for a non-finite value or
+ * lambda25 <= 0. */
+shg_status_t shg_set_phase_model(shg_plan_t *plan, const shg_qpm_t *model);
+
 /* Reverse sweep of the exact discrete forward map (conjugate propagator,
  * transposed RK4 with Wirtinger calculus), seeded with d_eta = dJ/deta, using
  * the sqrt(nz) checkpoints of the last propagation (shg_propagate or

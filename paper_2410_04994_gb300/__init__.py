@@ -54,6 +54,12 @@ class shg_beams_t(ctypes.Structure):
                 ("t_oven_offset", ctypes.c_double), ("undepleted", ctypes.c_int)]
 
 
+class shg_qpm_t(ctypes.Structure):
+    _fields_ = [("t_oven", ctypes.c_double), ("lambda25", ctypes.c_double),
+                ("a_lambda", ctypes.c_double), ("b_lambda", ctypes.c_double),
+                ("n_f", ctypes.c_double * 4), ("n_sh", ctypes.c_double * 4)]
+
+
 class ShgError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -93,6 +99,7 @@ _SIGS = {
     "shg_set_monitor": [_P, _I],
     "shg_set_heat_boundary": [_P, _IP, _DP, _D],
     "shg_set_heat_method": [_P, _I],
+    "shg_set_phase_model": [_P, ctypes.POINTER(shg_qpm_t)],
     "shg_get_monitor": [_P, _DP, _DP, _DP, _I, _IP],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
@@ -343,6 +350,22 @@ def shg_set_heat_method(plan: int, method: int) -> None:
     _check(_lib().shg_set_heat_method(plan, int(method)), "shg_set_heat_method")
 
 
+def shg_set_phase_model(plan: int, qpm=None) -> None:
+    """Eq. (4) phase model from an object with t_oven, lambda25, a_lambda,
+    b_lambda, n_f_t, n_sh_t (index polynomials in T - 25 C, up to cubic), or
+    None for the linearised model."""
+    if qpm is None:
+        _check(_lib().shg_set_phase_model(plan, None), "shg_set_phase_model")
+        return
+    nf, ns = list(qpm.n_f_t), list(qpm.n_sh_t)
+    if len(nf) > 4 or len(ns) > 4:
+        raise ValueError("index polynomials of degree 3 at most")
+    m = shg_qpm_t(float(qpm.t_oven), float(qpm.lambda25), float(qpm.a_lambda),
+                  float(qpm.b_lambda), (ctypes.c_double * 4)(*(nf + [0.0] * (4 - len(nf)))),
+                  (ctypes.c_double * 4)(*(ns + [0.0] * (4 - len(ns)))))
+    _check(_lib().shg_set_phase_model(plan, ctypes.byref(m)), "shg_set_phase_model")
+
+
 def shg_set_monitor(plan: int, every: int) -> None:
     _check(_lib().shg_set_monitor(plan, int(every)), "shg_set_monitor")
 
@@ -403,6 +426,8 @@ class Plan:
         self.fp64 = bool(flags & SHG_FLAG_FP64)
         self.handle = shg_plan_create(*structs_from(w), flags)
         self._dT = None
+        if getattr(w, "qpm", None) is not None:
+            shg_set_phase_model(self.handle, w.qpm)
         faces = tuple(getattr(w, "heat_faces", ("D",) * 6))
         if (flags & SHG_FLAG_THERMAL) and any(f != "D" for f in faces):
             shg_set_heat_boundary(self.handle, faces, getattr(w, "h_conv", 0.0),

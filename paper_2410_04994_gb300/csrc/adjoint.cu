@@ -222,17 +222,21 @@ __global__ void k_gather(const float* __restrict__ Gc, const float* __restrict__
     outT[k] = st;
 }
 
-// dT_bar[l'] = T_bar[l'] + dZ/2 (S[l'+1] + [l' >= 1] S[l']), S[l] = sum_{m >= l} C_bar[m]:
-// the transpose of the trapezoid cumulative integral C[l] = sum_{m=1..l} dZ/2 (dT[m-1] + dT[m]).
+// dT_bar[l'] = T_bar[l'] + f'(dT[l']) dZ/2 (S[l'+1] + [l' >= 1] S[l']), S[l] = sum_{m >= l} C_bar[m]:
+// the transpose of the trapezoid cumulative integral C[l] = sum_{m=1..l} dZ/2 (f[m-1] + f[m])
+// of the phase integrand f (f = dT, f' = 1 for the linearised model; f = Dk(T_ref + dT) -
+// Dk(T_ref), f' = dDk/dT at the node's temperature for Eq. 4).
 __global__ void k_trapz_T(const double* __restrict__ Cb, const double* __restrict__ Tb, int tx,
-                          int ty, int tz, double dZ, float* __restrict__ g) {
+                          int ty, int tz, double dZ, const float* __restrict__ dT, DkModel m,
+                          float* __restrict__ g) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= tx * ty) return;
     const size_t plane = size_t(tx) * ty;
     double S_next = 0;  // S[l + 1]
     for (int l = tz - 1; l >= 0; --l) {
         const double S_l = S_next + Cb[l * plane + col];
-        const double v = Tb[l * plane + col] + 0.5 * dZ * (S_next + (l >= 1 ? S_l : 0.0));
+        const double fp = m.on ? dk_eq4_slope(m, m.t_ref + double(dT[l * plane + col])) : 1.0;
+        const double v = Tb[l * plane + col] + fp * 0.5 * dZ * (S_next + (l >= 1 ? S_l : 0.0));
         g[l * plane + col] = float(v);
         S_next = S_l;
     }
@@ -398,8 +402,9 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
         for (double v : r) t += v;
         if (g_toven) *g_toven = t;
     }
-    // temperature-map nodes
-    if (thermal && g_dT_dev) {
+    // temperature-map nodes (also needed for the oven offset under Eq. 4)
+    const bool eq4_map = thermal && p->dkm.on;
+    if (thermal && (g_dT_dev || eq4_map)) {
         const int tx = p->tx, ty = p->ty, tz = p->tz;
         const size_t nn = size_t(tx) * ty * tz;
         if (a->ntx != tx || a->nty != ty || a->ntz != tz) {
@@ -455,9 +460,21 @@ extern "C" shg_status_t shg_propagate_adjoint(shg_plan_t* p, double d_eta, doubl
                                                   static_cast<float*>(fx), iy,
                                                   static_cast<float*>(fy), csd, rsd, Cb, Tb);
         k_trapz_T<<<(tx * ty + 127) / 128, 128, 0, st>>>(Cb, Tb, tx, ty, tz, p->c.L / (tz - 1),
-                                                         a->gdT);
+                                                         p->tmap, plan_dk_model(p), a->gdT);
         SHG_CK(cudaGetLastError());
-        SHG_CK(cudaMemcpyAsync(g_dT_dev, a->gdT, nn * sizeof(float), cudaMemcpyDeviceToDevice, st));
+        if (g_dT_dev)
+            SHG_CK(cudaMemcpyAsync(g_dT_dev, a->gdT, nn * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   st));
+        if (eq4_map && g_toven) {
+            // Under Eq. (4) T_off is exactly a uniform shift of every map node (in
+            // the phase and in the lens), so dJ/dT_off is the sum of the node gradients.
+            std::vector<float> h(nn);
+            SHG_CK(cudaMemcpyAsync(h.data(), a->gdT, nn * sizeof(float), cudaMemcpyDeviceToHost, st));
+            SHG_CK(cudaStreamSynchronize(st));
+            double t = 0;
+            for (float v : h) t += double(v);
+            *g_toven = t;
+        }
         SHG_CK(cudaStreamSynchronize(st));
         cudaFree(cellbuf);
     }

@@ -123,11 +123,19 @@ static shg_status_t build_prop_tables(shg_plan* p) {
     return upload(p->pyc, hyc);
 }
 
-// e^{i theta} at every quarter step, theta = (dk0 + g T_off) z reduced mod 2 pi.
+DkModel plan_dk_model(const shg_plan* p) {
+    DkModel m = p->dkm;
+    m.t_ref = m.t_oven + p->b.t_oven_offset;
+    return m;
+}
+
+// e^{i theta} at every quarter step, theta = (dk0 + g T_off) z, or Dk(T_oven +
+// T_off) z with the Eq. (4) model, reduced mod 2 pi.
 static shg_status_t build_phase_table(shg_plan* p) {
     const int nq = 4 * p->g.nz + 1;
     const double dq = p->c.L / p->g.nz / 4;
-    const double rate = p->c.dk0 + p->c.ddk_dT * p->b.t_oven_offset;
+    const DkModel m = plan_dk_model(p);
+    const double rate = m.on ? dk_eq4(m, m.t_ref) : p->c.dk0 + p->c.ddk_dT * p->b.t_oven_offset;
     std::vector<unsigned char> h(nq * p->csize);
     for (int q = 0; q < nq; ++q) {
         const double th = std::fmod(rate * (q * dq), 2 * kPi);
@@ -247,7 +255,15 @@ template <class R> static void fill_desc(const shg_plan* p, InstDesc<R>* d, void
     d->lS = R(2 * kPi / lam_s * p->c.dn_dT);
     d->psi0F = R(2 * kPi / lam_f * p->c.dn_dT * p->b.t_oven_offset);
     d->psi0S = R(2 * kPi / lam_s * p->c.dn_dT * p->b.t_oven_offset);
-    d->g = R(p->c.ddk_dT);
+    // the phase is theta(z) + g C: with the Eq. (4) model the table's C already
+    // holds the integral of Dk (g = 1); without a map g is the slope dDk/dT at
+    // T_oven + T_off, which only the adjoint's oven-offset gradient uses
+    if (p->dkm.on) {
+        const DkModel m = plan_dk_model(p);
+        d->g = R(p->ttab ? 1.0 : dk_eq4_slope(m, m.t_ref));
+    } else {
+        d->g = R(p->c.ddk_dT);
+    }
     d->dz = R(p->c.L / p->g.nz);
     d->undepleted = p->b.undepleted ? 1 : 0;
     d->status = p->status;
@@ -360,17 +376,28 @@ static int forced_variant() {
     return (f && f[0] >= '0' && f[0] <= '4' && f[1] == 0) ? f[0] - '0' : -1;
 }
 
+static bool p_fp32(const std::vector<shg_plan*>& plans) {
+    for (const shg_plan* p : plans)
+        if (p->fp64) return false;
+    return true;
+}
+
 int row_umap_bit(const std::vector<shg_plan*>& plans) {
-    bool any = false;
+    bool any = false, extras = false;
     for (const shg_plan* p : plans) {
+        extras |= ((p->flags & SHG_FLAG_THERMAL) && p->Q) || p->mon;
         if (!p->ttab) continue;
         if (!p->umap || !(double(p->tz - 1) < 0.99 * p->g.nz)) return 0;
         any = true;
     }
-    return any ? kRowUmap : 0;
+    if (!any) return 0;
+    const char* v = getenv("SHG_ROW_LEAN");  // 0: always the instantiation with the z_s code
+    const bool lean_ok = !(v && v[0] == '0');
+    return (lean_ok && p_fp32(plans) && !extras) ? (kRowUmap | kRowLean) : kRowUmap;
 }
 
-static_assert(kRowUmap > 4, "the table-path bit must not collide with a flavour number");
+static_assert(kRowUmap > 4 && kRowLean > 4 && kRowLean != kRowUmap,
+              "the row-pass bits must not collide with a flavour number");
 
 // Candidate flavours of a pass for a length: the default shape, the
 // alternative shape, the default shape in 128-thread CTAs and (column pass)
@@ -514,6 +541,14 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     int hx = 0;
     for (shg_plan* p : plans)
         if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+    if (cluster_path(plans)) {
+        // the whole z-march in one cluster-resident launch
+        e = launch_cluster(nx, descs, ninst, nz, tw, st);
+        if (e != cudaSuccess) return cuda_fail(e, "cluster propagation");
+        e = launch_power(fp64, idescs, descs, ninst, nx, ny, st);
+        if (e != cudaSuccess) return cuda_fail(e, "power");
+        return SHG_OK;
+    }
     const int rb = row_umap_bit(plans);
     const int vr = fft_variant(fp64, nx, 0, rb, ninst) | rb;
     const int vc = fft_variant(fp64, ny, 1, 0, ninst);
@@ -565,7 +600,7 @@ static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
         return enqueue_forward(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, p->idesc, 1, p->tw,
                                one, s, tmaps);
     };
-    {
+    if (!cluster_path(one)) {
         int hx = ((p->flags & SHG_FLAG_THERMAL) && p->Q) ? p->g.hx : 0;
         shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st,
                                     p->has_cmap ? p->cmap_dev : nullptr, row_umap_bit(one));
@@ -610,6 +645,17 @@ const char* shg_status_string(shg_status_t s) {
 const char* shg_last_error(void) { return g_last_error.c_str(); }
 
 static void plan_free(shg_plan* p);
+
+// The map tables of an Eq. (4) plan depend on T_oven + T_off: rebuild them
+// (synchronously) after a change of either.
+static shg_status_t rebuild_model_tables(shg_plan* p) {
+    if (!p->dkm.on || !p->ttab) return SHG_OK;
+    SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, p->tx, p->ty, p->tz,
+                             p->c.L / (p->tz - 1), plan_dk_model(p), nullptr));
+    if (p->umap) SHG_CK(launch_upsample_map(p->desc, p->umap, p->g.nx, p->g.ny, p->tz, nullptr));
+    SHG_CK(cudaStreamSynchronize(nullptr));
+    return SHG_OK;
+}
 
 // Non-null and pairwise distinct: the same plan twice in one call would have
 // two instances write its fields (or rebuild its tables) at once.
@@ -775,7 +821,8 @@ shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
         p->gvalid = false;
     }
     if ((st = build_phase_table(p)) != SHG_OK) return st;
-    return upload_desc(p);
+    if ((st = upload_desc(p)) != SHG_OK) return st;
+    return rebuild_model_tables(p);
 }
 
 shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int ty, int tz,
@@ -800,7 +847,8 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
         if (dT_dev != p->tmap)
             SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice,
                                    s));
-        SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+        SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1),
+                                 plan_dk_model(p), s));
         if (p->umap) SHG_CK(launch_upsample_map(p->desc, p->umap, p->g.nx, p->g.ny, tz, s));
         SHG_CK(cudaEventRecord(p->ready, s));
         p->ready_pending = true;
@@ -845,7 +893,8 @@ shg_status_t shg_set_temperature(shg_plan_t* p, const float* dT_dev, int tx, int
     p->tly = t_ly > 0 ? t_ly : p->g.ly;
     if (dT_dev != p->tmap)
         SHG_CK(cudaMemcpyAsync(p->tmap, dT_dev, n * sizeof(float), cudaMemcpyDeviceToDevice, s));
-    SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1), s));
+    SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, tx, ty, tz, p->c.L / (tz - 1),
+                             plan_dk_model(p), s));
     // per-point table (FP32): tz layers of the field grid
     const size_t ub = size_t(tz) * p->g.nx * p->g.ny * sizeof(float2);
     const bool want = !p->fp64 && !(p->flags & SHG_FLAG_NODE_SAMPLER) && ub <= kUmapMaxBytes &&
@@ -907,7 +956,8 @@ shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const fl
         for (int k : fast) {
             shg_plan* p = plans[k];
             if (p->fp64 != (prec == 1)) continue;
-            jobs.push_back(TtabJob{dT_devs[k], p->tmap, p->ttab, p->c.L / (tz - 1)});
+            jobs.push_back(TtabJob{dT_devs[k], p->tmap, p->ttab, p->c.L / (tz - 1),
+                                   plan_dk_model(p)});
         }
         if (jobs.empty()) continue;
         void* dj = nullptr;
@@ -1040,6 +1090,48 @@ shg_status_t shg_set_monitor(shg_plan_t* p, int every) {
     forget_plan_batches(p);
     p->has_result = false;
     return upload_desc(p);
+}
+
+shg_status_t shg_set_phase_model(shg_plan_t* p, const shg_qpm_t* m) {
+    if (!p) return SHG_ERR_INVALID_ARG;
+    DkModel d{};
+    if (m) {
+        const double v[] = {m->t_oven, m->lambda25, m->a_lambda, m->b_lambda, m->n_f[0], m->n_f[1],
+                            m->n_f[2], m->n_f[3], m->n_sh[0], m->n_sh[1], m->n_sh[2], m->n_sh[3]};
+        for (double x : v)
+            if (!std::isfinite(x)) return SHG_ERR_INVALID_ARG;
+        if (!(m->lambda25 > 0)) return SHG_ERR_INVALID_ARG;
+        d.on = 1;
+        d.t_oven = m->t_oven;
+        d.k_mat = 4 * kPi / p->c.lambda_f;
+        d.lam25 = m->lambda25;
+        d.a = m->a_lambda;
+        d.b = m->b_lambda;
+        for (int k = 0; k < 4; ++k) {
+            d.nF[k] = m->n_f[k];
+            d.nS[k] = m->n_sh[k];
+        }
+    }
+    shg_status_t st = quiesce(p);
+    if (st != SHG_OK) return st;
+    if (p->ready_pending) {
+        SHG_CK(cudaEventSynchronize(p->ready));
+        p->ready_pending = false;
+    }
+    adjoint_forward_state(p, false);
+    const bool was_on = p->dkm.on != 0;
+    p->dkm = d;
+    if ((st = build_phase_table(p)) != SHG_OK) return st;
+    if ((st = upload_desc(p)) != SHG_OK) return st;
+    if (p->ttab && (d.on || was_on)) {
+        // the map's C channel changes meaning: rebuild it from the stored map
+        SHG_CK(launch_build_ttab(p->fp64, p->tmap, p->ttab, p->tx, p->ty, p->tz,
+                                 p->c.L / (p->tz - 1), plan_dk_model(p), nullptr));
+        if (p->umap)
+            SHG_CK(launch_upsample_map(p->desc, p->umap, p->g.nx, p->g.ny, p->tz, nullptr));
+        SHG_CK(cudaStreamSynchronize(nullptr));
+    }
+    return SHG_OK;
 }
 
 shg_status_t shg_get_monitor(shg_plan_t* p, double* z_out, double* p_f_out, double* p_sh_out,

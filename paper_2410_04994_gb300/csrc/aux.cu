@@ -203,17 +203,19 @@ cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, i
     return cudaGetLastError();
 }
 
-// (dT, C) table: C[l] = C[l-1] + dZ/2 (dT[l-1] + dT[l]) accumulated in double
-// (Eq. 3 by the trapezoid rule on the map's z-nodes), stored in the plan's
-// precision.
+// (dT, C) table: C[l] = C[l-1] + dZ/2 (f[l-1] + f[l]) accumulated in double
+// (Eq. 3 by the trapezoid rule on the map's z-nodes) of the integrand f of
+// the phase model (dT itself, or Dk(T_ref + dT) - Dk(T_ref) of Eq. 4),
+// stored in the plan's precision.
 template <class V>
 __global__ void k_build_ttab(const float* __restrict__ dT, V* __restrict__ tt, int tx, int ty,
-                             int tz, double dZ) {
+                             int tz, double dZ, DkModel m) {
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     if (col >= tx * ty) return;
     const size_t plane = size_t(tx) * ty;
     double c = 0;
     float prev = dT[col];
+    double fprev = phase_integrand(m, prev);
     tt[col] = mk<V>(prev, 0);
     // layers in chunks of 16: the loads of a chunk are independent and in
     // flight together; the sum runs in layer order
@@ -226,9 +228,10 @@ __global__ void k_build_ttab(const float* __restrict__ dT, V* __restrict__ tt, i
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (l0 + k < tz) {
-                c += 0.5 * dZ * (double(prev) + double(cur[k]));
+                const double f = phase_integrand(m, cur[k]);
+                c += 0.5 * dZ * (fprev + f);
                 tt[(l0 + k) * plane + col] = mk<V>(cur[k], c);
-                prev = cur[k];
+                fprev = f;
             }
         }
     }
@@ -245,6 +248,7 @@ __global__ void k_build_ttab_batch(const TtabJob* __restrict__ jobs, int tx, int
     V* tt = static_cast<V*>(j.tt);
     double c = 0;
     float prev = j.src[col];
+    double fprev = phase_integrand(j.dkm, prev);
     j.copy[col] = prev;
     tt[col] = mk<V>(prev, 0);
     constexpr int K = 16;
@@ -256,10 +260,11 @@ __global__ void k_build_ttab_batch(const TtabJob* __restrict__ jobs, int tx, int
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             if (l0 + k < tz) {
-                c += 0.5 * j.dZ * (double(prev) + double(cur[k]));
+                const double f = phase_integrand(j.dkm, cur[k]);
+                c += 0.5 * j.dZ * (fprev + f);
                 tt[(l0 + k) * plane + col] = mk<V>(cur[k], c);
                 j.copy[(l0 + k) * plane + col] = cur[k];
-                prev = cur[k];
+                fprev = f;
             }
         }
     }
@@ -276,14 +281,14 @@ cudaError_t launch_build_ttab_batch(bool fp64, const TtabJob* jobs, int njobs, i
 }
 
 cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
-                              double dZ, cudaStream_t st) {
+                              double dZ, const DkModel& dkm, cudaStream_t st) {
     const int cols = tx * ty;
     if (fp64)
         k_build_ttab<double2><<<(cols + 127) / 128, 128, 0, st>>>(dT, static_cast<double2*>(ttab),
-                                                                   tx, ty, tz, dZ);
+                                                                   tx, ty, tz, dZ, dkm);
     else
         k_build_ttab<float2><<<(cols + 127) / 128, 128, 0, st>>>(dT, static_cast<float2*>(ttab),
-                                                                  tx, ty, tz, dZ);
+                                                                  tx, ty, tz, dZ, dkm);
     return cudaGetLastError();
 }
 

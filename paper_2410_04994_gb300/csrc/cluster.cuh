@@ -1,0 +1,177 @@
+// Cluster-resident propagation of one small instance (FP32, N x N, N = 64 or
+// 128): the whole z-march of Eq. (15) in one launch, with the fields held in
+// the shared memory of a thread-block cluster instead of making two round
+// trips through global memory per step.
+//
+// The K CTAs of a cluster split the N x N grid of both fields: CTA c holds
+// rows [cR, cR + R) in its row buffer and columns [cR, cR + R) in its column
+// buffer (R = N / K).  Step s is the same pair of fused passes as the
+// streaming kernels (passes.cuh), with the exchanges through distributed
+// shared memory:
+//   row phase (local)        N_b(s-1), N_a(s) on this CTA's rows, then Lx
+//   cluster barrier
+//   column gather            every CTA reads its columns out of the other
+//                            CTAs' row buffers
+//   column phase (local)     Ly on this CTA's columns
+//   cluster barrier
+//   row gather               every CTA reads its rows out of the other CTAs'
+//                            column buffers
+// A CTA writes its own row buffer only in the row gather, after the second
+// barrier, when every other CTA has finished reading it; it writes its column
+// buffer only in the column gather, after the first barrier, when every other
+// CTA has finished the previous row gather.  So two barriers per step suffice.
+// The barriers are the hardware cluster barrier (every CTA executes the same
+// sequence of them; there is no spin-wait).  The arithmetic per point is that
+// of the streaming passes: the packed-FP32 RK4 of nonlinear.cuh and the
+// register FFT of fft.cuh.
+#pragma once
+#include <cooperative_groups.h>
+
+#include "common.cuh"
+#include "fft.cuh"
+#include "nonlinear.cuh"
+
+namespace shg {
+
+template <int N, int K> struct ClusterGeom {
+    static constexpr int R = N / K;          // rows (and columns) per CTA
+    static constexpr int V = 1;              // 8 points per thread per transform
+    using F = FftCfg<float, N, V>;
+    static constexpr int E = F::E, T = F::T;
+    static constexpr int NT = 2 * R * T;     // one group of T threads per transform (2 fields x R)
+    static constexpr int S = padded_len<float>(N, T < Bank<float>::W ? T : 1);
+    static constexpr int PAIRS = R * N / 2;  // point pairs per CTA
+    static_assert(PAIRS % NT == 0, "whole pairs per thread");
+    static constexpr size_t buf = size_t(2) * R * S * sizeof(float2);  // one of Rbuf, Cbuf
+    static constexpr size_t smem = 2 * buf + size_t(5) * N * sizeof(float4);
+};
+
+template <int N, int K>
+__global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
+    k_cluster_prop(const InstDesc<float>* __restrict__ descs, int nz, const float4* __restrict__ tw) {
+    namespace cg = cooperative_groups;
+    using G = ClusterGeom<N, K>;
+    constexpr int R = G::R, V = G::V, E = G::E, T = G::T, NT = G::NT, S = G::S;
+    cg::cluster_group cluster = cg::this_cluster();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ InstDesc<float> dsh;
+    __shared__ StageZ<float> zsh[5];
+    float2* Rbuf = reinterpret_cast<float2*>(smem_raw);              // [2][R][S] rows
+    float2* Cbuf = reinterpret_cast<float2*>(smem_raw + G::buf);     // [2][R][S] columns
+    float4* twS = reinterpret_cast<float4*>(smem_raw + 2 * G::buf);  // [N]
+    float4* pxS = twS + N;                                           // [2][N]
+    float4* pyS = pxS + 2 * N;                                       // [2][N]
+    const int tid = threadIdx.x;
+    const int cid = int(cluster.block_rank());
+    const int y0 = cid * R;
+    const InstDesc<float>& dg = descs[blockIdx.y];
+    // constant tables and this CTA's rows of both fields
+    stage_tables<float, N>(twS, pxS, tw, dg.px);
+    for (int k = tid; k < 2 * N; k += NT) cp_async(&pyS[k], &dg.py[k]);
+    for (int e = tid; e < 2 * R * N; e += NT) {
+        const int x = e % N, r = (e / N) % R, f = e / (R * N);
+        cp_async(&Rbuf[(f * R + r) * S + pidx<float>(x)], &dg.field[(size_t(f) * N + y0 + r) * N + x]);
+    }
+    if (tid == 0) dsh = dg;
+    cp_async_wait_all();
+    __syncthreads();
+    const InstDesc<float>& d = dsh;
+    const bool thermal = d.ttab != nullptr;   // the launcher admits only the per-point table then
+    const float4* umap4 = reinterpret_cast<const float4*>(d.umap);
+    const float h = 0.5f * d.dz;
+    // transform group of this thread
+    const int g = tid / T, t = tid - g * T;
+    const int gf = g / R, gr = g - gf * R;
+#pragma unroll 1
+    for (int s = 0; s <= nz; ++s) {
+        if (tid < 5) {
+            const int q = 4 * s - 2 + tid;
+            zsh[tid] = stage_z(d, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
+        }
+        __syncthreads();
+        const int lmin = zsh[0].l;
+        // ---- nonlinear half steps on this CTA's rows (two points per thread pass)
+#pragma unroll 1
+        for (int i = 0; i < G::PAIRS / NT; ++i) {
+            const int p = tid + NT * i;
+            const int r = p / (N / 2), j = p - r * (N / 2), x0 = 2 * j;
+            float2* rF = Rbuf + r * S;
+            float2* rS = Rbuf + (R + r) * S;
+            float2 aF0 = rF[pidx<float>(x0)], aF1 = rF[pidx<float>(x0 + 1)];
+            float2 aS0 = rS[pidx<float>(x0)], aS1 = rS[pidx<float>(x0 + 1)];
+            const PairSampler ps{thermal ? umap4 + (size_t(lmin) * N + (y0 + r)) * (N / 2) + j
+                                         : nullptr,
+                                 N * (N / 2), lmin};
+            auto cq = [&](int q) { return coef2_at(d, zsh[q], thermal, ps); };
+            Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, Sx{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
+            const Coef2 z2 = cq(2);
+            if (s > 0) {
+                const Coef2 c0 = cq(0);
+                const Coef2 cm = cq(1);
+                rk4_2(d, F, Sx, c0, cm, z2, h);
+            }
+            if (s < nz) {
+                const Coef2 cm = cq(3);
+                const Coef2 c1 = cq(4);
+                rk4_2(d, F, Sx, z2, cm, c1, h);
+            }
+            up2(F.r, aF0.x, aF1.x);
+            up2(F.i, aF0.y, aF1.y);
+            up2(Sx.r, aS0.x, aS1.x);
+            up2(Sx.i, aS0.y, aS1.y);
+            rF[pidx<float>(x0)] = aF0;
+            rF[pidx<float>(x0 + 1)] = aF1;
+            rS[pidx<float>(x0)] = aS0;
+            rS[pidx<float>(x0 + 1)] = aS1;
+        }
+        __syncthreads();
+        if (s == nz) break;  // the last row pass is N_b alone
+        // ---- Lx on each of this CTA's rows (group g: field gf, row gr)
+        {
+            float2* row = Rbuf + g * S;
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = row[pidx<float>(t + T * m)];
+            __syncthreads();  // the transform's exchanges reuse the row buffer
+            fft_mul_ifft<float, N, V, N>(v, row, t, twS, pxS + gf * N);
+#pragma unroll
+            for (int m = 0; m < E; ++m) row[pidx<float>(t + T * m)] = v[m];
+        }
+        cluster.sync();
+        // ---- column gather: Cbuf[f][c][y] = row y of CTA y / R, column cid R + c
+        for (int e = tid; e < 2 * R * N; e += NT) {
+            const int c = e % R, y = (e / R) % N, f = e / (R * N);
+            const float2* src = cluster.map_shared_rank(Rbuf, y / R);
+            Cbuf[(f * R + c) * S + pidx<float>(y)] = src[(f * R + y % R) * S + pidx<float>(y0 + c)];
+        }
+        __syncthreads();
+        // ---- Ly on each of this CTA's columns (group g: field gf, column gr)
+        {
+            float2* col = Cbuf + g * S;
+            float2 v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = col[pidx<float>(t + T * m)];
+            __syncthreads();
+            fft_mul_ifft<float, N, V, N>(v, col, t, twS, pyS + gf * N);
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[pidx<float>(t + T * m)] = v[m];
+        }
+        cluster.sync();
+        // ---- row gather: Rbuf[f][r][x] = column x of CTA x / R, row y0 + r
+        for (int e = tid; e < 2 * R * N; e += NT) {
+            const int r = e % R, x = (e / R) % N, f = e / (R * N);
+            const float2* src = cluster.map_shared_rank(Cbuf, x / R);
+            Rbuf[(f * R + r) * S + pidx<float>(x)] = src[(f * R + x % R) * S + pidx<float>(y0 + r)];
+        }
+        __syncthreads();
+    }
+    // the final state to global memory
+    for (int e = tid; e < 2 * R * N; e += NT) {
+        const int x = e % N, r = (e / N) % R, f = e / (R * N);
+        d.field[(size_t(f) * N + y0 + r) * N + x] = Rbuf[(f * R + r) * S + pidx<float>(x)];
+    }
+    // no CTA leaves while another may still read its buffers
+    cluster.sync();
+}
+
+}  // namespace shg

@@ -74,10 +74,47 @@ template <class C> SHG_HD C cmulc(C a, C b) {
 template <class C> SHG_HD C cscale(C a, decltype(C::x) s) { return mk<C>(a.x * s, a.y * s); }
 template <class C> SHG_HD C cconj(C a) { return mk<C>(a.x, -a.y); }
 
+// ------------------------------------------------ phase-mismatch model ----
+// Eq. (4): Dk(T) = (4 pi / lambda_F) (n_SH(T) - n_F(T)) - 2 pi / Lambda(T),
+// Lambda(T) = Lambda(25 C) (1 + a (T - 25) + b (T - 25)^2), n_j(T) cubic
+// polynomials in (T - 25 C).  `on` = 0 selects the linearised dk0 + g dT.
+struct DkModel {
+    int on;
+    double t_oven;         // oven temperature (deg C)
+    double t_ref;          // T_oven + T_off (deg C): the uniform part of the temperature
+    double k_mat;          // 4 pi / lambda_F
+    double lam25, a, b;    // grating period at 25 C and its expansion
+    double nF[4], nS[4];   // index polynomial coefficients
+};
+SHG_HD double dk_eq4(const DkModel& m, double T) {
+    const double u = T - 25.0;
+    const double nF = m.nF[0] + u * (m.nF[1] + u * (m.nF[2] + u * m.nF[3]));
+    const double nS = m.nS[0] + u * (m.nS[1] + u * (m.nS[2] + u * m.nS[3]));
+    const double lam = m.lam25 * (1.0 + m.a * u + m.b * u * u);
+    return m.k_mat * (nS - nF) - 6.283185307179586477 / lam;
+}
+// dDk/dT of Eq. (4) at T.
+SHG_HD double dk_eq4_slope(const DkModel& m, double T) {
+    const double u = T - 25.0;
+    const double dF = m.nF[1] + u * (2.0 * m.nF[2] + 3.0 * u * m.nF[3]);
+    const double dS = m.nS[1] + u * (2.0 * m.nS[2] + 3.0 * u * m.nS[3]);
+    const double lam = m.lam25 * (1.0 + m.a * u + m.b * u * u);
+    return m.k_mat * (dS - dF) + 6.283185307179586477 * m.lam25 * (m.a + 2.0 * m.b * u) / (lam * lam);
+}
+// The integrand of the map table's C channel at a node of temperature offset dT:
+// dT itself (linearised model), or Dk(T_ref + dT) - Dk(T_ref) (Eq. 4).
+SHG_HD double phase_integrand(const DkModel& m, double dT) {
+    return m.on ? dk_eq4(m, m.t_ref + dT) - dk_eq4(m, m.t_ref) : dT;
+}
+
 // ------------------------------------------------------ per-instance ----
 // Everything one pass needs about one instance; built on the host by the plan.
 // Launch-variant bit of the row pass: read the per-point temperature table.
 constexpr int kRowUmap = 8;  // above every flavour number (0-4)
+// Launch bit of the row pass (with kRowUmap only): no instance of the group
+// deposits heat or monitors its power, so the kernel is instantiated without
+// that code at z_s.
+constexpr int kRowLean = 16;
 
 template <class R> struct InstDesc {
     cx<R>* field;          // [2][ny][nx]: A_F then A_SH

@@ -44,9 +44,9 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads>
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
 cudaError_t row_attr() {
-    return allow_max_dyn_smem(k_row_pass<R, N, V, UM, NTH>);
+    return allow_max_dyn_smem(k_row_pass<R, N, V, UM, NTH, ZS>);
 }
 
 // Dynamic shared memory of a row pass: transform buffers + table prefetch
@@ -60,12 +60,13 @@ template <class R, int N, int V = 0, int NTH = kPassThreads> cudaError_t col_att
     return allow_max_dyn_smem(k_col_pass<R, N, V, NTH>);
 }
 
-template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads>
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
 cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, const void* tw,
                        int hx, cudaStream_t st) {
     using G = RowGeom<R, N, V, NTH>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    return launch_pdl(k_row_pass<R, N, V, UM, NTH>, grid, dim3(NTH), row_smem<R, N, V, UM, NTH>(hx),
+    return launch_pdl(k_row_pass<R, N, V, UM, NTH, ZS>, grid, dim3(NTH),
+                      row_smem<R, N, V, UM, NTH>(ZS ? hx : 0),
                       st, static_cast<const InstDesc<R>*>(descs), ny, nz, s,
                       static_cast<const pt<R>*>(tw));
 }

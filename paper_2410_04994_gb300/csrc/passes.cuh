@@ -120,7 +120,9 @@ SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, i
 // point samples the node table bilinearly.  The heat deposit at z_s (THERMAL plans) is binned
 // per CTA in shared memory and added to the heat grid with one
 // double-precision atomic per touched node.
-template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads>
+// ZS = false: the instantiation for groups without heat deposits or power
+// monitors (the code at z_s between the two half steps is compiled out).
+template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
 __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             }
         }
     }
-    const bool dep = descs[blockIdx.y].Q != nullptr;
+    const bool dep = ZS && descs[blockIdx.y].Q != nullptr;
     float4* slots = reinterpret_cast<float4*>(smem_raw + G::fields);
     const float4* umap4 = reinterpret_cast<const float4*>(descs[blockIdx.y].umap);
     float* bins = reinterpret_cast<float*>(pS + 2 * NX);
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
         }
     };
     // Power monitor: this thread's share of sum |A_F|^2, sum |A_SH|^2 at z_s.
-    const bool mon = d.mon != nullptr && (s % d.mon_every == 0 || s == nz);
+    const bool mon = ZS && d.mon != nullptr && (s % d.mon_every == 0 || s == nz);
     R monF = R(0), monS = R(0);
     auto monitor = [&](const C& aF, const C& aS) {
         monF += aF.x * aF.x + aF.y * aF.y;

@@ -42,8 +42,16 @@ static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int n
     return cudaErrorInvalidValue;
 }
 
+// passes_f32_lean.cu: the table-path rows without the code at z_s.
+cudaError_t row_f32_lean(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
+                         const void* tw, cudaStream_t st);
+cudaError_t attr_f32_lean();
+
 cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
                     const void* tw, int hx, cudaStream_t st) {
+    if ((v & kRowUmap) && (v & kRowLean))
+        return row_f32_lean(nx, v & ~(kRowUmap | kRowLean), descs, ninst, ny, nz, s, tw, st);
+    v &= ~kRowLean;
     return (v & kRowUmap) ? row_f32_um<true>(nx, v & ~kRowUmap, descs, ninst, ny, nz, s, tw, hx, st)
                           : row_f32_um<false>(nx, v, descs, ninst, ny, nz, s, tw, hx, st);
 }
@@ -135,12 +143,14 @@ cudaError_t attr_f32() {
     if (e == cudaSuccess) e = col_tma_attr<n>();
     SHG_F32_TMA_SIZES(X)
 #undef X
+    if (e == cudaSuccess) e = attr_f32_lean();
     return e;
 }
 
 size_t row_smem_f32(int nx, int v, int hx) {
     const bool um = (v & kRowUmap) != 0;
-    v &= ~kRowUmap;
+    if (um && (v & kRowLean)) hx = 0;  // no deposit bins
+    v &= ~(kRowUmap | kRowLean);
     if (v == 3) {
         switch (nx) {
 #define X(n) case n: return um ? row_smem<float, n, 0, true, 128>(hx) : row_smem<float, n, 0, false, 128>(hx);

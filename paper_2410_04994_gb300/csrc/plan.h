@@ -87,6 +87,7 @@ struct shg_plan {
     double heat_h[6] = {0, 0, 0, 0, 0, 0};  // heat transfer coefficient of each convective face
     double heat_tinf = 0;                    // T_inf - T_oven (K)
     int heat_method = 0;                     // SHG_HEAT_DIRECT or SHG_HEAT_SOR
+    DkModel dkm{};                           // Eq. (4) model (dkm.on) or the linearised one
     shg::HeatDirect* hdir = nullptr;         // eigenbases and work buffers of the direct solve
 
     // tensor map of `field` for the TMA column pass (FP32, supported lengths)
@@ -146,19 +147,21 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
 // kRowUmap if the row passes of these plans (one grid) read the per-point
 // temperature table: every plan with a map keeps one, and one z-step spans
 // less than one map layer (so a pass touches at most three layers); else 0.
+// With kRowUmap, also kRowLean when no plan deposits heat or monitors power.
 int row_umap_bit(const std::vector<shg_plan*>& plans);
 cudaError_t launch_init(bool fp64, const InitDesc* idescs, void* const* fields_unused, int ninst,
                         const void* descs, int nx, int ny, cudaStream_t st);
 cudaError_t launch_power(bool fp64, const InitDesc* idescs, const void* descs, int ninst, int nx,
                          int ny, cudaStream_t st);
 cudaError_t launch_build_ttab(bool fp64, const float* dT, void* ttab, int tx, int ty, int tz,
-                              double dZ, cudaStream_t st);
+                              double dZ, const DkModel& dkm, cudaStream_t st);
 // One map update of a batched temperature update (device-resident array).
 struct TtabJob {
     const float* src;  // the new map [tz][ty][tx]
     float* copy;       // the plan's copy of it
     void* tt;          // the plan's (dT, C) table
     double dZ;         // layer spacing L / (tz - 1)
+    DkModel dkm;       // the plan's phase-mismatch model (integrand of C)
 };
 cudaError_t launch_build_ttab_batch(bool fp64, const TtabJob* jobs, int njobs, int tx, int ty,
                                     int tz, cudaStream_t st);
@@ -190,6 +193,14 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
                              const std::vector<shg_plan*>& plans, cudaStream_t st,
                              const void* tmaps = nullptr, int* status_arr = nullptr);
 
+// Cluster-resident propagation of a single small FP32 instance (cluster_f32.cu):
+// whether the plans (one plan) take it, the cluster size used for an n x n
+// grid (0: none), and the launch of the whole z-march.
+bool cluster_path(const std::vector<shg_plan*>& plans);
+int cluster_size(int n);
+cudaError_t launch_cluster(int n, const void* descs, int ninst, int nz, const void* tw,
+                           cudaStream_t st);
+
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);
 void free_adjoint(shg_plan* p);
@@ -200,6 +211,9 @@ shg_status_t heat_direct_solve(shg_plan* p, int max_iters, double tol, double* r
 shg_status_t adjoint_alloc(shg_plan* p);
 // Enqueue the checkpoint copy of the state entering row pass R(s) (adjoint plans).
 shg_status_t adjoint_checkpoint(shg_plan* p, int s, cudaStream_t st);
+// The plan's phase-mismatch model with its reference temperature set to
+// T_oven + T_off (no-op copy for the linearised model).
+DkModel plan_dk_model(const shg_plan* p);
 // Whether the checkpoints hold the forward pass of the plan's current inputs:
 // set by every completed shg_propagate or shg_batch_submit (both write the
 // checkpoints of adjoint plans), cleared by every change of beams,

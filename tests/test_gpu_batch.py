@@ -27,8 +27,11 @@ def _mixed(nz=30):
     return W.sweep_instances(nz=nz, groups=((16, 3), (32, 4), (64, 2)), tgrid=(9, 9, 12))
 
 
-def test_batch_equals_single_plan_propagation():
+def test_batch_equals_single_plan_propagation(monkeypatch):
     import paper_2410_04994_gb300 as pkg
+    # the same streaming kernels on both sides (single small plans would
+    # otherwise take the cluster-resident path)
+    monkeypatch.setenv("SHG_CLUSTER", "0")
     insts = _mixed()
     plans = _plans(insts)
     etas = pkg.shg_batch_submit([p.handle for p in plans])

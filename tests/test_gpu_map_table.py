@@ -22,6 +22,13 @@ from tests.helpers import ETA_TOL, FIELD_TOL, oracle_run, rel_l2
 pytestmark = pytest.mark.gpu
 
 
+@pytest.fixture(autouse=True)
+def _streaming_passes(monkeypatch):
+    """These tests are about the streaming passes' temperature lookup: keep
+    single plans off the cluster-resident path."""
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+
+
 def _run(w, node_sampler=False):
     import paper_2410_04994_gb300 as pkg
     plan = pkg.Plan(w, node_sampler=node_sampler)

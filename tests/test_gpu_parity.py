@@ -114,8 +114,9 @@ def test_every_kernel_flavour_of_the_autotuner(n, variant, monkeypatch):
     """Each kernel flavour the autotuner can pick, forced through
     SHG_FFT_VARIANT (0/1: the two FFT shapes with cp.async staging, 2: the
     TMA-staged column pass, 3/4: both passes in 128-/64-thread CTAs), matches
-    the oracle on its own."""
+    the oracle on its own (single plans kept on the streaming passes)."""
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
+    monkeypatch.setenv("SHG_CLUSTER", "0")
     w = W.depleted_absorbing(n=n, nz=6 if n < 1024 else 1, tgrid=(9, 7, 5), p1=400.0)
     _compare(w, ETA_TOL, FIELD_TOL)
 
@@ -128,6 +129,7 @@ def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
     matches the oracle."""
     import paper_2410_04994_gb300 as pkg
     monkeypatch.setenv("SHG_FFT_VARIANT", "2")
+    monkeypatch.setenv("SHG_CLUSTER", "0")   # the TMA column pass is a streaming pass
     w = W.plain_focused(n=64, nz=4, precision="f32")
     plan = pkg.Plan(w)
     pkg.shg_set_wait_limit(plan.handle, 0)
