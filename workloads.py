@@ -247,6 +247,75 @@ def thermal_loop(n: int = 1024, nz: int = 8000, xi: float = 2.84, p1: float = 10
                            hz=hz, n_outer=n_outer, t_lx=CRYSTAL_WX, t_ly=CRYSTAL_WY))
 
 
+@dataclass
+class ThreeWave:
+    """One three-wave mixing instance (sum- or difference-frequency
+    generation, omega_3 = omega_1 + omega_2): grid, crystal, the three input
+    beams (power 0: no input at that wave) and an optional temperature map."""
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    lx: float
+    ly: float
+    lambda1: float
+    lambda2: float
+    n1: float
+    n2: float
+    n3: float
+    L: float = L_CRYSTAL
+    d_eff: float = D_EFF
+    alpha: tuple = (0.0, 0.0, 0.0)
+    beta: tuple = (0.0, 0.0, 0.0)
+    dk0: float = 0.0
+    ddk_dT: float = 0.0
+    dn_dT: float = 0.0
+    walkoff: tuple = (0.0, 0.0, 0.0)
+    p: tuple = (1.0, 1.0, 0.0)
+    w0: tuple = (30e-6, 30e-6, 30e-6)
+    z_focus: tuple = (L_CRYSTAL / 2,) * 3
+    t_off: float = 0.0
+    undepleted: bool = False
+    precision: str = "f32"
+    dT: Optional[np.ndarray] = None
+    t_lx: float = 0.0
+    t_ly: float = 0.0
+
+    def with_(self, **kw) -> "ThreeWave":
+        return replace(self, **kw)
+
+
+def sfg_case(n: int = 64, nz: int = 200, p=(20.0, 30.0, 0.0), xi: float = 1.5,
+             seed: int = 0, tgrid=(16, 16, 32), with_map: bool = True) -> ThreeWave:
+    """Sum-frequency generation 1550 nm + 1064 nm -> 631 nm in the 30 mm QPM
+    crystal: both inputs focused at the centre with the same confocal
+    parameter (xi for the 1550 nm beam), the losses and temperature
+    coefficients of the absorbing SHG workloads, a seeded map."""
+    l1, l2 = 1.55e-6, LAMBDA_F
+    n1, n2, n3 = 2.13, N_F, 2.165
+    k1 = 2 * math.pi * n1 / l1
+    k2 = 2 * math.pi * n2 / l2
+    zr = L_CRYSTAL / (2 * xi)
+    w01, w02 = math.sqrt(2 * zr / k1), math.sqrt(2 * zr / k2)
+    lw = 10.0 * max(w01, w02) * math.sqrt(1 + xi * xi)
+    dT = None
+    if with_map:
+        rng = np.random.default_rng(seed)
+        tx, ty, tz = tgrid
+        dT = gaussian_dT_map(tx, ty, tz, lw, lw, L_CRYSTAL, w02, L_CRYSTAL / 2, rng)
+    return ThreeWave(name=f"sfg_{n}x{n}_nz{nz}", nx=n, ny=n, nz=nz, lx=lw, ly=lw, lambda1=l1,
+                     lambda2=l2, n1=n1, n2=n2, n3=n3, alpha=(0.1, ALPHA_F, 1.0),
+                     beta=(0.0, 0.0, BETA_SH), ddk_dT=DDK_DT, dn_dT=DN_DT, p=tuple(p),
+                     w0=(w01, w02, w02), dT=dT, t_lx=lw, t_ly=lw)
+
+
+def dfg_case(n: int = 64, nz: int = 200, **kw) -> ThreeWave:
+    """Difference-frequency generation 631 nm - 1064 nm -> 1550 nm: the same
+    crystal with the pump at omega_3 and a seed at omega_2; wave 1 grows."""
+    w = sfg_case(n=n, nz=nz, p=(0.0, 2.0, 40.0), **kw)
+    return w.with_(name=f"dfg_{n}x{n}_nz{nz}")
+
+
 # Oven arrangements of Sec. 4.2 (Tfield::setOvenSurrounded / setBottomOvens):
 # the faces held at the oven temperature, the rest cooled by convection.
 OVENS = {
