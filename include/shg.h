@@ -286,8 +286,9 @@ shg_status_t shg_set_heat_boundary(shg_plan_t *plan, const int *kinds, const dou
 /* Method of shg_heat_solve and shg_thermal_loop:
  *   SHG_HEAT_DIRECT (default): the operator of Eq. (16) is a Kronecker sum of
  *     three 1-D operators, so it is solved directly: FP32 transforms to the
- *     eigenbases of the x and y operators (computed once per boundary by
- *     Jacobi rotations on the host), one tridiagonal solve along z per
+ *     eigenbases of the x and y operators (computed by Jacobi rotations on
+ *     the host when the plan is created and when the boundary changes, tens of
+ *     milliseconds at 128 nodes per axis), one tridiagonal solve along z per
  *     transverse mode, transforms back, repeated as FP64 iterative refinement
  *     of dT until the largest Jacobi correction is below tol (max_sweeps
  *     bounds the refinement passes, at most 50; the solves report passes).
@@ -361,6 +362,55 @@ shg_status_t shg_measure_peaks(double *fp32_tflops, double *l2_read_gbs,
 shg_status_t shg_field_powers_noalloc(const void *fields_dev, int nx, int ny, int n_inst,
                                       int fp64, double lx, double ly, double n_f,
                                       double n_sh, double *powers_dev, shg_stream_t stream);
+
+/* ---- Three-wave mixing (sum- and difference-frequency generation) ----
+ * The paper closes (Sec. 6) with the coupled-wave model as a starting point
+ * for other three-wave processes.  A three-wave plan propagates three fields
+ * at omega_3 = omega_1 + omega_2 with the split step of Eq. (15):
+ *   dA1/dz = i k1 A3 conj(A2) e^{-i phi} - (1/2) beta1 I1 A1 + i psi1 A1
+ *   dA2/dz = i k2 A3 conj(A1) e^{-i phi} - (1/2) beta2 I2 A2 + i psi2 A2
+ *   dA3/dz = i k3 A1 A2 e^{+i phi}       - (1/2) beta3 I3 A3 + i psi3 A3
+ * with k_j = 2 pi d_eff / (n_j lambda_j), lambda3 = 1 / (1/lambda1 + 1/lambda2),
+ * I_j = eps0 c n_j |A_j|^2 / 2, phi and psi_j as for SHG (dk0 + g (T_off + dT),
+ * lens (2 pi / lambda_j) dn/dT (dT + T_off)), and each wave's own diffraction,
+ * absorption alpha_j and walk-off rho_j in K-space.  Sum-frequency generation
+ * starts with P1, P2 > 0 and P3 = 0; difference-frequency generation with a
+ * pump at omega_3 and a seed at omega_2 (P1 = 0).  With lambda1 = lambda2,
+ * n1 = n2 and A1 = A2 the equations are those of SHG (k3 = 2 k_SH). */
+typedef struct {
+    double L, lambda1, lambda2;   /* crystal length, input wavelengths (m) */
+    double n1, n2, n3, d_eff;
+    double alpha[3], beta[3];     /* per wave: 1/m (power), m/W */
+    double dk0, ddk_dT, dn_dT;
+    double walkoff[3];            /* rad, |rho| < 1.5 */
+} shg_crystal3_t;
+
+typedef struct {
+    double p[3], w0[3], z_focus[3];  /* per wave: power (W, >= 0), waist, focus (Eq. 5) */
+    double t_oven_offset;
+    int undepleted;                  /* drop the coupling terms of waves 1 and 2 */
+} shg_beams3_t;
+
+/* Create a three-wave plan.  flags: 0 or SHG_FLAG_FP64 (no heat grid,
+ * adjoint or sampler flags).  The plan accepts shg_set_temperature (and the
+ * batched form), shg_propagate, shg_efficiency (eta = P3(L) / sum of the input
+ * powers, *p_f = P1(L), *p_sh = P3(L)), shg_powers, shg_get_field, shg_set_wait_limit
+ * and shg_plan_destroy; the calls of the SHG-specific state (beams, fields,
+ * monitor, phase model, adjoint, heat, batches, pass timing) return
+ * SHG_ERR_INVALID_ARG or SHG_ERR_STATE.  SHG_ERR_INVALID_ARG for a non-finite
+ * value, a non-positive length, wavelength, index or waist, a negative
+ * power, no input power, or another flag. */
+shg_status_t shg_plan_create_3w(const shg_grid_t *grid, const shg_crystal3_t *crystal,
+                                const shg_beams3_t *beams, int flags, shg_plan_t **out);
+
+/* Copy field j (0-based: 0 = A_F, 1 = A_SH of an SHG plan; 0, 1, 2 = A1, A2,
+ * A3 of a three-wave plan) of the current state to a device buffer of
+ * ny x nx complex values of the plan's precision. */
+shg_status_t shg_get_field(shg_plan_t *plan, int j, void *dev, shg_stream_t stream);
+
+/* Discrete powers of the last propagation's fields (W): out[0..n) with n >= 2
+ * (SHG: P_F, P_SH) or n >= 3 (three-wave: P1, P2, P3).  Synchronises. */
+shg_status_t shg_powers(shg_plan_t *plan, double *out, int n);
 
 /* Static description of a status code. */
 const char *shg_status_string(shg_status_t status);

@@ -60,6 +60,20 @@ class shg_qpm_t(ctypes.Structure):
                 ("n_f", ctypes.c_double * 4), ("n_sh", ctypes.c_double * 4)]
 
 
+class shg_crystal3_t(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("lambda1", ctypes.c_double), ("lambda2", ctypes.c_double),
+                ("n1", ctypes.c_double), ("n2", ctypes.c_double), ("n3", ctypes.c_double),
+                ("d_eff", ctypes.c_double), ("alpha", ctypes.c_double * 3),
+                ("beta", ctypes.c_double * 3), ("dk0", ctypes.c_double), ("ddk_dT", ctypes.c_double),
+                ("dn_dT", ctypes.c_double), ("walkoff", ctypes.c_double * 3)]
+
+
+class shg_beams3_t(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_double * 3), ("w0", ctypes.c_double * 3),
+                ("z_focus", ctypes.c_double * 3), ("t_oven_offset", ctypes.c_double),
+                ("undepleted", ctypes.c_int)]
+
+
 class ShgError(RuntimeError):
     def __init__(self, status: int, where: str):
         self.status = status
@@ -100,6 +114,10 @@ _SIGS = {
     "shg_set_heat_boundary": [_P, _IP, _DP, _D],
     "shg_set_heat_method": [_P, _I],
     "shg_set_phase_model": [_P, ctypes.POINTER(shg_qpm_t)],
+    "shg_plan_create_3w": [ctypes.POINTER(shg_grid_t), ctypes.POINTER(shg_crystal3_t),
+                           ctypes.POINTER(shg_beams3_t), _I, ctypes.POINTER(_P)],
+    "shg_get_field": [_P, _I, _P, _P],
+    "shg_powers": [_P, _DP, _I],
     "shg_get_monitor": [_P, _DP, _DP, _DP, _I, _IP],
 }
 EXPORTED = list(_SIGS) + ["shg_status_string", "shg_last_error"]
@@ -350,6 +368,24 @@ def shg_set_heat_method(plan: int, method: int) -> None:
     _check(_lib().shg_set_heat_method(plan, int(method)), "shg_set_heat_method")
 
 
+def shg_plan_create_3w(grid: shg_grid_t, crystal: shg_crystal3_t, beams: shg_beams3_t,
+                       flags: int = 0) -> int:
+    out = _P()
+    _check(_lib().shg_plan_create_3w(ctypes.byref(grid), ctypes.byref(crystal), ctypes.byref(beams),
+                                     int(flags), ctypes.byref(out)), "shg_plan_create_3w")
+    return out.value
+
+
+def shg_get_field(plan: int, j: int, dev, stream=None) -> None:
+    _check(_lib().shg_get_field(plan, int(j), _ptr(dev), _stream(stream)), "shg_get_field")
+
+
+def shg_powers(plan: int, n: int = 3):
+    out = (_D * n)()
+    _check(_lib().shg_powers(plan, out, int(n)), "shg_powers")
+    return list(out)
+
+
 def shg_set_phase_model(plan: int, qpm=None) -> None:
     """Eq. (4) phase model from an object with t_oven, lambda25, a_lambda,
     b_lambda, n_f_t, n_sh_t (index polynomials in T - 25 C, up to cubic), or
@@ -477,3 +513,55 @@ class Plan:
         a_sh = torch.empty_like(a_f)
         shg_get_fields(self.handle, a_f, a_sh, stream)
         return a_f, a_sh
+
+
+def structs3_from(w):
+    """(grid, crystal, beams) structs of a three-wave workload (an object with
+    nx, ny, nz, lx, ly, L, lambda1, lambda2, n1, n2, n3, d_eff, alpha, beta,
+    dk0, ddk_dT, dn_dT, walkoff, p, w0, z_focus, t_off, undepleted)."""
+    t3 = ctypes.c_double * 3
+    grid = shg_grid_t(w.nx, w.ny, w.nz, w.lx, w.ly, 0, 0, 0)
+    crystal = shg_crystal3_t(w.L, w.lambda1, w.lambda2, w.n1, w.n2, w.n3, w.d_eff, t3(*w.alpha),
+                             t3(*w.beta), w.dk0, w.ddk_dT, w.dn_dT, t3(*w.walkoff))
+    beams = shg_beams3_t(t3(*w.p), t3(*w.w0), t3(*w.z_focus), w.t_off, 1 if w.undepleted else 0)
+    return grid, crystal, beams
+
+
+class Plan3:
+    """Owning handle around a three-wave (sum/difference-frequency) plan."""
+
+    def __init__(self, w):
+        self.w = w
+        self.fp64 = getattr(w, "precision", "f32") == "f64"
+        self.handle = shg_plan_create_3w(*structs3_from(w), SHG_FLAG_FP64 if self.fp64 else 0)
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h:
+            try:
+                shg_plan_destroy(h)
+            except Exception:
+                pass
+            self.handle = None
+
+    def set_temperature(self, dT, t_lx=0.0, t_ly=0.0, stream=None):
+        import torch
+        dT = torch.as_tensor(dT).to(device="cuda", dtype=torch.float32).contiguous()
+        self._dT = dT
+        shg_set_temperature(self.handle, dT, t_lx, t_ly, stream)
+
+    def propagate(self, stream=None):
+        shg_propagate(self.handle, stream)
+
+    def powers(self):
+        return shg_powers(self.handle, 3)
+
+    def fields(self, stream=None):
+        import torch
+        dt = torch.complex128 if self.fp64 else torch.complex64
+        out = []
+        for j in range(3):
+            a = torch.empty((self.w.ny, self.w.nx), dtype=dt, device="cuda")
+            shg_get_field(self.handle, j, a, stream)
+            out.append(a)
+        return out

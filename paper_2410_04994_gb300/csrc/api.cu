@@ -323,6 +323,7 @@ static shg_status_t upload_desc(shg_plan* p) {
     InitDesc id;
     fill_init(p, &id);
     SHG_CK(cudaMemcpy(p->idesc, &id, sizeof(id), cudaMemcpyHostToDevice));
+    if (p->w3) return upload_desc3(p);
     return SHG_OK;
 }
 
@@ -385,7 +386,7 @@ static bool p_fp32(const std::vector<shg_plan*>& plans) {
 int row_umap_bit(const std::vector<shg_plan*>& plans) {
     bool any = false, extras = false;
     for (const shg_plan* p : plans) {
-        extras |= ((p->flags & SHG_FLAG_THERMAL) && p->Q) || p->mon;
+        extras |= p->mon != nullptr;
         if (!p->ttab) continue;
         if (!p->umap || !(double(p->tz - 1) < 0.99 * p->g.nz)) return 0;
         any = true;
@@ -593,6 +594,22 @@ static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
 }
 
 static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
+    if (p->w3) {
+        // three-wave mixing: its own passes, captured into the plan's graph
+        auto body3 = [&](cudaStream_t q) { return enqueue_forward3(p, q); };
+        if (!use_graphs()) return body3(st);
+        if (!p->gvalid) {
+            if (p->gexec) {
+                cudaGraphExecDestroy(p->gexec);
+                p->gexec = nullptr;
+            }
+            shg_status_t r = capture(p->cap, body3, &p->gexec);
+            if (r != SHG_OK) return r;
+            p->gvalid = true;
+        }
+        SHG_CK(cudaGraphLaunch(p->gexec, st));
+        return SHG_OK;
+    }
     std::vector<shg_plan*> one{p};
     PdlScope pdl(true);  // one grid group
     const void* tmaps = p->has_cmap ? p->cmap_dev : nullptr;
@@ -766,6 +783,8 @@ shg_status_t shg_plan_create(const shg_grid_t* grid, const shg_crystal_t* crysta
         (st = build_tensor_map(p)) != SHG_OK ||
         (st = build_twiddles(p)) != SHG_OK ||
         ((flags & SHG_FLAG_THERMAL) && (st = build_heat_index(p)) != SHG_OK) ||
+        // eigenbases of the direct heat solve for the default (oven-held) faces
+        ((flags & SHG_FLAG_THERMAL) && (st = heat_direct_setup(p)) != SHG_OK) ||
         (st = upload_desc(p)) != SHG_OK ||
         ((flags & SHG_FLAG_ADJOINT) && (st = adjoint_alloc(p)) != SHG_OK)) {
         plan_free(p);
@@ -781,6 +800,7 @@ static void plan_free(shg_plan* p) {
     shg::forget_plan_batches(p);
     shg::free_adjoint(p);
     shg::free_heat_direct(p);
+    shg::free_three_wave(p);
     if (p->gexec) cudaGraphExecDestroy(p->gexec);
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->done) cudaEventDestroy(p->done);
@@ -811,7 +831,7 @@ shg_status_t shg_set_wait_limit(shg_plan_t* p, unsigned polls) {
 }
 
 shg_status_t shg_set_beams(shg_plan_t* p, const shg_beams_t* beams) {
-    if (!p || !beams || !finite_beams(beams)) return SHG_ERR_INVALID_ARG;
+    if (!p || !beams || !finite_beams(beams) || p->w3) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
     adjoint_forward_state(p, false);
@@ -1001,7 +1021,7 @@ shg_status_t shg_set_temperature_batch(shg_plan_t* const* plans, int n, const fl
 
 shg_status_t shg_set_fields(shg_plan_t* p, const void* a_f_dev, const void* a_sh_dev,
                             shg_stream_t stream) {
-    if (!p) return SHG_ERR_INVALID_ARG;
+    if (!p || p->w3) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
     adjoint_forward_state(p, false);
@@ -1041,6 +1061,18 @@ shg_status_t shg_propagate(shg_plan_t* p, shg_stream_t stream) {
 shg_status_t shg_efficiency(shg_plan_t* p, double* eta, double* p_f, double* p_sh) {
     if (!p) return SHG_ERR_INVALID_ARG;
     if (!p->has_result) return SHG_ERR_STATE;
+    if (p->w3) {
+        double pw[3];
+        shg_status_t r = three_wave_powers(p, pw);
+        if (r != SHG_OK) return r;
+        const double pin = three_wave_input_power(p);
+        const double e = pin > 0 ? pw[2] / pin : 0.0;
+        if (eta) *eta = e;
+        if (p_f) *p_f = pw[0];
+        if (p_sh) *p_sh = pw[2];
+        return (std::isfinite(e) && std::isfinite(pw[0]) && std::isfinite(pw[1])) ? SHG_OK
+                                                                                  : SHG_ERR_NONFINITE;
+    }
     SHG_CK(cudaStreamSynchronize(p->last_stream));
     int kst = p->batch_kst;  // a batch reports kernel errors per instance on the host
     if (!p->batch_result)
@@ -1057,7 +1089,7 @@ shg_status_t shg_efficiency(shg_plan_t* p, double* eta, double* p_f, double* p_s
 }
 
 shg_status_t shg_get_fields(shg_plan_t* p, void* a_f_dev, void* a_sh_dev, shg_stream_t stream) {
-    if (!p) return SHG_ERR_INVALID_ARG;
+    if (!p || p->w3) return SHG_ERR_INVALID_ARG;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (p->last_stream != s && p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
     const size_t one = size_t(p->g.nx) * p->g.ny * p->csize;
@@ -1067,8 +1099,101 @@ shg_status_t shg_get_fields(shg_plan_t* p, void* a_f_dev, void* a_sh_dev, shg_st
     return SHG_OK;
 }
 
+shg_status_t shg_get_field(shg_plan_t* p, int j, void* dev, shg_stream_t stream) {
+    const int nf = (p && p->w3) ? 3 : 2;
+    if (!p || !dev || j < 0 || j >= nf) return SHG_ERR_INVALID_ARG;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->last_stream != s && p->has_result) SHG_CK(cudaStreamSynchronize(p->last_stream));
+    const size_t one = size_t(p->g.nx) * p->g.ny * p->csize;
+    SHG_CK(cudaMemcpyAsync(dev, static_cast<const unsigned char*>(p->field) + size_t(j) * one, one,
+                           cudaMemcpyDeviceToDevice, s));
+    return SHG_OK;
+}
+
+shg_status_t shg_powers(shg_plan_t* p, double* out, int n) {
+    const int nf = (p && p->w3) ? 3 : 2;
+    if (!p || !out || n < nf) return SHG_ERR_INVALID_ARG;
+    if (!p->has_result) return SHG_ERR_STATE;
+    if (p->w3) return three_wave_powers(p, out);
+    double e = 0;
+    shg_status_t r = shg_efficiency(p, &e, &out[0], &out[1]);
+    return r;
+}
+
+static bool finite3(const shg_crystal3_t* c, const shg_beams3_t* b) {
+    const double v[] = {c->L, c->lambda1, c->lambda2, c->n1, c->n2, c->n3, c->d_eff, c->alpha[0],
+                        c->alpha[1], c->alpha[2], c->beta[0], c->beta[1], c->beta[2], c->dk0,
+                        c->ddk_dT, c->dn_dT, c->walkoff[0], c->walkoff[1], c->walkoff[2],
+                        b->p[0], b->p[1], b->p[2], b->w0[0], b->w0[1], b->w0[2], b->z_focus[0],
+                        b->z_focus[1], b->z_focus[2], b->t_oven_offset};
+    for (double x : v)
+        if (!std::isfinite(x)) return false;
+    return true;
+}
+
+shg_status_t shg_plan_create_3w(const shg_grid_t* grid, const shg_crystal3_t* c,
+                                const shg_beams3_t* b, int flags, shg_plan_t** out) {
+    if (out) *out = nullptr;
+    if (!grid || !c || !b || !out || !finite3(c, b)) return SHG_ERR_INVALID_ARG;
+    if (flags & ~SHG_FLAG_FP64) return SHG_ERR_INVALID_ARG;  // no heat grid, adjoint or sampler flags
+    if (!(c->L > 0) || !(c->lambda1 > 0) || !(c->lambda2 > 0) || !(c->n1 > 0) || !(c->n2 > 0) ||
+        !(c->n3 > 0))
+        return SHG_ERR_INVALID_ARG;
+    for (int j = 0; j < 3; ++j)
+        if (!(b->w0[j] > 0) || b->p[j] < 0 || !(std::fabs(c->walkoff[j]) < 1.5))
+            return SHG_ERR_INVALID_ARG;
+    if (!(b->p[0] + b->p[1] + b->p[2] > 0)) return SHG_ERR_INVALID_ARG;
+    // the shared state (grid checks, phase and twiddle tables, map machinery,
+    // streams and events) of an SHG plan with the same grid, crystal length,
+    // phase and temperature coefficients; the fields and K-space tables are
+    // then replaced by three-wave ones
+    shg_crystal_t c2{};
+    c2.L = c->L;
+    c2.lambda_f = c->lambda1;
+    c2.n_f = c->n1;
+    c2.n_sh = c->n3;
+    c2.d_eff = c->d_eff;
+    c2.dk0 = c->dk0;
+    c2.ddk_dT = c->ddk_dT;
+    c2.dn_dT = c->dn_dT;
+    c2.kappa_th = 1.0;
+    c2.wx = c2.wy = 1.0;
+    shg_beams_t b2{};
+    b2.p1 = b->p[0] + b->p[1] + b->p[2];
+    b2.w0 = b->w0[0];
+    b2.z_focus = b->z_focus[0];
+    b2.t_oven_offset = b->t_oven_offset;
+    b2.undepleted = b->undepleted;
+    shg_plan_t* p = nullptr;
+    shg_status_t st = shg_plan_create(grid, &c2, &b2, flags | SHG_FLAG_NODE_SAMPLER, &p);
+    if (st != SHG_OK) return st;
+    auto fail = [&](shg_status_t s2) {
+        shg_plan_destroy(p);
+        return s2;
+    };
+    const size_t npts = size_t(grid->nx) * grid->ny;
+    cudaFree(p->field);
+    cudaFree(p->px);
+    cudaFree(p->py);
+    p->field = p->px = p->py = nullptr;
+    if (p->cmap_dev) cudaFree(p->cmap_dev);  // the tensor map described the two-field buffer
+    p->cmap_dev = nullptr;
+    p->has_cmap = false;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->field, 3 * npts * p->csize)) != cudaSuccess ||
+        (e = cudaMemset(p->field, 0, 3 * npts * p->csize)) != cudaSuccess ||
+        (e = cudaMalloc(&p->px, size_t(3) * grid->nx * 16)) != cudaSuccess ||
+        (e = cudaMalloc(&p->py, size_t(3) * grid->ny * 16)) != cudaSuccess)
+        return fail(cuda_fail(e, "three-wave buffers"));
+    if ((st = three_wave_alloc(p, c, b)) != SHG_OK || (st = build_prop_tables3(p, p->px, p->py)) != SHG_OK ||
+        (st = upload_desc(p)) != SHG_OK)
+        return fail(st);
+    *out = p;
+    return SHG_OK;
+}
+
 shg_status_t shg_set_monitor(shg_plan_t* p, int every) {
-    if (!p || every < 0) return SHG_ERR_INVALID_ARG;
+    if (!p || every < 0 || p->w3) return SHG_ERR_INVALID_ARG;
     shg_status_t st = quiesce(p);
     if (st != SHG_OK) return st;
     if (p->mon) {
@@ -1093,7 +1218,7 @@ shg_status_t shg_set_monitor(shg_plan_t* p, int every) {
 }
 
 shg_status_t shg_set_phase_model(shg_plan_t* p, const shg_qpm_t* m) {
-    if (!p) return SHG_ERR_INVALID_ARG;
+    if (!p || p->w3) return SHG_ERR_INVALID_ARG;
     DkModel d{};
     if (m) {
         const double v[] = {m->t_oven, m->lambda25, m->a_lambda, m->b_lambda, m->n_f[0], m->n_f[1],
@@ -1368,6 +1493,8 @@ void forget_plan_batches(shg_plan* p) {
 extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double* eta_host_out,
                                          shg_stream_t stream) {
     if (!plans || n <= 0 || !distinct_plans(plans, n)) return SHG_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (plans[i]->w3) return SHG_ERR_INVALID_ARG;  // three-wave plans propagate one by one
     std::vector<shg_plan*> key(plans, plans + n);
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     std::lock_guard<std::mutex> lk(g_batch_mu);
@@ -1473,6 +1600,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
     if (!plans || n <= 0 || nsteps <= 0 || !out || !ngroups || max_groups <= 0 ||
         !distinct_plans(plans, n))
         return SHG_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i)
+        if (plans[i]->w3) return SHG_ERR_INVALID_ARG;
     std::vector<shg_plan*> key(plans, plans + n);
     for (auto p : key)
         if (!p) return SHG_ERR_INVALID_ARG;

@@ -112,8 +112,7 @@ SHG_HD double phase_integrand(const DkModel& m, double dT) {
 // Launch-variant bit of the row pass: read the per-point temperature table.
 constexpr int kRowUmap = 8;  // above every flavour number (0-4)
 // Launch bit of the row pass (with kRowUmap only): no instance of the group
-// deposits heat or monitors its power, so the kernel is instantiated without
-// that code at z_s.
+// monitors its power, so the kernel is instantiated without that code.
 constexpr int kRowLean = 16;
 
 template <class R> struct InstDesc {

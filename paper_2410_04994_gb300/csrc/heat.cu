@@ -197,7 +197,10 @@ extern "C" shg_status_t shg_set_heat_boundary(shg_plan_t* p, const int* kinds, c
         p->heat_h[k] = kinds[k] == SHG_FACE_CONVECTIVE ? (h ? h[k] : 0.0) : 0.0;
     }
     p->heat_tinf = t_inf;
-    free_heat_direct(p);  // rebuilt for the new boundary at the next direct solve
+    // eigenbases of the direct solve for the new boundary (host Jacobi
+    // rotations: tens of milliseconds at 128 nodes per axis)
+    shg_status_t r = heat_direct_setup(p);
+    if (r != SHG_OK) return r;
     // the previous solution belongs to the old boundary (nodes now held at the
     // oven may be non-zero): the next solve starts from dT = 0
     const size_t nh = size_t(p->g.hx) * p->g.hy * p->g.hz;

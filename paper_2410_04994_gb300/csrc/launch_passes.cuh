@@ -66,7 +66,7 @@ cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, cons
     using G = RowGeom<R, N, V, NTH>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
     return launch_pdl(k_row_pass<R, N, V, UM, NTH, ZS>, grid, dim3(NTH),
-                      row_smem<R, N, V, UM, NTH>(ZS ? hx : 0),
+                      row_smem<R, N, V, UM, NTH>(hx),
                       st, static_cast<const InstDesc<R>*>(descs), ny, nz, s,
                       static_cast<const pt<R>*>(tw));
 }

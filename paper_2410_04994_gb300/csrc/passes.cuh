@@ -120,8 +120,9 @@ SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, i
 // point samples the node table bilinearly.  The heat deposit at z_s (THERMAL plans) is binned
 // per CTA in shared memory and added to the heat grid with one
 // double-precision atomic per touched node.
-// ZS = false: the instantiation for groups without heat deposits or power
-// monitors (the code at z_s between the two half steps is compiled out).
+// ZS = false: the instantiation for groups without power monitors (the
+// monitor's code at z_s is compiled out; the heat deposit stays a runtime
+// branch: removing it too made the compiler spill in the 256-point kernel).
 template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
 __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
@@ -162,7 +163,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             }
         }
     }
-    const bool dep = ZS && descs[blockIdx.y].Q != nullptr;
+    const bool dep = descs[blockIdx.y].Q != nullptr;
     float4* slots = reinterpret_cast<float4*>(smem_raw + G::fields);
     const float4* umap4 = reinterpret_cast<const float4*>(descs[blockIdx.y].umap);
     float* bins = reinterpret_cast<float*>(pS + 2 * NX);

@@ -44,13 +44,13 @@ static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int n
 
 // passes_f32_lean.cu: the table-path rows without the code at z_s.
 cudaError_t row_f32_lean(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
-                         const void* tw, cudaStream_t st);
+                         const void* tw, int hx, cudaStream_t st);
 cudaError_t attr_f32_lean();
 
 cudaError_t row_f32(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
                     const void* tw, int hx, cudaStream_t st) {
     if ((v & kRowUmap) && (v & kRowLean))
-        return row_f32_lean(nx, v & ~(kRowUmap | kRowLean), descs, ninst, ny, nz, s, tw, st);
+        return row_f32_lean(nx, v & ~(kRowUmap | kRowLean), descs, ninst, ny, nz, s, tw, hx, st);
     v &= ~kRowLean;
     return (v & kRowUmap) ? row_f32_um<true>(nx, v & ~kRowUmap, descs, ninst, ny, nz, s, tw, hx, st)
                           : row_f32_um<false>(nx, v, descs, ninst, ny, nz, s, tw, hx, st);
@@ -149,7 +149,6 @@ cudaError_t attr_f32() {
 
 size_t row_smem_f32(int nx, int v, int hx) {
     const bool um = (v & kRowUmap) != 0;
-    if (um && (v & kRowLean)) hx = 0;  // no deposit bins
     v &= ~(kRowUmap | kRowLean);
     if (v == 3) {
         switch (nx) {

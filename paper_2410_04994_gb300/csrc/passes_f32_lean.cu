@@ -1,7 +1,6 @@
 // Single-precision row passes on the per-point temperature table without the
-// code at z_s (heat deposits, power monitor): the instantiations for groups
-// that use neither, in a translation unit of their own so that the library
-// builds in parallel.
+// power monitor's code: the instantiations for groups without a monitor, in
+// a translation unit of their own so that the library builds in parallel.
 #include "launch_passes.cuh"
 #include "plan.h"
 
@@ -11,13 +10,13 @@ namespace shg {
 #define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
 
 cudaError_t row_f32_lean(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
-                         const void* tw, cudaStream_t st) {
+                         const void* tw, int hx, cudaStream_t st) {
     if (v == 3 || v == 4) {
         switch (nx) {
 #define X(n)                                                                                    \
     case n:                                                                                     \
-        return v == 3 ? row_launch<float, n, 0, true, 128, false>(descs, ninst, ny, nz, s, tw, 0, st) \
-                      : row_launch<float, n, 0, true, 64, false>(descs, ninst, ny, nz, s, tw, 0, st);
+        return v == 3 ? row_launch<float, n, 0, true, 128, false>(descs, ninst, ny, nz, s, tw, hx, st) \
+                      : row_launch<float, n, 0, true, 64, false>(descs, ninst, ny, nz, s, tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
@@ -25,14 +24,14 @@ cudaError_t row_f32_lean(int nx, int v, const void* descs, int ninst, int ny, in
     if (v == 1) {
         switch (nx) {
 #define X(n) \
-    case n: return row_launch<float, n, 1, true, kPassThreads, false>(descs, ninst, ny, nz, s, tw, 0, st);
+    case n: return row_launch<float, n, 1, true, kPassThreads, false>(descs, ninst, ny, nz, s, tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
     }
     switch (nx) {
 #define X(n) \
-    case n: return row_launch<float, n, 0, true, kPassThreads, false>(descs, ninst, ny, nz, s, tw, 0, st);
+    case n: return row_launch<float, n, 0, true, kPassThreads, false>(descs, ninst, ny, nz, s, tw, hx, st);
         SHG_F32_SIZES(X)
 #undef X
     }

@@ -32,6 +32,7 @@ struct InitDesc {
 struct Adjoint;     // adjoint.cu
 struct Heat;        // heat.cu
 struct HeatDirect;  // heat_direct.cu
+struct ThreeWave;   // threewave.cu
 
 }  // namespace shg
 
@@ -89,6 +90,7 @@ struct shg_plan {
     int heat_method = 0;                     // SHG_HEAT_DIRECT or SHG_HEAT_SOR
     DkModel dkm{};                           // Eq. (4) model (dkm.on) or the linearised one
     shg::HeatDirect* hdir = nullptr;         // eigenbases and work buffers of the direct solve
+    shg::ThreeWave* w3 = nullptr;            // three-wave plans: their crystal, beams, descriptor
 
     // tensor map of `field` for the TMA column pass (FP32, supported lengths)
     CUtensorMap cmap;
@@ -200,6 +202,15 @@ bool cluster_path(const std::vector<shg_plan*>& plans);
 int cluster_size(int n);
 cudaError_t launch_cluster(int n, const void* descs, int ninst, int nz, const void* tw,
                            cudaStream_t st);
+
+// Three-wave plans (threewave.cu).
+shg_status_t three_wave_alloc(shg_plan* p, const shg_crystal3_t* c, const shg_beams3_t* b);
+shg_status_t build_prop_tables3(shg_plan* p, void* px, void* py);
+shg_status_t upload_desc3(shg_plan* p);
+shg_status_t enqueue_forward3(shg_plan* p, cudaStream_t st);
+shg_status_t three_wave_powers(shg_plan* p, double out[3]);
+double three_wave_input_power(const shg_plan* p);
+void free_three_wave(shg_plan* p);
 
 // Lifetime hooks: drop cached batch graphs / adjoint buffers of a plan.
 void forget_plan_batches(shg_plan* p);
