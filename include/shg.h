@@ -106,8 +106,8 @@ enum {
 
 typedef struct shg_plan shg_plan_t;
 
-/* Create a plan (Sec. 4: the Efields / Tfield / PhaseMatching state of the
- * paper as one object).  Validates the grid, allocates the device state and
+/* Create a plan (Sec. 4: the field, temperature and phase-matching state of
+ * the paper's solver as one object).  Validates the grid, allocates the device state and
  * the twiddle / propagator / phase tables (FP64-computed, rounded once).
  * SHG_ERR_INVALID_ARG for 1 <= nz <= 2^26 violated, for any non-finite
  * double of the three structs, or for a non-positive length, wavelength,

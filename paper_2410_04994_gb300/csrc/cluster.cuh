@@ -42,6 +42,7 @@ template <int N, int K> struct ClusterGeom {
     static constexpr int S = padded_len<float>(N, T < Bank<float>::W ? T : 1);
     static constexpr int PAIRS = R * N / 2;  // point pairs per CTA
     static_assert(PAIRS % NT == 0, "whole pairs per thread");
+    static_assert(2 * R * N == E * NT, "each gather moves E points per thread");
     static constexpr size_t buf = size_t(2) * R * S * sizeof(float2);  // one of Rbuf, Cbuf
     static constexpr size_t smem = 2 * buf + size_t(5) * N * sizeof(float4);
 };
@@ -55,7 +56,7 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
     cg::cluster_group cluster = cg::this_cluster();
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<float> dsh;
-    __shared__ StageZ<float> zsh[5];
+    __shared__ StageZ<float> zsh[2][5];  // stage data of step s in zsh[s & 1]
     float2* Rbuf = reinterpret_cast<float2*>(smem_raw);              // [2][R][S] rows
     float2* Cbuf = reinterpret_cast<float2*>(smem_raw + G::buf);     // [2][R][S] columns
     float4* twS = reinterpret_cast<float4*>(smem_raw + 2 * G::buf);  // [N]
@@ -77,32 +78,64 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
     __syncthreads();
     const InstDesc<float>& d = dsh;
     const bool thermal = d.ttab != nullptr;   // the launcher admits only the per-point table then
-    const float4* umap4 = reinterpret_cast<const float4*>(d.umap);
+    const float4* __restrict__ umap4 = reinterpret_cast<const float4*>(d.umap);
     const float h = 0.5f * d.dz;
     // transform group of this thread
     const int g = tid / T, t = tid - g * T;
-    const int gf = g / R, gr = g - gf * R;
-#pragma unroll 1
-    for (int s = 0; s <= nz; ++s) {
+    const int gf = g / R;
+    // Stage data of step s (5 stage points) into zsh[s & 1].
+    auto stage = [&](int s) {
         if (tid < 5) {
             const int q = 4 * s - 2 + tid;
-            zsh[tid] = stage_z(d, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
+            zsh[s & 1][tid] = stage_z(d, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
-        __syncthreads();
-        const int lmin = zsh[0].l;
-        // ---- nonlinear half steps on this CTA's rows (two points per thread pass)
+    };
+    // Per-point table entries of this thread's pairs for the map layers that
+    // step s's stage points fall between (at most three: the launcher admits
+    // the table path only when one step spans less than one layer), loaded
+    // into registers one step ahead, so that their latency is hidden behind
+    // the transforms and cluster barriers of the step before.  Layers past
+    // the span are not read.
+    constexpr int PPT = G::PAIRS / NT;
+    float4 tv[PPT][3];
+#pragma unroll
+    for (int i = 0; i < PPT; ++i) tv[i][0] = tv[i][1] = tv[i][2] = make_float4(0.f, 0.f, 0.f, 0.f);
+    auto load_tables = [&](int s) {
+        if (!thermal) return;
+        const int q0 = 4 * s - 2, q4 = 4 * s + 2;
+        const int l0 = stage_z(d, q0 < 0 ? 0 : q0).l;
+        const int l4 = stage_z(d, q4 > 4 * nz ? 4 * nz : q4).l;
+        const int span = l4 + 2 - l0;
+        if (span > 3 && tid == 0 && d.status) atomicExch(d.status, int(SHG_ERR_STATE));
+        const int nl = span < 3 ? span : 3;
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
+            const int p = tid + NT * i;
+            const int r = p / (N / 2), j = p - r * (N / 2);
+            const float4* src = umap4 + (size_t(l0) * N + (y0 + r)) * (N / 2) + j;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                if (k < nl) tv[i][k] = __ldg(src + size_t(k) * N * (N / 2));
+        }
+    };
+    stage(0);
+    load_tables(0);
+    __syncthreads();
 #pragma unroll 1
-        for (int i = 0; i < G::PAIRS / NT; ++i) {
+    for (int s = 0; s <= nz; ++s) {
+        const StageZ<float>* zs = zsh[s & 1];
+        const int lmin = zs[0].l;
+        // ---- nonlinear half steps on this CTA's rows (two points per thread pass)
+#pragma unroll
+        for (int i = 0; i < PPT; ++i) {
             const int p = tid + NT * i;
             const int r = p / (N / 2), j = p - r * (N / 2), x0 = 2 * j;
             float2* rF = Rbuf + r * S;
             float2* rS = Rbuf + (R + r) * S;
             float2 aF0 = rF[pidx<float>(x0)], aF1 = rF[pidx<float>(x0 + 1)];
             float2 aS0 = rS[pidx<float>(x0)], aS1 = rS[pidx<float>(x0 + 1)];
-            const PairSampler ps{thermal ? umap4 + (size_t(lmin) * N + (y0 + r)) * (N / 2) + j
-                                         : nullptr,
-                                 N * (N / 2), lmin};
-            auto cq = [&](int q) { return coef2_at(d, zsh[q], thermal, ps); };
+            const RegPairSampler ps{tv[i][0], tv[i][1], tv[i][2], lmin};
+            auto cq = [&](int q) { return coef2_at(d, zs[q], thermal, ps); };
             Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, Sx{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
             const Coef2 z2 = cq(2);
             if (s > 0) {
@@ -124,6 +157,12 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
             rS[pidx<float>(x0)] = aS0;
             rS[pidx<float>(x0 + 1)] = aS1;
         }
+        // the next step's stage data and table entries, in flight during the
+        // transforms (zsh[(s + 1) & 1] was last read in step s - 1)
+        if (s < nz) {
+            stage(s + 1);
+            load_tables(s + 1);
+        }
         __syncthreads();
         if (s == nz) break;  // the last row pass is N_b alone
         // ---- Lx on each of this CTA's rows (group g: field gf, row gr)
@@ -138,11 +177,25 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
             for (int m = 0; m < E; ++m) row[pidx<float>(t + T * m)] = v[m];
         }
         cluster.sync();
-        // ---- column gather: Cbuf[f][c][y] = row y of CTA y / R, column cid R + c
-        for (int e = tid; e < 2 * R * N; e += NT) {
-            const int c = e % R, y = (e / R) % N, f = e / (R * N);
-            const float2* src = cluster.map_shared_rank(Rbuf, y / R);
-            Cbuf[(f * R + c) * S + pidx<float>(y)] = src[(f * R + y % R) * S + pidx<float>(y0 + c)];
+        // ---- column gather: Cbuf[f][c][y] = row y of CTA y / R, column cid R + c.
+        // All E remote loads of a thread are issued before its local stores
+        // (a store could alias a remote load for all the compiler knows, which
+        // would serialise the loads' latencies).
+        {
+            float2 gv[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = tid + NT * m;
+                const int c = e % R, y = (e / R) % N, f = e / (R * N);
+                const float2* src = cluster.map_shared_rank(Rbuf, y / R);
+                gv[m] = src[(f * R + y % R) * S + pidx<float>(y0 + c)];
+            }
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = tid + NT * m;
+                const int c = e % R, y = (e / R) % N, f = e / (R * N);
+                Cbuf[(f * R + c) * S + pidx<float>(y)] = gv[m];
+            }
         }
         __syncthreads();
         // ---- Ly on each of this CTA's columns (group g: field gf, column gr)
@@ -158,10 +211,21 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
         }
         cluster.sync();
         // ---- row gather: Rbuf[f][r][x] = column x of CTA x / R, row y0 + r
-        for (int e = tid; e < 2 * R * N; e += NT) {
-            const int r = e % R, x = (e / R) % N, f = e / (R * N);
-            const float2* src = cluster.map_shared_rank(Cbuf, x / R);
-            Rbuf[(f * R + r) * S + pidx<float>(x)] = src[(f * R + x % R) * S + pidx<float>(y0 + r)];
+        {
+            float2 gv[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = tid + NT * m;
+                const int r = e % R, x = (e / R) % N, f = e / (R * N);
+                const float2* src = cluster.map_shared_rank(Cbuf, x / R);
+                gv[m] = src[(f * R + x % R) * S + pidx<float>(y0 + r)];
+            }
+#pragma unroll
+            for (int m = 0; m < E; ++m) {
+                const int e = tid + NT * m;
+                const int r = e % R, x = (e / R) % N, f = e / (R * N);
+                Rbuf[(f * R + r) * S + pidx<float>(x)] = gv[m];
+            }
         }
         __syncthreads();
     }

@@ -13,6 +13,8 @@
 // Each pass reads and writes both fields once: 2 x (8+8) B of complex64 in
 // and out per grid point and pass.
 #pragma once
+#include <type_traits>
+
 #include "common.cuh"
 #include "fft.cuh"
 #include "nonlinear.cuh"
@@ -234,14 +236,16 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     // The same for two points at once in packed FP32 arithmetic, with the
     // stage coefficients of stage point q from cq(q) (the body exists for
     // FP32 only).
-    auto pair = [&](int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1, auto&& cq) {
+    auto pair_t = [&](auto tpa, int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1,
+                      auto&& cq) {
+        constexpr bool TPA = decltype(tpa)::value;
         if constexpr (sizeof(R) == 4) {
             const Coef2 z2 = cq(2);  // z_s, shared by both halves
             Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, S{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
             if (s > 0) {
                 const Coef2 c0 = cq(0);
                 const Coef2 cm = cq(1);
-                rk4_2(dsh, F, S, c0, cm, z2, h);
+                rk4_2<TPA>(dsh, F, S, c0, cm, z2, h);
             }
             if ((l_dep >= 0 && j_dep >= 0) || mon) {
                 up2(F.r, aF0.x, aF1.x);
@@ -260,13 +264,20 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             if (s < nz) {
                 const Coef2 cm = cq(3);
                 const Coef2 c1 = cq(4);
-                rk4_2(dsh, F, S, z2, cm, c1, h);
+                rk4_2<TPA>(dsh, F, S, z2, cm, c1, h);
             }
             up2(F.r, aF0.x, aF1.x);
             up2(F.i, aF0.y, aF1.y);
             up2(S.r, aS0.x, aS1.x);
             up2(S.i, aS0.y, aS1.y);
         }
+    };
+    // the pump-TPA-free form where bF = 0 (uniform over the CTA's instance)
+    auto pair = [&](int xa, int xb, auto& aF0, auto& aS0, auto& aF1, auto& aS1, auto&& cq) {
+        if (dsh.bF != R(0))
+            pair_t(std::true_type{}, xa, xb, aF0, aS0, aF1, aS1, cq);
+        else
+            pair_t(std::false_type{}, xa, xb, aF0, aS0, aF1, aS1, cq);
     };
     if (active) {
         // two adjacent points per iteration: in FP32 they advance together in

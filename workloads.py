@@ -316,8 +316,9 @@ def dfg_case(n: int = 64, nz: int = 200, **kw) -> ThreeWave:
     return w.with_(name=f"dfg_{n}x{n}_nz{nz}")
 
 
-# Oven arrangements of Sec. 4.2 (Tfield::setOvenSurrounded / setBottomOvens):
-# the faces held at the oven temperature, the rest cooled by convection.
+# Oven arrangements of Sec. 4.2 (the crystal surrounded by the oven, or an
+# oven under one face): the faces held at the oven temperature, the rest
+# cooled by convection.
 OVENS = {
     "all": ("D",) * 6,
     "surrounded": ("D", "D", "D", "D", "C", "C"),   # side faces in the oven, end facets in air
