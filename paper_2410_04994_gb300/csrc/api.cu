@@ -374,7 +374,7 @@ static void save_tune_decision(bool fp64, int n, int pass, int v) {
 
 static int forced_variant() {
     const char* f = getenv("SHG_FFT_VARIANT");
-    return (f && f[0] >= '0' && f[0] <= '4' && f[1] == 0) ? f[0] - '0' : -1;
+    return (f && f[0] >= '0' && f[0] <= '5' && f[1] == 0) ? f[0] - '0' : -1;
 }
 
 static bool p_fp32(const std::vector<shg_plan*>& plans) {
@@ -402,7 +402,7 @@ static_assert(kRowUmap > 4 && kRowLean > 4 && kRowLean != kRowUmap,
 
 // Candidate flavours of a pass for a length: the default shape, the
 // alternative shape, the default shape in 128-thread CTAs and (column pass)
-// the TMA-staged kernel.
+// the TMA-staged kernel and the default shape in 512-thread CTAs.
 static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     std::vector<int> c{0};
     if (has_fft_variant(fp64, n)) c.push_back(1);
@@ -411,6 +411,7 @@ static std::vector<int> candidates(bool fp64, int n, int pass, bool tmaps) {
     // alone, but whole single-instance propagations (graph, programmatic
     // launches) measured slower with it; SHG_FFT_VARIANT=4 still selects it
     if (has_col_small(fp64, n)) c.push_back(3);
+    if (pass == 1 && has_col_wide(fp64, n)) c.push_back(5);
     return c;
 }
 
@@ -427,6 +428,7 @@ static int tune_key(int pass, int row_bits, int ninst) {
 static int supported_flavour(bool fp64, int n, int pass, int f) {
     if (f == 1 && !has_fft_variant(fp64, n)) return 0;
     if (f == 2 && pass == 0) return 0;
+    if (f == 5) return (pass == 1 && has_col_wide(fp64, n)) ? 5 : 0;
     if (f >= 3 && !has_col_small(fp64, n)) return 0;
     return f;
 }

@@ -12,6 +12,7 @@ cudaError_t col_f64(int, int, const void*, int, int, const void*, cudaStream_t, 
 int col_tma_tile_f32(int);
 bool has_variant_f32(int);
 bool has_col_small_f32(int);
+bool has_col_wide_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
 
@@ -19,6 +20,7 @@ thread_local bool pdl_enabled = false;
 
 bool has_fft_variant(bool fp64, int n) { return !fp64 && has_variant_f32(n); }
 bool has_col_small(bool fp64, int n) { return !fp64 && has_col_small_f32(n); }
+bool has_col_wide(bool fp64, int n) { return !fp64 && has_col_wide_f32(n); }
 
 cudaError_t launch_row(bool fp64, int nx, const void* descs, int ninst, int ny, int nz, int s,
                        const void* tw, int hx, cudaStream_t st, int variant) {

@@ -374,14 +374,16 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     }
 }
 
-// Column pass C(s).  grid = (ceil(nx / TILE), instances); block = NTH (256,
-// or 128 for half as many columns per CTA and twice as many resident CTAs).
+// Column pass C(s).  grid = (ceil(nx / TILE), instances); block = NTH (256;
+// 128 or 64 for fewer columns per CTA and more resident CTAs; 512 at the
+// lengths 512 and 1024 for twice the columns per CTA, so that each row
+// segment a warp reads is a whole 32-byte sector).
 // The TILE columns of both fields are staged into padded shared buffers with
 // cp.async, one commit group per field, transformed field by field (the
 // second field is still landing while the first is transformed), and written
 // back from registers.
 template <class R, int NY, int V = 0, int NTH = kPassThreads>
-__global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
+__global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
     k_col_pass(const InstDesc<R>* __restrict__ descs, int nx, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
     using G = ColGeom<R, NY, V, NTH>;

@@ -8,11 +8,14 @@ namespace shg {
 #define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 #define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
 #define SHG_F32_TMA_SIZES(X) X(32) X(64) X(128) X(256) X(512) X(1024)
+#define SHG_F32_WIDE_SIZES(X) X(512) X(1024)
 
 bool has_variant_f32(int n) { return n == 64 || n == 128 || n == 256; }
 bool has_col_small_f32(int n) { return n == 64 || n == 128 || n == 256; }
+bool has_col_wide_f32(int n) { return n == 512 || n == 1024; }
 
-// v: flavour (0, 1: FFT shape; 3, 4: shape 0 in 128- or 64-thread CTAs), plus kRowUmap
+// v: flavour (0, 1: FFT shape; 3, 4: shape 0 in 128- or 64-thread CTAs; 5, column
+// pass only: shape 0 in 512-thread CTAs at 512 and 1024), plus kRowUmap
 // to read the per-point temperature table.
 template <bool UM>
 static cudaError_t row_f32_um(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
@@ -72,6 +75,13 @@ cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const v
         switch (ny) {
 #define X(n) case n: return col_tma_launch<n>(tmaps, descs, ninst, nx, tw, st);
             SHG_F32_TMA_SIZES(X)
+#undef X
+        }
+    }
+    if (v == 5) {
+        switch (ny) {
+#define X(n) case n: return col_launch<float, n, 0, 512>(descs, ninst, nx, tw, st);
+            SHG_F32_WIDE_SIZES(X)
 #undef X
         }
     }
@@ -142,6 +152,10 @@ cudaError_t attr_f32() {
 #define X(n) \
     if (e == cudaSuccess) e = col_tma_attr<n>();
     SHG_F32_TMA_SIZES(X)
+#undef X
+#define X(n) \
+    if (e == cudaSuccess) e = col_attr<float, n, 0, 512>();
+    SHG_F32_WIDE_SIZES(X)
 #undef X
     if (e == cudaSuccess) e = attr_f32_lean();
     return e;

@@ -140,6 +140,7 @@ cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, 
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
 bool has_col_small(bool fp64, int n);  // row and column passes in 128/64-thread CTAs (flavours 3, 4)
+bool has_col_wide(bool fp64, int n);   // the column pass in 512-thread CTAs (flavour 5)
 // Kernel flavour picked for (precision, length, pass, row-pass table bit) by the autotuner:
 // measured once per process on the first group that uses it, unless
 // SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.

@@ -108,17 +108,31 @@ def test_undepleted_fp32_matches_oracle():
     _compare(w, ETA_TOL, FIELD_TOL)
 
 
-@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4"])
-@pytest.mark.parametrize("n", [32, 64, 128, 256, 1024])
+@pytest.mark.parametrize("variant", ["0", "1", "2", "3", "4", "5"])
+@pytest.mark.parametrize("n", [32, 64, 128, 256, 512, 1024])
 def test_every_kernel_flavour_of_the_autotuner(n, variant, monkeypatch):
     """Each kernel flavour the autotuner can pick, forced through
     SHG_FFT_VARIANT (0/1: the two FFT shapes with cp.async staging, 2: the
-    TMA-staged column pass, 3/4: both passes in 128-/64-thread CTAs), matches
-    the oracle on its own (single plans kept on the streaming passes)."""
+    TMA-staged column pass, 3/4: both passes in 128-/64-thread CTAs, 5: the
+    column pass in 512-thread CTAs at 512 and 1024), matches the oracle on its
+    own (single plans kept on the streaming passes).  A flavour a length does
+    not have falls back to flavour 0."""
     monkeypatch.setenv("SHG_FFT_VARIANT", variant)
     monkeypatch.setenv("SHG_CLUSTER", "0")
-    w = W.depleted_absorbing(n=n, nz=6 if n < 1024 else 1, tgrid=(9, 7, 5), p1=400.0)
+    w = W.depleted_absorbing(n=n, nz=6 if n < 512 else (2 if n == 512 else 1), tgrid=(9, 7, 5),
+                             p1=400.0)
     _compare(w, ETA_TOL, FIELD_TOL)
+
+
+def test_wide_column_flavour_over_several_steps_and_rectangular(monkeypatch):
+    """Flavour 5 (4 columns per CTA at 1024, 8 at 512) over several steps, with
+    nx != ny, so that a CTA's tile is not the whole row (ny = 1024 columns of
+    length 1024, nx = 256 columns per row for ny = 512)."""
+    monkeypatch.setenv("SHG_FFT_VARIANT", "5")
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+    w = W.depleted_absorbing(n=256, nz=8, tgrid=(9, 7, 5), p1=400.0)
+    _compare(w.with_(ny=512, ly=2 * w.ly), ETA_TOL, FIELD_TOL)
+    _compare(w.with_(nx=128, lx=w.lx / 2, ny=1024, ly=4 * w.ly, nz=3), ETA_TOL, FIELD_TOL)
 
 
 def test_bounded_wait_reports_timeout_and_context_survives(monkeypatch):
