@@ -5,21 +5,19 @@
 //
 // The K CTAs of a cluster split the N x N grid of both fields: CTA c holds
 // rows [cR, cR + R) in its row buffer and columns [cR, cR + R) in its column
-// buffer (R = N / K).  Step s is the same pair of fused passes as the
-// streaming kernels (passes.cuh), with the exchanges through distributed
-// shared memory:
-//   row phase (local)        N_b(s-1), N_a(s) on this CTA's rows, then Lx
-//   cluster barrier
-//   column gather            every CTA reads its columns out of the other
-//                            CTAs' row buffers
-//   column phase (local)     Ly on this CTA's columns
-//   cluster barrier
-//   row gather               every CTA reads its rows out of the other CTAs'
-//                            column buffers
-// A CTA writes its own row buffer only in the row gather, after the second
-// barrier, when every other CTA has finished reading it; it writes its column
-// buffer only in the column gather, after the first barrier, when every other
-// CTA has finished the previous row gather.  So two barriers per step suffice.
+// buffer (R = N / K).  Step s applies N_b(s-1), N_a(s) (pointwise, in
+// whatever layout holds the fields) and L = Lx Ly.  Lx and Ly are diagonal
+// in separable spectra and commute exactly, so their order alternates and
+// one transpose per step suffices:
+//   s even (rows):    RK4 on the rows, Lx, barrier, gather the columns, Ly
+//   s odd (columns):  RK4 on the columns, Ly, barrier, gather the rows, Lx
+// A gather reads the other CTAs' buffers through distributed shared memory.
+// One cluster barrier per step is enough: a CTA rewrites its row buffer (RK4,
+// Lx, or the row gather that fills it) only after a barrier that every other
+// CTA reached after its last read of that buffer (the column gather of the
+// step before, in which the other CTAs read it), and the same holds for the
+// column buffer.  A last barrier keeps every CTA resident until the final
+// gather has read it.
 // The barriers are the hardware cluster barrier (every CTA executes the same
 // sequence of them; there is no spin-wait).  The arithmetic per point is that
 // of the streaming passes: the packed-FP32 RK4 of nonlinear.cuh and the
@@ -90,13 +88,33 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
             zsh[s & 1][tid] = stage_z(d, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
     };
+    // The layout of step s: rows (s even: Rbuf[f][r][x], this CTA's rows
+    // y0 + r) or columns (s odd: Cbuf[f][c][y], this CTA's columns y0 + c).
+    // Pair p of this thread: in rows, the points (2j, 2j + 1) of row y0 + r;
+    // in columns, the columns (y0 + 2jj, y0 + 2jj + 1) of row y.  Either way
+    // the pair is one entry [l][row][pair] of the per-point table.
+    constexpr int PPT = G::PAIRS / NT;
+    auto pair_of = [&](bool rows_l, int p, float2*& e0, float2*& e1, int& row, int& jg) {
+        if (rows_l) {
+            const int r = p / (N / 2), j = p - r * (N / 2);
+            e0 = Rbuf + r * S + pidx<float>(2 * j);
+            e1 = Rbuf + r * S + pidx<float>(2 * j + 1);
+            row = y0 + r;
+            jg = j;
+        } else {
+            const int y = p / (R / 2), jj = p - y * (R / 2);
+            e0 = Cbuf + (2 * jj) * S + pidx<float>(y);
+            e1 = Cbuf + (2 * jj + 1) * S + pidx<float>(y);
+            row = y;
+            jg = y0 / 2 + jj;
+        }
+    };
     // Per-point table entries of this thread's pairs for the map layers that
     // step s's stage points fall between (at most three: the launcher admits
     // the table path only when one step spans less than one layer), loaded
     // into registers one step ahead, so that their latency is hidden behind
-    // the transforms and cluster barriers of the step before.  Layers past
+    // the transforms and the cluster barrier of the step before.  Layers past
     // the span are not read.
-    constexpr int PPT = G::PAIRS / NT;
     float4 tv[PPT][3];
 #pragma unroll
     for (int i = 0; i < PPT; ++i) tv[i][0] = tv[i][1] = tv[i][2] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -110,12 +128,62 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
         const int nl = span < 3 ? span : 3;
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-            const int p = tid + NT * i;
-            const int r = p / (N / 2), j = p - r * (N / 2);
-            const float4* src = umap4 + (size_t(l0) * N + (y0 + r)) * (N / 2) + j;
+            float2 *e0, *e1;
+            int row, jg;
+            pair_of((s & 1) == 0, tid + NT * i, e0, e1, row, jg);
+            const float4* src = umap4 + (size_t(l0) * N + row) * (N / 2) + jg;
 #pragma unroll
             for (int k = 0; k < 3; ++k)
                 if (k < nl) tv[i][k] = __ldg(src + size_t(k) * N * (N / 2));
+        }
+    };
+    // F^-1 diag(p) F along the rows (Lx, factors pxS) or the columns (Ly,
+    // pyS) held in buf: group g transforms field gf, row or column g - gf R.
+    auto transform = [&](float2* buf, const float4* fac) {
+        float2* line = buf + g * S;
+        float2 v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = line[pidx<float>(t + T * m)];
+        __syncthreads();  // the transform's exchanges reuse the buffer
+        fft_mul_ifft<float, N, V, N>(v, line, t, twS, fac + gf * N);
+#pragma unroll
+        for (int m = 0; m < E; ++m) line[pidx<float>(t + T * m)] = v[m];
+    };
+    // Transposes through distributed shared memory.  All E remote loads of a
+    // thread are issued before its local stores (a store could alias a remote
+    // load for all the compiler knows, which would serialise the loads).
+    // Columns: Cbuf[f][c][y] = element y0 + c of row y, held by CTA y / R.
+    auto gather_columns = [&] {
+        float2 gv[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = tid + NT * m;
+            const int c = e % R, y = (e / R) % N, f = e / (R * N);
+            const float2* src = cluster.map_shared_rank(Rbuf, y / R);
+            gv[m] = src[(f * R + y % R) * S + pidx<float>(y0 + c)];
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = tid + NT * m;
+            const int c = e % R, y = (e / R) % N, f = e / (R * N);
+            Cbuf[(f * R + c) * S + pidx<float>(y)] = gv[m];
+        }
+    };
+    // Rows: Rbuf[f][r][x] = element y0 + r of column x, held by CTA x / R.
+    auto gather_rows = [&] {
+        float2 gv[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = tid + NT * m;
+            const int r = e % R, x = (e / R) % N, f = e / (R * N);
+            const float2* src = cluster.map_shared_rank(Cbuf, x / R);
+            gv[m] = src[(f * R + x % R) * S + pidx<float>(y0 + r)];
+        }
+#pragma unroll
+        for (int m = 0; m < E; ++m) {
+            const int e = tid + NT * m;
+            const int r = e % R, x = (e / R) % N, f = e / (R * N);
+            Rbuf[(f * R + r) * S + pidx<float>(x)] = gv[m];
         }
     };
     stage(0);
@@ -123,17 +191,17 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
     __syncthreads();
 #pragma unroll 1
     for (int s = 0; s <= nz; ++s) {
+        const bool rows_l = (s & 1) == 0;
         const StageZ<float>* zs = zsh[s & 1];
         const int lmin = zs[0].l;
-        // ---- nonlinear half steps on this CTA's rows (two points per thread pass)
+        // ---- nonlinear half steps on this CTA's points (two per thread pass)
 #pragma unroll
         for (int i = 0; i < PPT; ++i) {
-            const int p = tid + NT * i;
-            const int r = p / (N / 2), j = p - r * (N / 2), x0 = 2 * j;
-            float2* rF = Rbuf + r * S;
-            float2* rS = Rbuf + (R + r) * S;
-            float2 aF0 = rF[pidx<float>(x0)], aF1 = rF[pidx<float>(x0 + 1)];
-            float2 aS0 = rS[pidx<float>(x0)], aS1 = rS[pidx<float>(x0 + 1)];
+            float2 *e0, *e1;
+            int row, jg;
+            pair_of(rows_l, tid + NT * i, e0, e1, row, jg);
+            float2 aF0 = e0[0], aF1 = e1[0];
+            float2 aS0 = e0[R * S], aS1 = e1[R * S];
             const RegPairSampler ps{tv[i][0], tv[i][1], tv[i][2], lmin};
             auto cq = [&](int q) { return coef2_at(d, zs[q], thermal, ps); };
             Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, Sx{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
@@ -152,10 +220,10 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
             up2(F.i, aF0.y, aF1.y);
             up2(Sx.r, aS0.x, aS1.x);
             up2(Sx.i, aS0.y, aS1.y);
-            rF[pidx<float>(x0)] = aF0;
-            rF[pidx<float>(x0 + 1)] = aF1;
-            rS[pidx<float>(x0)] = aS0;
-            rS[pidx<float>(x0 + 1)] = aS1;
+            e0[0] = aF0;
+            e1[0] = aF1;
+            e0[R * S] = aS0;
+            e1[R * S] = aS1;
         }
         // the next step's stage data and table entries, in flight during the
         // transforms (zsh[(s + 1) & 1] was last read in step s - 1)
@@ -165,76 +233,37 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
         }
         __syncthreads();
         if (s == nz) break;  // the last row pass is N_b alone
-        // ---- Lx on each of this CTA's rows (group g: field gf, row gr)
-        {
-            float2* row = Rbuf + g * S;
-            float2 v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = row[pidx<float>(t + T * m)];
-            __syncthreads();  // the transform's exchanges reuse the row buffer
-            fft_mul_ifft<float, N, V, N>(v, row, t, twS, pxS + gf * N);
-#pragma unroll
-            for (int m = 0; m < E; ++m) row[pidx<float>(t + T * m)] = v[m];
-        }
-        cluster.sync();
-        // ---- column gather: Cbuf[f][c][y] = row y of CTA y / R, column cid R + c.
-        // All E remote loads of a thread are issued before its local stores
-        // (a store could alias a remote load for all the compiler knows, which
-        // would serialise the loads' latencies).
-        {
-            float2 gv[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int e = tid + NT * m;
-                const int c = e % R, y = (e / R) % N, f = e / (R * N);
-                const float2* src = cluster.map_shared_rank(Rbuf, y / R);
-                gv[m] = src[(f * R + y % R) * S + pidx<float>(y0 + c)];
-            }
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int e = tid + NT * m;
-                const int c = e % R, y = (e / R) % N, f = e / (R * N);
-                Cbuf[(f * R + c) * S + pidx<float>(y)] = gv[m];
-            }
-        }
-        __syncthreads();
-        // ---- Ly on each of this CTA's columns (group g: field gf, column gr)
-        {
-            float2* col = Cbuf + g * S;
-            float2 v[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) v[m] = col[pidx<float>(t + T * m)];
+        // ---- L = Lx Ly, in the order that needs one transpose: the layout
+        // this step starts in, the barrier, the transpose, the other layout
+        if (rows_l) {
+            transform(Rbuf, pxS);
+            cluster.sync();
+            gather_columns();
             __syncthreads();
-            fft_mul_ifft<float, N, V, N>(v, col, t, twS, pyS + gf * N);
-#pragma unroll
-            for (int m = 0; m < E; ++m) col[pidx<float>(t + T * m)] = v[m];
+            transform(Cbuf, pyS);
+        } else {
+            transform(Cbuf, pyS);
+            cluster.sync();
+            gather_rows();
+            __syncthreads();
+            transform(Rbuf, pxS);
         }
-        cluster.sync();
-        // ---- row gather: Rbuf[f][r][x] = column x of CTA x / R, row y0 + r
-        {
-            float2 gv[E];
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int e = tid + NT * m;
-                const int r = e % R, x = (e / R) % N, f = e / (R * N);
-                const float2* src = cluster.map_shared_rank(Cbuf, x / R);
-                gv[m] = src[(f * R + x % R) * S + pidx<float>(y0 + r)];
-            }
-#pragma unroll
-            for (int m = 0; m < E; ++m) {
-                const int e = tid + NT * m;
-                const int r = e % R, x = (e / R) % N, f = e / (R * N);
-                Rbuf[(f * R + r) * S + pidx<float>(x)] = gv[m];
-            }
+        __syncthreads();  // the next step's pairs were transformed by other groups
+    }
+    // the final state to global memory, from the layout of step nz
+    if ((nz & 1) == 0) {
+        for (int e = tid; e < 2 * R * N; e += NT) {
+            const int x = e % N, r = (e / N) % R, f = e / (R * N);
+            d.field[(size_t(f) * N + y0 + r) * N + x] = Rbuf[(f * R + r) * S + pidx<float>(x)];
         }
-        __syncthreads();
+    } else {
+        for (int e = tid; e < 2 * R * N; e += NT) {
+            const int c = e % R, y = (e / R) % N, f = e / (R * N);
+            d.field[(size_t(f) * N + y) * N + y0 + c] = Cbuf[(f * R + c) * S + pidx<float>(y)];
+        }
     }
-    // the final state to global memory
-    for (int e = tid; e < 2 * R * N; e += NT) {
-        const int x = e % N, r = (e / N) % R, f = e / (R * N);
-        d.field[(size_t(f) * N + y0 + r) * N + x] = Rbuf[(f * R + r) * S + pidx<float>(x)];
-    }
-    // no CTA leaves while another may still read its buffers
+    // no CTA leaves while another may still read its buffers (the transpose
+    // of step nz - 1 has no barrier after it)
     cluster.sync();
 }
 
