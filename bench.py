@@ -57,6 +57,15 @@ def row_flops_per_point(n: int, thermal: bool) -> float:
     return rk4 + coef + fft
 
 
+def step_flops_per_point(n: int, thermal: bool) -> float:
+    """Algorithmic FP32 flops per grid point of one pass of the one-pass-per-
+    step schedule (passes_per_step == 1 in shg_pass_times): a whole step, the
+    nonlinear part of row_flops_per_point and the transforms along the pass's
+    axis twice (the second half of L(s-1) and the first half of L(s))."""
+    fft = 2 * (2 * 5 * math.log2(n) + 6)
+    return row_flops_per_point(n, thermal) + fft
+
+
 def col_bytes_per_point() -> float:
     """Column pass: read and write both complex64 fields once."""
     return 2 * 2 * 8.0
@@ -424,14 +433,19 @@ def _pass_roof(pkg, plan, w, stream, fp32_peak, fp64_peak, l2_gbs, hbm_gbs, ther
     npts = w.nx * w.ny
     fp64 = getattr(w, "precision", "f32") == "f64"
     peak = fp64_peak if fp64 else fp32_peak
-    row_flops = row_flops_per_point(w.nx, thermal) * npts
+    one = t.get("passes_per_step", 2) == 1
+    row_flops = (step_flops_per_point if one else row_flops_per_point)(w.nx, thermal) * npts
     col_bytes = col_bytes_per_point() * (2 if fp64 else 1) * npts
-    return {"row_ms": t["row_ms"], "col_ms": t["col_ms"],
+    out = {"row_ms": t["row_ms"], "col_ms": t["col_ms"], "passes_per_step": t.get("passes_per_step", 2),
             "row_alu_frac": row_flops / (t["row_ms"] * 1e-3) / (peak * 1e12),
             "row_alu_peak_tflops": peak,
             "col_gbs": col_bytes / (t["col_ms"] * 1e-3) / 1e9,
             "col_hbm_frac": col_bytes / (t["col_ms"] * 1e-3) / 1e9 / hbm_gbs,
             "col_l2_frac": col_bytes / (t["col_ms"] * 1e-3) / 1e9 / l2_gbs}
+    if one:
+        out["col_alu_frac"] = (step_flops_per_point(w.ny, thermal) * npts / (t["col_ms"] * 1e-3)
+                               / (peak * 1e12))
+    return out
 
 
 def time_configs(pkg, stream, mp, hbm_gbs):
@@ -585,8 +599,8 @@ def run_ours(args, rank, world):
     for w in insts:
         groups.setdefault((w.nx, w.ny, w.nz), 0)
         groups[(w.nx, w.ny, w.nz)] += 1
-    for (nx, ny, nz), _ in groups.items():
-        kernels_per_step += 2 + (nz + 1) + nz + 2
+    for (nx, ny, nz), _ in groups.items():   # two passes per step; recounted below from the
+        kernels_per_step += 2 + (nz + 1) + nz + 2   # schedule each group reports
 
     l2_flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -666,32 +680,56 @@ def run_ours(args, rank, world):
              for i, g in enumerate(runs[0])]
     for g in times:
         npts = g["nx"] * g["ny"] * g["instances"]
-        g["row_alu_frac"] = (row_flops_per_point(g["nx"], True) * npts / (g["row_ms"] * 1e-3)
-                             / (fp32_peak * 1e12))
+        one = g["passes_per_step"] == 1
+        g["row_alu_frac"] = ((step_flops_per_point if one else row_flops_per_point)(g["nx"], True)
+                             * npts / (g["row_ms"] * 1e-3) / (fp32_peak * 1e12))
+        if one:
+            g["col_alu_frac"] = (step_flops_per_point(g["ny"], True) * npts / (g["col_ms"] * 1e-3)
+                                 / (fp32_peak * 1e12))
         gbs = col_bytes_per_point() * npts / (g["col_ms"] * 1e-3) / 1e9
         g["col_gbs"] = gbs
         g["col_hbm_frac"] = gbs / pk["hbm_gbs"]
         g["col_l2_frac"] = gbs / mpk["l2_read_gbs"]
+    # launches per timed step: 2 init + 2 power + the passes of each group
+    # (nz + 1 on the one-pass-per-step schedule, 2 nz + 1 otherwise)
+    kernels_per_step = sum(4 + (args.nz + 1 if g["passes_per_step"] == 1 else 2 * args.nz + 1)
+                           for g in times)
+    if rank == 0:
+        result["gpu_launches"] = kernels_per_step * args.steps
     best = None
     for g in times:
         npts = g["nx"] * g["ny"] * g["instances"]
         nz = args.nz
-        for kind, t_ms, launches in (("row", g["row_ms"], nz + 1), ("col", g["col_ms"], nz)):
-            share = t_ms * launches
+        # launches per propagation: one pass per step (even s in the row
+        # layout, odd s in the column layout) or a row and a column pass
+        launches = ((nz // 2 + 1, (nz + 1) // 2) if g["passes_per_step"] == 1 else (nz + 1, nz))
+        for kind, t_ms, n_l in (("row", g["row_ms"], launches[0]), ("col", g["col_ms"], launches[1])):
+            share = t_ms * n_l
             if best is None or share > best[0]:
                 best = (share, kind, g, t_ms, npts)
     _, kind, g, t_ms, npts = best
-    if kind == "row":
-        flops = row_flops_per_point(g["nx"], True) * npts
-        achieved = flops / (t_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "kernel": f"k_row_pass<float,{g['nx']}>", "achieved": achieved,
-                "peak": fp32_peak, "unit": "TFLOP/s", "frac": achieved / fp32_peak,
+    alu_peak = {"peak": fp32_peak, "unit": "TFLOP/s",
                 "peak_source": "measured: FP32 FMA throughput kernel (shg_measure_peaks), "
                                "burst, timed alone like the pass",
                 "derived_peak_at_sm_max": N_SM * FP32_LANES_PER_SM * 2
-                * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12,
-                "algorithmic_per_point": row_flops_per_point(g["nx"], True),
-                "points_per_launch": npts, "launch_ms": t_ms, "traffic": None}
+                * pk.get("sm_max_mhz", 2070.0) * 1e6 / 1e12}
+    if g["passes_per_step"] == 1:
+        n = g["nx"] if kind == "row" else g["ny"]
+        per_point = step_flops_per_point(n, True)
+        achieved = per_point * npts / (t_ms * 1e-3) / 1e12
+        name = (f"k_row_pass<float,{n}> (row-layout step pass: Lx, N, Lx)" if kind == "row"
+                else f"k_col_step<{n}> (column-layout step pass: Ly, N, Ly)")
+        roof = dict({"bound": "alu", "kernel": name, "achieved": achieved,
+                     "frac": achieved / fp32_peak}, **alu_peak,
+                    algorithmic_per_point=per_point, points_per_launch=npts, launch_ms=t_ms,
+                    traffic=None)
+    elif kind == "row":
+        flops = row_flops_per_point(g["nx"], True) * npts
+        achieved = flops / (t_ms * 1e-3) / 1e12
+        roof = dict({"bound": "alu", "kernel": f"k_row_pass<float,{g['nx']}>", "achieved": achieved,
+                     "frac": achieved / fp32_peak}, **alu_peak,
+                    algorithmic_per_point=row_flops_per_point(g["nx"], True),
+                    points_per_launch=npts, launch_ms=t_ms, traffic=None)
     else:
         byts = col_bytes_per_point() * npts
         peak = pk["hbm_gbs"]

@@ -172,8 +172,13 @@ shg_status_t shg_set_fields(shg_plan_t *plan, const void *a_f_dev, const void *a
                             shg_stream_t stream);
 
 /* Propagate z = 0 -> L (Eq. 15 marched nz times, Fig. 2 "Compute CWEs"):
- * initial fields, 2 nz + 1 fused passes, and the FP64 power reductions.
- * Asynchronous on `stream`. */
+ * initial fields, the fused passes and the FP64 power reductions.  The
+ * passes are 2 nz + 1 (N with Lx, then Ly, per step), or nz + 1 when Lx and
+ * Ly alternate their order so that one pass per step suffices (FP32 plans
+ * with the per-point temperature table and no monitor, heat deposit or
+ * adjoint state; SHG_STEP_PASSES=0 turns that off); single FP32 64^2 and
+ * 128^2 plans run in one cluster-resident launch.  Asynchronous on
+ * `stream`. */
 shg_status_t shg_propagate(shg_plan_t *plan, shg_stream_t stream);
 
 /* eta = P_SH(L)/P1 and the powers P_F(L), P_SH(L) (W) of the last
@@ -313,9 +318,14 @@ shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
 /* Profiling aid.  Runs `nsteps` z-steps of the plans' row and column passes
  * eagerly (not from a graph) on `stream`, grouped by grid as in
  * shg_batch_submit, with a CUDA event pair around every launch.  For group g
- * (g < *ngroups <= max_groups) it writes out[4g..4g+3] = {nx, ny, average
- * row-pass ms, average column-pass ms} and inst_out[g] = instances in the
- * group.  A group not tuned yet in this process is tuned first (outside
+ * (g < *ngroups <= max_groups) it writes out[5g..5g+4] = {nx, ny, average
+ * row-pass ms, average column-pass ms, passes per step (1 or 2)} and
+ * inst_out[g] = instances in the
+ * group.  The passes timed are those the group's propagation runs: for a
+ * group on the one-pass-per-step schedule (FP32, per-point temperature
+ * table, no monitor, heat deposit or adjoint state; nz >= 3), the row-layout
+ * pass (Lx, N, Lx) and the column-layout pass (Ly, N, Ly); otherwise the
+ * row pass (N, Lx) and the column pass (Ly).  A group not tuned yet in this process is tuned first (outside
  * the event pairs).  The plans' fields are advanced (use shg_propagate or
  * shg_batch_submit afterwards for a clean result).  SHG_ERR_INVALID_ARG for
  * n <= 0, nsteps <= 0, max_groups <= 0, NULL outputs, or more groups than

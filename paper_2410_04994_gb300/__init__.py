@@ -306,16 +306,19 @@ def shg_get_heat(plan: int, q=None, dT=None, stream=None) -> None:
 
 
 def shg_pass_times(plans: Sequence[int], nsteps: int = 4, stream=None, max_groups: int = 16):
-    """Average row/column pass launch times per grid group (CUDA events)."""
+    """Average row/column pass launch times per grid group (CUDA events), and
+    the group's schedule: passes_per_step 1 (row- and column-layout step
+    passes alternate) or 2 (row pass, column pass)."""
     n = len(plans)
     arr = (_P * n)(*plans)
-    out = (_D * (4 * max_groups))()
+    out = (_D * (5 * max_groups))()
     inst = (_I * max_groups)()
     ng = _I()
     _check(_lib().shg_pass_times(arr, n, int(nsteps), out, inst, max_groups, ctypes.byref(ng),
                                  _stream(stream)), "shg_pass_times")
-    return [dict(nx=int(out[4 * g]), ny=int(out[4 * g + 1]), row_ms=out[4 * g + 2],
-                 col_ms=out[4 * g + 3], instances=inst[g]) for g in range(ng.value)]
+    return [dict(nx=int(out[5 * g]), ny=int(out[5 * g + 1]), row_ms=out[5 * g + 2],
+                 col_ms=out[5 * g + 3], passes_per_step=int(out[5 * g + 4]), instances=inst[g])
+            for g in range(ng.value)]
 
 
 def shg_field_powers_noalloc(fields, nx: int, ny: int, n_inst: int, lx: float, ly: float,

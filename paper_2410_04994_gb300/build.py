@@ -12,7 +12,7 @@ CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libshg.so")
 
-SOURCES = ["api.cu", "aux.cu", "passes_f32.cu", "passes_f32_lean.cu", "passes_f64.cu", "adjoint.cu", "adjoint_f32.cu",
+SOURCES = ["api.cu", "aux.cu", "passes_f32.cu", "passes_f32_lean.cu", "passes_f32_step.cu", "passes_f64.cu", "adjoint.cu", "adjoint_f32.cu",
            "adjoint_f64.cu", "heat.cu", "heat_direct.cu", "noalloc.cu", "peaks.cu",
            "cluster_f32.cu", "threewave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

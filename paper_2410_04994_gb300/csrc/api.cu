@@ -397,7 +397,19 @@ int row_umap_bit(const std::vector<shg_plan*>& plans) {
     return (lean_ok && p_fp32(plans) && !extras) ? (kRowUmap | kRowLean) : kRowUmap;
 }
 
-static_assert(kRowUmap > 4 && kRowLean > 4 && kRowLean != kRowUmap,
+// The one-pass-per-step schedule (k_col_step): FP32 groups on the per-point
+// table without monitors (the monitor-free rows), heat deposits or adjoint
+// checkpoints.  SHG_STEP_PASSES=0 keeps two passes per step.
+static bool step_schedule(bool fp64, const std::vector<shg_plan*>& plans, int rb) {
+    const char* v = getenv("SHG_STEP_PASSES");
+    if (v && v[0] == '0') return false;
+    if (fp64 || (rb & (kRowUmap | kRowLean)) != (kRowUmap | kRowLean)) return false;
+    for (const shg_plan* p : plans)
+        if (p->adj || ((p->flags & SHG_FLAG_THERMAL) && p->Q)) return false;
+    return true;
+}
+
+static_assert(kRowUmap > 5 && kRowLean > 5 && kRowLean != kRowUmap,
               "the row-pass bits must not collide with a flavour number");
 
 // Candidate flavours of a pass for a length: the default shape, the
@@ -555,6 +567,21 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     const int rb = row_umap_bit(plans);
     const int vr = fft_variant(fp64, nx, 0, rb, ninst) | rb;
     const int vc = fft_variant(fp64, ny, 1, 0, ninst);
+    if (step_schedule(fp64, plans, rb)) {
+        // one pass per step: rows (even s) and columns (odd s) alternate
+        for (int s = 0; s <= nz; ++s) {
+            if (s == 0)
+                e = launch_row(fp64, nx, descs, ninst, ny, nz, 0, tw, 0, st, vr);
+            else if ((s & 1) == 0)
+                e = launch_row_step(nx, descs, ninst, ny, nz, s, tw, st, vr);
+            else
+                e = launch_col_step(ny, descs, ninst, nx, nz, s, tw, st);
+            if (e != cudaSuccess) return cuda_fail(e, "step pass");
+        }
+        e = launch_power(fp64, idescs, descs, ninst, nx, ny, st);
+        if (e != cudaSuccess) return cuda_fail(e, "power");
+        return SHG_OK;
+    }
     for (int s = 0; s <= nz; ++s) {
         for (shg_plan* p : plans) {
             shg_status_t r = adjoint_checkpoint(p, s, st);
@@ -1623,6 +1650,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
         return SHG_ERR_INVALID_ARG;
     }
     std::vector<cudaEvent_t> ev(4 * nsteps * ng, nullptr);
+    std::vector<int> one_pass(ng, 0);
     auto release = [&] {
         for (auto& x : ev)
             if (x) cudaEventDestroy(x);
@@ -1650,15 +1678,28 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 }
                 cudaEventRecord(E[0], st);
             }
-            e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
-                           g.plans[0]->tw, hx, st,
-                           fft_variant(g.fp64, g.nx, 0, row_umap_bit(g.plans), int(g.plans.size())) |
-                               row_umap_bit(g.plans));
+            const int rbg = row_umap_bit(g.plans);
+            const int vrg = fft_variant(g.fp64, g.nx, 0, rbg, int(g.plans.size())) | rbg;
+            // the kernels the group's propagation runs: with one pass per step,
+            // a row-layout pass (s = 2) and a column-layout pass (s = 1)
+            const bool steps = step_schedule(g.fp64, g.plans, rbg) && g.nz >= 3;
+            one_pass[gi] = steps ? 1 : 0;
+            if (steps)
+                e = launch_row_step(g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, 2,
+                                    g.plans[0]->tw, st, vrg);
+            else
+                e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
+                               g.plans[0]->tw, hx, st, vrg);
             cudaEventRecord(E[1], st);
             if (e == cudaSuccess) {
                 cudaEventRecord(E[2], st);
-                e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx, g.plans[0]->tw, st,
-                               fft_variant(g.fp64, g.ny, 1, 0, int(g.plans.size())), g.tmaps);
+                if (steps)
+                    e = launch_col_step(g.ny, g.descs, int(g.plans.size()), g.nx, g.nz, 1,
+                                        g.plans[0]->tw, st);
+                else
+                    e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx,
+                                   g.plans[0]->tw, st,
+                                   fft_variant(g.fp64, g.ny, 1, 0, int(g.plans.size())), g.tmaps);
                 cudaEventRecord(E[3], st);
             }
         }
@@ -1675,10 +1716,11 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 tr += a;
                 tc += b;
             }
-            out[4 * gi] = ent->groups[gi].nx;
-            out[4 * gi + 1] = ent->groups[gi].ny;
-            out[4 * gi + 2] = tr / nsteps;
-            out[4 * gi + 3] = tc / nsteps;
+            out[5 * gi] = ent->groups[gi].nx;
+            out[5 * gi + 1] = ent->groups[gi].ny;
+            out[5 * gi + 2] = tr / nsteps;
+            out[5 * gi + 3] = tc / nsteps;
+            out[5 * gi + 4] = one_pass[gi] ? 1 : 2;
             if (inst_out) inst_out[gi] = int(ent->groups[gi].plans.size());
         }
         *ngroups = ng;

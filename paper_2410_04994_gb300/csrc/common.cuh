@@ -110,7 +110,7 @@ SHG_HD double phase_integrand(const DkModel& m, double dT) {
 // ------------------------------------------------------ per-instance ----
 // Everything one pass needs about one instance; built on the host by the plan.
 // Launch-variant bit of the row pass: read the per-point temperature table.
-constexpr int kRowUmap = 8;  // above every flavour number (0-4)
+constexpr int kRowUmap = 8;  // above every flavour number (0-5)
 // Launch bit of the row pass (with kRowUmap only): no instance of the group
 // monitors its power, so the kernel is instantiated without that code.
 constexpr int kRowLean = 16;

@@ -44,9 +44,10 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
-template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true,
+          bool PRE = false>
 cudaError_t row_attr() {
-    return allow_max_dyn_smem(k_row_pass<R, N, V, UM, NTH, ZS>);
+    return allow_max_dyn_smem(k_row_pass<R, N, V, UM, NTH, ZS, PRE>);
 }
 
 // Dynamic shared memory of a row pass: transform buffers + table prefetch
@@ -60,12 +61,13 @@ template <class R, int N, int V = 0, int NTH = kPassThreads> cudaError_t col_att
     return allow_max_dyn_smem(k_col_pass<R, N, V, NTH>);
 }
 
-template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
+template <class R, int N, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true,
+          bool PRE = false>
 cudaError_t row_launch(const void* descs, int ninst, int ny, int nz, int s, const void* tw,
                        int hx, cudaStream_t st) {
     using G = RowGeom<R, N, V, NTH>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    return launch_pdl(k_row_pass<R, N, V, UM, NTH, ZS>, grid, dim3(NTH),
+    return launch_pdl(k_row_pass<R, N, V, UM, NTH, ZS, PRE>, grid, dim3(NTH),
                       row_smem<R, N, V, UM, NTH>(hx),
                       st, static_cast<const InstDesc<R>*>(descs), ny, nz, s,
                       static_cast<const pt<R>*>(tw));
@@ -89,6 +91,22 @@ cudaError_t col_tma_launch(const void* tmaps, const void* descs, int ninst, int 
     return launch_pdl(k_col_tma<N>, grid, dim3(kPassThreads), K::smem, st,
                       static_cast<const CUtensorMap*>(tmaps), static_cast<const InstDesc<float>*>(descs),
                       nx, static_cast<const pt<float>*>(tw));
+}
+
+// The column-layout pass of the one-pass-per-step schedule (FP32).
+template <int N> constexpr size_t col_step_smem() {
+    using G = ColGeom<float, N, 0, kPassThreads>;
+    return G::fields + slot_bytes<float, kPassThreads>() + size_t(3) * N * sizeof(pt<float>);
+}
+template <int N> cudaError_t col_step_attr() { return allow_max_dyn_smem(k_col_step<N>); }
+template <int N>
+cudaError_t col_step_launch(const void* descs, int ninst, int nx, int nz, int s, const void* tw,
+                            cudaStream_t st) {
+    using G = ColGeom<float, N, 0, kPassThreads>;
+    dim3 grid((nx + G::TILE - 1) / G::TILE, ninst);
+    return launch_pdl(k_col_step<N>, grid, dim3(kPassThreads), col_step_smem<N>(), st,
+                      static_cast<const InstDesc<float>*>(descs), nx, nz, s,
+                      static_cast<const pt<float>*>(tw));
 }
 
 }  // namespace shg

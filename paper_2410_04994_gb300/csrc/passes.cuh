@@ -125,7 +125,12 @@ SHG_D void prefetch_slots(float4* slots, const float4* umap, int lmin, int nl, i
 // ZS = false: the instantiation for groups without power monitors (the
 // monitor's code at z_s is compiled out; the heat deposit stays a runtime
 // branch: removing it too made the compiler spill in the 256-point kernel).
-template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true>
+// PRE = true: the row-layout pass of the one-pass-per-step schedule
+// (k_col_step below), which applies Lx to the staged rows before the
+// nonlinear part as well: the second half of L(s-1) = Ly Lx, then N_b(s-1),
+// N_a(s), then the first half of L(s) = Lx Ly.
+template <class R, int NX, int V = 0, bool UM = false, int NTH = kPassThreads, bool ZS = true,
+          bool PRE = false>
 __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH))
     k_row_pass(const InstDesc<R>* __restrict__ descs, int ny, int nz, int s,
                const pt<R>* __restrict__ tw) {
@@ -195,6 +200,23 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     }
     if (!staged) cp_async_wait_all();
     __syncthreads();
+    if constexpr (PRE) {
+        // Lx on both staged rows (the rows of inactive threads are zeros)
+#pragma unroll 1
+        for (int f = 0; f < 2; ++f) {
+            C* sb = f == 0 ? sF : sS;
+            C v[E];
+#pragma unroll
+            for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
+            __syncthreads();  // the transform's exchanges reuse the buffer
+            fft_mul_ifft<R, NX, V, NX>(v, sb, t, twS, pS + f * NX);
+            if (active) {
+#pragma unroll
+                for (int m = 0; m < E; ++m) sb[pidx<R>(t + T * m)] = v[m];
+            }
+        }
+        __syncthreads();  // the nonlinear part reads points other threads transformed
+    }
     const R h = R(0.5) * d.dz;
     const int l_dep = dep ? d.hlz[s] : -1;
     const int j_dep = (dep && active) ? d.hiy[y] : -1;
@@ -424,6 +446,176 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
         fft_mul_ifft<R, NY, V, NY>(v, sb, t, twS, pS + f * NY);
         if (active) {
             C* col = field + size_t(f) * NY * nx + x;
+#pragma unroll
+            for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
+        }
+    }
+}
+
+// Column-layout pass of the one-pass-per-step schedule.  Lx and Ly commute
+// exactly (diagonal factors of a separable spectrum), so step s may apply
+// L(s) as Lx Ly or as Ly Lx, and the nonlinear part, being pointwise, may run
+// in either layout.  Pass s of the schedule applies the second half of
+// L(s-1), then N_b(s-1) and N_a(s), then the first half of L(s): in the row
+// layout for even s (k_row_pass with PRE: Lx, N, Lx) and in the column layout
+// for odd s (here: Ly, N, Ly; no Ly after the last step).  That is nz + 1
+// passes per propagation, each reading and writing both fields once, instead
+// of 2 nz + 1.  FP32; per-point temperature table or uniform temperature; no
+// heat deposit or monitor (the launcher checks).  The TILE columns of both
+// fields are staged as in k_col_pass.  Pair i of a thread is the columns
+// (x0 + 2 jj, x0 + 2 jj + 1) of row y, whose table entry is
+// [l][y][x0 / 2 + jj]; it is streamed into the thread's slots one iteration
+// ahead, as in the row pass.
+template <int NY, int NTH = kPassThreads>
+__global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
+    k_col_step(const InstDesc<float>* __restrict__ descs, int nx, int nz, int s,
+               const pt<float>* __restrict__ tw) {
+    using C = cx<float>;
+    using G = ColGeom<float, NY, 0, NTH>;
+    constexpr int E = FftCfg<float, NY, 0>::E, T = G::T, TILE = G::TILE, S = G::S;
+    constexpr int NP = E / 2;  // pairs per thread
+    static_assert((TILE / 2) * NY == NP * NTH, "whole pairs per thread");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ InstDesc<float> dsh;
+    __shared__ StageZ<float> zsh[5];
+    C* smem = reinterpret_cast<C*>(smem_raw);                         // [2][TILE][S]
+    float4* slots = reinterpret_cast<float4*>(smem_raw + G::fields);  // [2][layers][NTH]
+    pt<float>* twS = reinterpret_cast<pt<float>*>(smem_raw + G::fields + slot_bytes<float, NTH>());
+    pt<float>* pS = twS + NY;  // [2][NY]
+    const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
+    const int x0 = blockIdx.x * TILE, x = x0 + c;
+    const bool active = x < nx;
+    pdl_trigger();
+    {
+        const InstDesc<float>& dg = descs[blockIdx.y];
+        stage_tables<float, NY>(twS, pS, tw, dg.py);
+        if (threadIdx.x == 0) dsh = dg;
+        if (threadIdx.x < 5) {
+            const int q = 4 * s - 2 + threadIdx.x;
+            zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
+        }
+        pdl_wait();  // the fields are the previous pass's output
+        if (active) {
+#pragma unroll
+            for (int f = 0; f < 2; ++f) {
+                const C* col = dg.field + size_t(f) * NY * nx + x;
+                C* sb = smem + (f * TILE + c) * S;
+#pragma unroll
+                for (int m = 0; m < E; ++m)
+                    cp_async(&sb[pidx<float>(t + T * m)], col + size_t(t + T * m) * nx);
+            }
+        }
+    }
+    cp_async_commit();  // the field columns and the constant tables
+    __syncthreads();    // dsh, zsh
+    const InstDesc<float>& d = dsh;
+    const bool thermal = d.ttab != nullptr;
+    const float4* umap4 = reinterpret_cast<const float4*>(d.umap);
+    const int lmin = zsh[0].l, nl = zsh[4].l + 2 - zsh[0].l;
+    if (thermal && (d.umap == nullptr || nl > kSlotLayers)) {  // excluded by the launcher
+        cp_async_wait_all();
+        if (threadIdx.x == 0 && d.status) atomicExch(d.status, int(SHG_ERR_STATE));
+        return;
+    }
+    // pair i of this thread: the columns x0 + 2 jj, x0 + 2 jj + 1 of row y
+    auto pair_at = [&](int i, int& y, int& jj) {
+        const int p = threadIdx.x + NTH * i;
+        y = p / (TILE / 2);
+        jj = p - y * (TILE / 2);
+    };
+    // the table entries of pair i (layers lmin .. lmin + nl - 1) into slot
+    // buffer b, as one commit group
+    auto prefetch = [&](int i, int b) {
+        int y, jj;
+        pair_at(i, y, jj);
+        if (x0 + 2 * jj < nx) {
+            const uint64_t pol = l2_evict_first_policy();
+#pragma unroll 1
+            for (int k = 0; k < nl; ++k) {
+                const size_t o = (size_t(lmin + k) * NY + y) * size_t(nx / 2) + x0 / 2 + jj;
+                cp_async_stream(slots + (b * kSlotLayers + k) * NTH + threadIdx.x, umap4 + o, pol);
+            }
+        }
+        cp_async_commit();
+    };
+    if (thermal) {
+        prefetch(0, 0);
+        cp_async_wait_group<1>();
+    } else {
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    // Ly: the second half of L(s-1) (s >= 1 for every pass of this kernel)
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        C* sb = smem + (f * TILE + c) * S;
+        C v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<float>(t + T * m)] : mk<C>(0.f, 0.f);
+        __syncthreads();  // the transform's exchanges reuse the buffer
+        fft_mul_ifft<float, NY, 0, NY>(v, sb, t, twS, pS + f * NY);
+        if (active) {
+#pragma unroll
+            for (int m = 0; m < E; ++m) sb[pidx<float>(t + T * m)] = v[m];
+        }
+    }
+    __syncthreads();  // the pairs were transformed by other threads
+    // N_b(s-1), N_a(s), two adjacent columns per iteration in packed FP32
+    const float h = 0.5f * d.dz;
+#pragma unroll 1
+    for (int i = 0; i < NP; ++i) {
+        const int b = i & 1;
+        if (thermal) {
+            if (i + 1 < NP) {
+                prefetch(i + 1, b ^ 1);
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+        }
+        int y, jj;
+        pair_at(i, y, jj);
+        if (x0 + 2 * jj >= nx) continue;
+        C* e0 = smem + (2 * jj) * S + pidx<float>(y);
+        C* e1 = smem + (2 * jj + 1) * S + pidx<float>(y);
+        C aF0 = e0[0], aF1 = e1[0], aS0 = e0[TILE * S], aS1 = e1[TILE * S];
+        const PairSampler ps{slots + b * kSlotLayers * NTH + threadIdx.x, NTH, lmin};
+        auto cq = [&](int q) { return coef2_at(dsh, zsh[q], thermal, ps); };
+        Cx2 F{pk2(aF0.x, aF1.x), pk2(aF0.y, aF1.y)}, Sx{pk2(aS0.x, aS1.x), pk2(aS0.y, aS1.y)};
+        const Coef2 z2 = cq(2);
+        if (s > 0) {
+            const Coef2 c0 = cq(0);
+            const Coef2 cm = cq(1);
+            rk4_2(dsh, F, Sx, c0, cm, z2, h);
+        }
+        if (s < nz) {
+            const Coef2 cm = cq(3);
+            const Coef2 c1 = cq(4);
+            rk4_2(dsh, F, Sx, z2, cm, c1, h);
+        }
+        up2(F.r, aF0.x, aF1.x);
+        up2(F.i, aF0.y, aF1.y);
+        up2(Sx.r, aS0.x, aS1.x);
+        up2(Sx.i, aS0.y, aS1.y);
+        e0[0] = aF0;
+        e1[0] = aF1;
+        e0[TILE * S] = aS0;
+        e1[TILE * S] = aS1;
+    }
+    __syncthreads();  // the transforms read points that other threads advanced
+    // Ly: the first half of L(s) (none after the last step); results to global
+#pragma unroll 1
+    for (int f = 0; f < 2; ++f) {
+        C* sb = smem + (f * TILE + c) * S;
+        C v[E];
+#pragma unroll
+        for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<float>(t + T * m)] : mk<C>(0.f, 0.f);
+        if (s < nz) {
+            __syncthreads();
+            fft_mul_ifft<float, NY, 0, NY>(v, sb, t, twS, pS + f * NY);
+        }
+        if (active) {
+            C* col = d.field + size_t(f) * NY * nx + x;
 #pragma unroll
             for (int m = 0; m < E; ++m) col[size_t(t + T * m) * nx] = v[m];
         }

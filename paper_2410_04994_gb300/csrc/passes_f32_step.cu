@@ -1,0 +1,76 @@
+// Single-precision passes of the one-pass-per-step schedule: the row-layout
+// pass (k_row_pass with the per-point table, without the z_s code, with Lx
+// before the nonlinear part) in every flavour of the monitor-free rows, and
+// the column-layout pass k_col_step (n = 8..1024).  A translation unit of its
+// own so that the library builds in parallel.
+#include "launch_passes.cuh"
+#include "plan.h"
+
+namespace shg {
+
+#define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
+#define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
+
+// v: the row flavour (0, 1, 3, 4) without the row-pass bits.
+cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
+                         const void* tw, cudaStream_t st) {
+    if (v == 3 || v == 4) {
+        switch (nx) {
+#define X(n)                                                                                   \
+    case n:                                                                                    \
+        return v == 3 ? row_launch<float, n, 0, true, 128, false, true>(descs, ninst, ny, nz, s, \
+                                                                         tw, 0, st)            \
+                      : row_launch<float, n, 0, true, 64, false, true>(descs, ninst, ny, nz, s,  \
+                                                                        tw, 0, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
+    if (v == 1) {
+        switch (nx) {
+#define X(n)                                                                                   \
+    case n:                                                                                    \
+        return row_launch<float, n, 1, true, kPassThreads, false, true>(descs, ninst, ny, nz, s, \
+                                                                         tw, 0, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
+    switch (nx) {
+#define X(n)                                                                                   \
+    case n:                                                                                    \
+        return row_launch<float, n, 0, true, kPassThreads, false, true>(descs, ninst, ny, nz, s, \
+                                                                         tw, 0, st);
+        SHG_F32_SIZES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t col_f32_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
+                         const void* tw, cudaStream_t st) {
+    switch (ny) {
+#define X(n) case n: return col_step_launch<n>(descs, ninst, nx, nz, s, tw, st);
+        SHG_F32_SIZES(X)
+#undef X
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t attr_f32_step() {
+    cudaError_t e = cudaSuccess;
+#define X(n)                                                                           \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true, kPassThreads, false, true>(); \
+    if (e == cudaSuccess) e = col_step_attr<n>();
+    SHG_F32_SIZES(X)
+#undef X
+#define X(n)                                                                           \
+    if (e == cudaSuccess) e = row_attr<float, n, 1, true, kPassThreads, false, true>(); \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true, 128, false, true>();          \
+    if (e == cudaSuccess) e = row_attr<float, n, 0, true, 64, false, true>();
+    SHG_F32_VARIANT_SIZES(X)
+#undef X
+    return e;
+}
+
+}  // namespace shg

@@ -149,7 +149,7 @@ def test_the_same_plan_twice_is_refused(pkg):
     maps = (ctypes.c_void_p * 2)(fake, fake)
     ext = (ctypes.c_double * 2)(0.0, 0.0)
     assert lib.shg_set_temperature_batch(arr, 2, maps, 2, 2, 2, ext, ext, None) == 1
-    out = (ctypes.c_double * 8)()
+    out = (ctypes.c_double * 10)()
     ng = ctypes.c_int()
     assert lib.shg_pass_times(arr, 2, 1, out, None, 2, ctypes.byref(ng), None) == 1
 
