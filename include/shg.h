@@ -175,8 +175,8 @@ shg_status_t shg_set_fields(shg_plan_t *plan, const void *a_f_dev, const void *a
  * initial fields, the fused passes and the FP64 power reductions.  The
  * passes are 2 nz + 1 (N with Lx, then Ly, per step), or nz + 1 when Lx and
  * Ly alternate their order so that one pass per step suffices (FP32 plans
- * with the per-point temperature table and no monitor, heat deposit or
- * adjoint state; SHG_STEP_PASSES=0 turns that off); single FP32 64^2 and
+ * with the per-point temperature table and no monitor or adjoint state;
+ * SHG_STEP_PASSES=0 turns that off); single FP32 64^2 and
  * 128^2 plans run in one cluster-resident launch.  Asynchronous on
  * `stream`. */
 shg_status_t shg_propagate(shg_plan_t *plan, shg_stream_t stream);
@@ -323,7 +323,7 @@ shg_status_t shg_get_heat(shg_plan_t *plan, double *q_dev, float *dT_dev,
  * inst_out[g] = instances in the
  * group.  The passes timed are those the group's propagation runs: for a
  * group on the one-pass-per-step schedule (FP32, per-point temperature
- * table, no monitor, heat deposit or adjoint state; nz >= 3), the row-layout
+ * table, no monitor or adjoint state; nz >= 3), the row-layout
  * pass (Lx, N, Lx) and the column-layout pass (Ly, N, Ly); otherwise the
  * row pass (N, Lx) and the column pass (Ly).  A group not tuned yet in this process is tuned first (outside
  * the event pairs).  The plans' fields are advanced (use shg_propagate or

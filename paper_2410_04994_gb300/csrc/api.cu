@@ -398,14 +398,15 @@ int row_umap_bit(const std::vector<shg_plan*>& plans) {
 }
 
 // The one-pass-per-step schedule (k_col_step): FP32 groups on the per-point
-// table without monitors (the monitor-free rows), heat deposits or adjoint
-// checkpoints.  SHG_STEP_PASSES=0 keeps two passes per step.
+// table without monitors (the monitor-free rows) or adjoint checkpoints (the
+// adjoint replays the two-pass states).  Heat deposits are binned in either
+// layout.  SHG_STEP_PASSES=0 keeps two passes per step.
 static bool step_schedule(bool fp64, const std::vector<shg_plan*>& plans, int rb) {
     const char* v = getenv("SHG_STEP_PASSES");
     if (v && v[0] == '0') return false;
     if (fp64 || (rb & (kRowUmap | kRowLean)) != (kRowUmap | kRowLean)) return false;
     for (const shg_plan* p : plans)
-        if (p->adj || ((p->flags & SHG_FLAG_THERMAL) && p->Q)) return false;
+        if (p->adj) return false;
     return true;
 }
 
@@ -553,9 +554,12 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
             if (e != cudaSuccess) return cuda_fail(e, "memset Q");
         }
     }
-    int hx = 0;
+    int hx = 0, hy = 0;
     for (shg_plan* p : plans)
-        if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+        if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
+            hx = std::max(hx, p->g.hx);
+            hy = std::max(hy, p->g.hy);
+        }
     if (cluster_path(plans)) {
         // the whole z-march in one cluster-resident launch
         e = launch_cluster(nx, descs, ninst, nz, tw, st);
@@ -571,11 +575,11 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
         // one pass per step: rows (even s) and columns (odd s) alternate
         for (int s = 0; s <= nz; ++s) {
             if (s == 0)
-                e = launch_row(fp64, nx, descs, ninst, ny, nz, 0, tw, 0, st, vr);
+                e = launch_row(fp64, nx, descs, ninst, ny, nz, 0, tw, hx, st, vr);
             else if ((s & 1) == 0)
-                e = launch_row_step(nx, descs, ninst, ny, nz, s, tw, st, vr);
+                e = launch_row_step(nx, descs, ninst, ny, nz, s, tw, hx, st, vr);
             else
-                e = launch_col_step(ny, descs, ninst, nx, nz, s, tw, st);
+                e = launch_col_step(ny, descs, ninst, nx, nz, s, tw, hy, st);
             if (e != cudaSuccess) return cuda_fail(e, "step pass");
         }
         e = launch_power(fp64, idescs, descs, ninst, nx, ny, st);
@@ -1665,9 +1669,12 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             const int zs = std::min(s, g.nz - 1 > 0 ? g.nz - 1 : 0);
             cudaEvent_t* E = &ev[4 * ((s - 1) * ng + gi)];
             cudaEventRecord(E[0], st);
-            int hx = 0;
+            int hx = 0, hy = 0;
             for (shg_plan* p : g.plans)
-                if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+                if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
+                    hx = std::max(hx, p->g.hx);
+                    hy = std::max(hy, p->g.hy);
+                }
             if (s == 1) {
                 shg_status_t r2 = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs,
                                              int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps,
@@ -1686,7 +1693,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             one_pass[gi] = steps ? 1 : 0;
             if (steps)
                 e = launch_row_step(g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, 2,
-                                    g.plans[0]->tw, st, vrg);
+                                    g.plans[0]->tw, hx, st, vrg);
             else
                 e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
                                g.plans[0]->tw, hx, st, vrg);
@@ -1695,7 +1702,7 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 cudaEventRecord(E[2], st);
                 if (steps)
                     e = launch_col_step(g.ny, g.descs, int(g.plans.size()), g.nx, g.nz, 1,
-                                        g.plans[0]->tw, st);
+                                        g.plans[0]->tw, hy, st);
                 else
                     e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx,
                                    g.plans[0]->tw, st,

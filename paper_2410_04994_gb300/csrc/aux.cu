@@ -15,8 +15,8 @@ bool has_col_small_f32(int);
 bool has_col_wide_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
-cudaError_t row_f32_step(int, int, const void*, int, int, int, int, const void*, cudaStream_t);
-cudaError_t col_f32_step(int, const void*, int, int, int, int, const void*, cudaStream_t);
+cudaError_t row_f32_step(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+cudaError_t col_f32_step(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
 cudaError_t attr_f32_step();
 
 thread_local bool pdl_enabled = false;
@@ -44,13 +44,13 @@ cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, 
 int col_tma_tile(bool fp64, int ny) { return fp64 ? 0 : col_tma_tile_f32(ny); }
 
 cudaError_t launch_row_step(int nx, const void* descs, int ninst, int ny, int nz, int s,
-                            const void* tw, cudaStream_t st, int variant) {
-    return row_f32_step(nx, variant & ~(kRowUmap | kRowLean), descs, ninst, ny, nz, s, tw, st);
+                            const void* tw, int hx, cudaStream_t st, int variant) {
+    return row_f32_step(nx, variant & ~(kRowUmap | kRowLean), descs, ninst, ny, nz, s, tw, hx, st);
 }
 
 cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
-                            const void* tw, cudaStream_t st) {
-    return col_f32_step(ny, descs, ninst, nx, nz, s, tw, st);
+                            const void* tw, int hy, cudaStream_t st) {
+    return col_f32_step(ny, descs, ninst, nx, nz, s, tw, hy, st);
 }
 
 cudaError_t setup_pass_attributes() {

@@ -461,7 +461,10 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
 // for odd s (here: Ly, N, Ly; no Ly after the last step).  That is nz + 1
 // passes per propagation, each reading and writing both fields once, instead
 // of 2 nz + 1.  FP32; per-point temperature table or uniform temperature; no
-// heat deposit or monitor (the launcher checks).  The TILE columns of both
+// monitor (the launcher checks).  The heat deposit at z_s (THERMAL plans) is
+// binned per CTA in shared memory, [TILE][hy] (the heat-grid column of each
+// field column is fixed, its row varies), and added to the heat grid with one
+// double-precision atomic per touched node.  The TILE columns of both
 // fields are staged as in k_col_pass.  Pair i of a thread is the columns
 // (x0 + 2 jj, x0 + 2 jj + 1) of row y, whose table entry is
 // [l][y][x0 / 2 + jj]; it is streamed into the thread's slots one iteration
@@ -482,9 +485,13 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
     float4* slots = reinterpret_cast<float4*>(smem_raw + G::fields);  // [2][layers][NTH]
     pt<float>* twS = reinterpret_cast<pt<float>*>(smem_raw + G::fields + slot_bytes<float, NTH>());
     pt<float>* pS = twS + NY;  // [2][NY]
+    float* bins = reinterpret_cast<float*>(pS + 2 * NY);  // [TILE][hy] heat deposits
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x0 = blockIdx.x * TILE, x = x0 + c;
     const bool active = x < nx;
+    const bool dep = descs[blockIdx.y].Q != nullptr;
+    const int nb = dep ? TILE * descs[blockIdx.y].hy : 0;
+    for (int i = threadIdx.x; i < nb; i += NTH) bins[i] = 0.f;
     pdl_trigger();
     {
         const InstDesc<float>& dg = descs[blockIdx.y];
@@ -560,8 +567,20 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
         }
     }
     __syncthreads();  // the pairs were transformed by other threads
-    // N_b(s-1), N_a(s), two adjacent columns per iteration in packed FP32
+    // N_b(s-1), the heat deposit at z_s, N_a(s), two adjacent columns per
+    // iteration in packed FP32
     const float h = 0.5f * d.dz;
+    const int l_dep = dep ? d.hlz[s] : -1;
+    const float w_dep = dep ? d.dxdy * d.dz * ((s == 0 || s == nz) ? 0.5f : 1.f) : 0.f;
+    auto deposit = [&](int xi, int y, const C& aF, const C& aS) {
+        const int i = __ldg(&d.hix[xi]), j = __ldg(&d.hiy[y]);
+        if (i >= 0 && j >= 0) {
+            const float aF2 = aF.x * aF.x + aF.y * aF.y;
+            const float aS2 = aS.x * aS.x + aS.y * aS.y;
+            const float q = aF2 * (d.qaF + d.qbF * aF2) + aS2 * (d.qaS + d.qbS * aS2);
+            atomicAdd(&bins[(xi - x0) * d.hy + j], q * w_dep);
+        }
+    };
 #pragma unroll 1
     for (int i = 0; i < NP; ++i) {
         const int b = i & 1;
@@ -588,6 +607,14 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
             const Coef2 cm = cq(1);
             rk4_2(dsh, F, Sx, c0, cm, z2, h);
         }
+        if (l_dep >= 0) {
+            up2(F.r, aF0.x, aF1.x);
+            up2(F.i, aF0.y, aF1.y);
+            up2(Sx.r, aS0.x, aS1.x);
+            up2(Sx.i, aS0.y, aS1.y);
+            deposit(x0 + 2 * jj, y, aF0, aS0);
+            deposit(x0 + 2 * jj + 1, y, aF1, aS1);
+        }
         if (s < nz) {
             const Coef2 cm = cq(3);
             const Coef2 c1 = cq(4);
@@ -603,6 +630,17 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
         e1[TILE * S] = aS1;
     }
     __syncthreads();  // the transforms read points that other threads advanced
+    if (l_dep >= 0) {
+        // one double atomic per touched heat node
+        for (int k = threadIdx.x; k < nb; k += NTH) {
+            const float v = bins[k];
+            if (v != 0.f) {
+                const int cc = k / d.hy, j = k - cc * d.hy;
+                const int i = __ldg(&d.hix[x0 + cc]);
+                atomicAdd(&d.Q[(size_t(l_dep) * d.hy + j) * d.hx + i], double(v));
+            }
+        }
+    }
     // Ly: the first half of L(s) (none after the last step); results to global
 #pragma unroll 1
     for (int f = 0; f < 2; ++f) {

@@ -13,15 +13,15 @@ namespace shg {
 
 // v: the row flavour (0, 1, 3, 4) without the row-pass bits.
 cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
-                         const void* tw, cudaStream_t st) {
+                         const void* tw, int hx, cudaStream_t st) {
     if (v == 3 || v == 4) {
         switch (nx) {
 #define X(n)                                                                                   \
     case n:                                                                                    \
         return v == 3 ? row_launch<float, n, 0, true, 128, false, true>(descs, ninst, ny, nz, s, \
-                                                                         tw, 0, st)            \
+                                                                         tw, hx, st)            \
                       : row_launch<float, n, 0, true, 64, false, true>(descs, ninst, ny, nz, s,  \
-                                                                        tw, 0, st);
+                                                                        tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
@@ -31,7 +31,7 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
 #define X(n)                                                                                   \
     case n:                                                                                    \
         return row_launch<float, n, 1, true, kPassThreads, false, true>(descs, ninst, ny, nz, s, \
-                                                                         tw, 0, st);
+                                                                         tw, hx, st);
             SHG_F32_VARIANT_SIZES(X)
 #undef X
         }
@@ -40,7 +40,7 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
 #define X(n)                                                                                   \
     case n:                                                                                    \
         return row_launch<float, n, 0, true, kPassThreads, false, true>(descs, ninst, ny, nz, s, \
-                                                                         tw, 0, st);
+                                                                         tw, hx, st);
         SHG_F32_SIZES(X)
 #undef X
     }
@@ -48,9 +48,9 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
 }
 
 cudaError_t col_f32_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
-                         const void* tw, cudaStream_t st) {
+                         const void* tw, int hy, cudaStream_t st) {
     switch (ny) {
-#define X(n) case n: return col_step_launch<n>(descs, ninst, nx, nz, s, tw, st);
+#define X(n) case n: return col_step_launch<n>(descs, ninst, nx, nz, s, tw, hy, st);
         SHG_F32_SIZES(X)
 #undef X
     }

@@ -137,13 +137,14 @@ size_t row_pass_smem(bool fp64, int nx, int hx, int variant = 0);
 // the TMA-staged column pass, or nullptr for the cp.async-staged one.
 cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, const void* tw,
                        cudaStream_t st, int variant = 0, const void* tmaps = nullptr);
-// The one-pass-per-step schedule (FP32, per-point table, no monitor, deposit
-// or adjoint state): the row-layout pass s (even s >= 2; Lx, N, Lx) in row
-// flavour `variant`, and the column-layout pass s (odd s; Ly, N, Ly).
+// The one-pass-per-step schedule (FP32, per-point table, no monitor or
+// adjoint state): the row-layout pass s (even s >= 2; Lx, N, Lx) in row
+// flavour `variant`, and the column-layout pass s (odd s; Ly, N, Ly); hx, hy:
+// the largest heat grid of the group (0 without deposits), for the bins.
 cudaError_t launch_row_step(int nx, const void* descs, int ninst, int ny, int nz, int s,
-                            const void* tw, cudaStream_t st, int variant);
+                            const void* tw, int hx, cudaStream_t st, int variant);
 cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
-                            const void* tw, cudaStream_t st);
+                            const void* tw, int hy, cudaStream_t st);
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
 bool has_col_small(bool fp64, int n);  // row and column passes in 128/64-thread CTAs (flavours 3, 4)

@@ -98,3 +98,30 @@ def test_pass_times_report_the_step_kernels():
     assert g["nx"] == 256 and g["instances"] == 4 and g["passes_per_step"] == 1
     assert g["row_ms"] > 0 and g["col_ms"] > 0
     assert 0.3 < g["col_ms"] / g["row_ms"] < 3
+
+
+def test_heat_deposits_agree_between_the_schedules(monkeypatch):
+    """A THERMAL plan with a map deposits q_dot dV at every z_s in whichever
+    layout the pass runs; the heat grid and eta agree with the two-pass
+    schedule (deposit order differs: float bins, double atomics)."""
+    import numpy as np
+    import paper_2410_04994_gb300 as pkg
+    w = W.thermal_loop(n=128, nz=60, heat=(32, 24, 40), p1=100.0, n_outer=1)
+    dT = np.asarray(W.depleted_absorbing(n=128, nz=60, tgrid=(12, 12, 20)).dT)
+
+    def run():
+        plan = pkg.Plan(w, thermal=True)
+        plan.set_temperature(torch.as_tensor(dT), w.t_lx, w.t_ly)
+        plan.propagate()
+        eta = plan.efficiency()[0]
+        q = torch.empty((w.hz, w.hy, w.hx), dtype=torch.float64, device="cuda")
+        pkg.shg_get_heat(plan.handle, q, None)
+        return eta, q.cpu().numpy()
+
+    eta_s, q_s = run()
+    monkeypatch.setenv("SHG_STEP_PASSES", "0")
+    eta_t, q_t = run()
+    assert abs(eta_s / eta_t - 1) < 2e-5
+    assert q_s.sum() > 0
+    assert np.abs(q_s - q_t).max() <= 2e-5 * np.abs(q_t).max()
+    assert abs(q_s.sum() / q_t.sum() - 1) < 1e-5
