@@ -446,6 +446,27 @@ static int supported_flavour(bool fp64, int n, int pass, int f) {
     return f;
 }
 
+// Tuner keys of the one-pass-per-step kernels: 8 the row-layout pass, 9 the
+// column-layout pass (+4 for groups of at most kFewInstances instances).
+static int step_key(int which, int ninst) { return 8 + which + (ninst <= kFewInstances ? 4 : 0); }
+
+// Flavour of a step kernel: which = 0, the row-layout pass (row flavours 0,
+// 1, 3, 4); which = 1, the column-layout pass (3: 128-thread CTAs where they
+// exist, else 0).
+static int supported_step_flavour(bool fp64, int n, int which, int f) {
+    if (which == 0) return supported_flavour(fp64, n, 0, f == 2 || f == 5 ? 0 : f);
+    return (f == 3 || f == 4) && has_col_step_small(n) ? 3 : 0;
+}
+
+int step_variant(bool fp64, int n, int which, int ninst) {
+    const int f = forced_variant();
+    if (f >= 0) return supported_step_flavour(fp64, n, which, f);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    load_tune_cache();
+    auto it = g_tuned.find(std::make_tuple(fp64, n, step_key(which, ninst)));
+    return it == g_tuned.end() ? 0 : supported_step_flavour(fp64, n, which, it->second);
+}
+
 int fft_variant(bool fp64, int n, int pass, int row_bits, int ninst) {
     const int f = forced_variant();
     if (f >= 0) return supported_flavour(fp64, n, pass, f);
@@ -471,16 +492,28 @@ struct EventPair {
 // candidate's time is its best round.  The group's fields are modified; every
 // propagation re-initialises them first.
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits) {
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits,
+                        bool steps, int hy) {
     if (forced_variant() >= 0) return SHG_OK;
-    for (int pass = 0; pass < 2; ++pass) {
+    steps = steps && nz >= 3;  // the step kernels are timed at s = 2 (rows) and s = 1 (columns)
+    // passes: 0 rows, 1 the column pass of the two-pass schedule; with one
+    // pass per step, 0 the row-layout and 2 the column-layout step pass
+    for (int pass = 0; pass < 3; ++pass) {
+        if ((pass == 1 && steps) || (pass == 2 && !steps)) continue;
         const int n = pass == 0 ? nx : ny;
-        const std::vector<int> cand = candidates(fp64, n, pass, tmaps != nullptr);
+        std::vector<int> cand;
+        if (pass == 2) {
+            cand.push_back(0);
+            if (has_col_step_small(n)) cand.push_back(3);
+        } else {
+            cand = candidates(fp64, n, pass, tmaps != nullptr && !steps);
+        }
         if (cand.size() < 2) continue;
+        const int key = steps ? step_key(pass == 0 ? 0 : 1, ninst) : tune_key(pass, row_bits, ninst);
         {
             std::lock_guard<std::mutex> lk(g_tune_mu);
             load_tune_cache();
-            if (g_tuned.count(std::make_tuple(fp64, n, tune_key(pass, row_bits, ninst)))) continue;
+            if (g_tuned.count(std::make_tuple(fp64, n, key))) continue;
         }
         EventPair ev;
         SHG_CK(cudaEventCreate(&ev.e0));
@@ -488,6 +521,9 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         cudaEvent_t e0 = ev.e0, e1 = ev.e1;
         const int s = nz > 1 ? 1 : 0;
         auto launch = [&](int v) {
+            if (steps)
+                return pass == 0 ? launch_row_step(nx, descs, ninst, ny, nz, 2, tw, hx, st, v | row_bits)
+                                 : launch_col_step(ny, descs, ninst, nx, nz, 1, tw, hy, st, v);
             return pass == 0 ? launch_row(fp64, nx, descs, ninst, ny, nz, s, tw, hx, st, v | row_bits)
                              : launch_col(fp64, ny, descs, ninst, nx, tw, st, v, tmaps);
         };
@@ -518,7 +554,6 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
                 best_v = cand[c];
             }
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        const int key = tune_key(pass, row_bits, ninst);
         g_tuned[std::make_tuple(fp64, n, key)] = best_v;
         save_tune_decision(fp64, n, key, best_v);
     }
@@ -573,13 +608,15 @@ shg_status_t enqueue_forward(bool fp64, int nx, int ny, int nz, const void* desc
     const int vc = fft_variant(fp64, ny, 1, 0, ninst);
     if (step_schedule(fp64, plans, rb)) {
         // one pass per step: rows (even s) and columns (odd s) alternate
+        const int vrs = step_variant(fp64, nx, 0, ninst) | rb;
+        const int vcs = step_variant(fp64, ny, 1, ninst);
         for (int s = 0; s <= nz; ++s) {
             if (s == 0)
-                e = launch_row(fp64, nx, descs, ninst, ny, nz, 0, tw, hx, st, vr);
+                e = launch_row(fp64, nx, descs, ninst, ny, nz, 0, tw, hx, st, vrs);
             else if ((s & 1) == 0)
-                e = launch_row_step(nx, descs, ninst, ny, nz, s, tw, hx, st, vr);
+                e = launch_row_step(nx, descs, ninst, ny, nz, s, tw, hx, st, vrs);
             else
-                e = launch_col_step(ny, descs, ninst, nx, nz, s, tw, hy, st);
+                e = launch_col_step(ny, descs, ninst, nx, nz, s, tw, hy, st, vcs);
             if (e != cudaSuccess) return cuda_fail(e, "step pass");
         }
         e = launch_power(fp64, idescs, descs, ninst, nx, ny, st);
@@ -651,9 +688,11 @@ static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
                                one, s, tmaps);
     };
     if (!cluster_path(one)) {
-        int hx = ((p->flags & SHG_FLAG_THERMAL) && p->Q) ? p->g.hx : 0;
-        shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw, hx, st,
-                                    p->has_cmap ? p->cmap_dev : nullptr, row_umap_bit(one));
+        const bool dep = (p->flags & SHG_FLAG_THERMAL) && p->Q;
+        const int rb = row_umap_bit(one);
+        shg_status_t r = tune_group(p->fp64, p->g.nx, p->g.ny, p->g.nz, p->desc, 1, p->tw,
+                                    dep ? p->g.hx : 0, st, p->has_cmap ? p->cmap_dev : nullptr, rb,
+                                    step_schedule(p->fp64, one, rb), dep ? p->g.hy : 0);
         if (r != SHG_OK) return r;
     }
     if (!use_graphs()) return body(st);
@@ -1557,11 +1596,16 @@ extern "C" shg_status_t shg_batch_submit(shg_plan_t* const* plans, int n, double
     }
     if ((r = refresh_entry(ent, st)) != SHG_OK) return r;
     for (auto& g : ent->groups) {
-        int hx = 0;
+        int hx = 0, hy = 0;
         for (shg_plan* p : g.plans)
-            if ((p->flags & SHG_FLAG_THERMAL) && p->Q) hx = std::max(hx, p->g.hx);
+            if ((p->flags & SHG_FLAG_THERMAL) && p->Q) {
+                hx = std::max(hx, p->g.hx);
+                hy = std::max(hy, p->g.hy);
+            }
+        const int rb = row_umap_bit(g.plans);
         if ((r = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs, int(g.plans.size()),
-                            g.plans[0]->tw, hx, st, g.tmaps, row_umap_bit(g.plans))) != SHG_OK)
+                            g.plans[0]->tw, hx, st, g.tmaps, rb,
+                            step_schedule(g.fp64, g.plans, rb), hy)) != SHG_OK)
             return r;
     }
     if (use_graphs()) {
@@ -1676,9 +1720,10 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                     hy = std::max(hy, p->g.hy);
                 }
             if (s == 1) {
+                const int rb0 = row_umap_bit(g.plans);
                 shg_status_t r2 = tune_group(g.fp64, g.nx, g.ny, g.nz, g.descs,
                                              int(g.plans.size()), g.plans[0]->tw, hx, st, g.tmaps,
-                                             row_umap_bit(g.plans));
+                                             rb0, step_schedule(g.fp64, g.plans, rb0), hy);
                 if (r2 != SHG_OK) {
                     release();
                     return r2;
@@ -1693,7 +1738,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
             one_pass[gi] = steps ? 1 : 0;
             if (steps)
                 e = launch_row_step(g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, 2,
-                                    g.plans[0]->tw, hx, st, vrg);
+                                    g.plans[0]->tw, hx, st,
+                                    step_variant(g.fp64, g.nx, 0, int(g.plans.size())) | rbg);
             else
                 e = launch_row(g.fp64, g.nx, g.descs, int(g.plans.size()), g.ny, g.nz, zs,
                                g.plans[0]->tw, hx, st, vrg);
@@ -1702,7 +1748,8 @@ extern "C" shg_status_t shg_pass_times(shg_plan_t* const* plans, int n, int nste
                 cudaEventRecord(E[2], st);
                 if (steps)
                     e = launch_col_step(g.ny, g.descs, int(g.plans.size()), g.nx, g.nz, 1,
-                                        g.plans[0]->tw, hy, st);
+                                        g.plans[0]->tw, hy, st,
+                                        step_variant(g.fp64, g.ny, 1, int(g.plans.size())));
                 else
                     e = launch_col(g.fp64, g.ny, g.descs, int(g.plans.size()), g.nx,
                                    g.plans[0]->tw, st,

@@ -16,7 +16,8 @@ bool has_col_wide_f32(int);
 cudaError_t attr_f32();
 cudaError_t attr_f64();
 cudaError_t row_f32_step(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
-cudaError_t col_f32_step(int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+cudaError_t col_f32_step(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
+bool has_col_step_small_f32(int);
 cudaError_t attr_f32_step();
 
 thread_local bool pdl_enabled = false;
@@ -49,9 +50,11 @@ cudaError_t launch_row_step(int nx, const void* descs, int ninst, int ny, int nz
 }
 
 cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
-                            const void* tw, int hy, cudaStream_t st) {
-    return col_f32_step(ny, descs, ninst, nx, nz, s, tw, hy, st);
+                            const void* tw, int hy, cudaStream_t st, int variant) {
+    return col_f32_step(ny, variant, descs, ninst, nx, nz, s, tw, hy, st);
 }
+
+bool has_col_step_small(int n) { return has_col_step_small_f32(n); }
 
 cudaError_t setup_pass_attributes() {
     cudaError_t e = attr_f32();

@@ -10,6 +10,9 @@ namespace shg {
 
 #define SHG_F32_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512) X(1024)
 #define SHG_F32_VARIANT_SIZES(X) X(64) X(128) X(256)
+#define SHG_F32_SMALL_COL_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512)
+
+bool has_col_step_small_f32(int n) { return n >= 8 && n <= 512; }
 
 // v: the row flavour (0, 1, 3, 4) without the row-pass bits.
 cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
@@ -47,8 +50,17 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
     return cudaErrorInvalidValue;
 }
 
-cudaError_t col_f32_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
+// v: 3 for 128-thread CTAs (lengths up to 512: half the columns per CTA), else
+// 256-thread CTAs.
+cudaError_t col_f32_step(int ny, int v, const void* descs, int ninst, int nx, int nz, int s,
                          const void* tw, int hy, cudaStream_t st) {
+    if (v == 3) {
+        switch (ny) {
+#define X(n) case n: return col_step_launch<n, 128>(descs, ninst, nx, nz, s, tw, hy, st);
+            SHG_F32_SMALL_COL_SIZES(X)
+#undef X
+        }
+    }
     switch (ny) {
 #define X(n) case n: return col_step_launch<n>(descs, ninst, nx, nz, s, tw, hy, st);
         SHG_F32_SIZES(X)
@@ -63,6 +75,10 @@ cudaError_t attr_f32_step() {
     if (e == cudaSuccess) e = row_attr<float, n, 0, true, kPassThreads, false, true>(); \
     if (e == cudaSuccess) e = col_step_attr<n>();
     SHG_F32_SIZES(X)
+#undef X
+#define X(n) \
+    if (e == cudaSuccess) e = col_step_attr<n, 128>();
+    SHG_F32_SMALL_COL_SIZES(X)
 #undef X
 #define X(n)                                                                           \
     if (e == cudaSuccess) e = row_attr<float, n, 1, true, kPassThreads, false, true>(); \

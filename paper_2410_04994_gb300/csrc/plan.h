@@ -144,7 +144,8 @@ cudaError_t launch_col(bool fp64, int ny, const void* descs, int ninst, int nx, 
 cudaError_t launch_row_step(int nx, const void* descs, int ninst, int ny, int nz, int s,
                             const void* tw, int hx, cudaStream_t st, int variant);
 cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz, int s,
-                            const void* tw, int hy, cudaStream_t st);
+                            const void* tw, int hy, cudaStream_t st, int variant);
+bool has_col_step_small(int n);  // the column-layout pass in 128-thread CTAs (flavour 3)
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
 bool has_col_small(bool fp64, int n);  // row and column passes in 128/64-thread CTAs (flavours 3, 4)
@@ -153,8 +154,14 @@ bool has_col_wide(bool fp64, int n);   // the column pass in 512-thread CTAs (fl
 // measured once per process on the first group that uses it, unless
 // SHG_FFT_VARIANT forces one.  tune_group() must run outside stream capture.
 int fft_variant(bool fp64, int n, int pass, int row_bits = 0, int ninst = 1 << 30);
+// steps: the group runs one pass per step (the row- and column-layout step
+// kernels are tuned then, under keys of their own; hy sizes the deposit bins).
 shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, int ninst,
-                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits);
+                        const void* tw, int hx, cudaStream_t st, const void* tmaps, int row_bits,
+                        bool steps = false, int hy = 0);
+// Flavour of a one-pass-per-step kernel: which = 0 the row-layout pass, 1 the
+// column-layout pass.
+int step_variant(bool fp64, int n, int which, int ninst);
 // kRowUmap if the row passes of these plans (one grid) read the per-point
 // temperature table: every plan with a map keeps one, and one z-step spans
 // less than one map layer (so a pass touches at most three layers); else 0.

@@ -125,3 +125,12 @@ def test_heat_deposits_agree_between_the_schedules(monkeypatch):
     assert q_s.sum() > 0
     assert np.abs(q_s - q_t).max() <= 2e-5 * np.abs(q_t).max()
     assert abs(q_s.sum() / q_t.sum() - 1) < 1e-5
+
+
+@pytest.mark.parametrize("n", [16, 64, 256, 512])
+def test_column_layout_pass_in_128_thread_ctas(n, monkeypatch):
+    """SHG_FFT_VARIANT=3 forces the column-layout pass in 128-thread CTAs (half
+    the columns per CTA; lengths up to 512), which the tuner may also pick."""
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+    monkeypatch.setenv("SHG_FFT_VARIANT", "3")
+    _check(W.depleted_absorbing(n=n, nz=5, tgrid=(9, 7, 4), p1=400.0))
