@@ -162,6 +162,15 @@ template <int R, int DIR, class C> SHG_D void dft_reg(C (&u)[R]) {
 // TL = N > 0: copies in shared memory, twiddles W_N^k, k < N (so that
 // streamed tiles cannot evict them from L1).
 template <int TL> constexpr int tab_len() { return TL == 0 ? 1024 : TL; }
+
+// Position of twiddle k in a shared table (TL > 0).  A stage reads entries
+// jm r (times a stride) with jm = 0 .. NS-1 across the lanes of a row group;
+// for even r those fall into a few of the eight 16-byte bank groups of a
+// 128-byte shared-memory row ((hi, lo) pairs are 16 bytes), up to 8 ways for
+// r = 8.  XOR-ing bits 0-2 of k with bits 3-5 spreads every such run over all
+// eight groups.  It permutes each aligned block of 64 entries (or the whole
+// table when N < 64), so the table keeps its size.
+template <int TL> SHG_HD int tw_pos(int k) { return TL == 0 ? k : (k ^ ((k >> 3) & 7)); }
 template <int TL, class P> SHG_D P ld_tab(const P* p) {
     if constexpr (TL == 0)
         return __ldg(p);
@@ -184,7 +193,7 @@ SHG_D void stage(C (&v)[E], C* sm, int t, const pt<decltype(C::x)>* __restrict__
         if (NS > 1) {
 #pragma unroll
             for (int r = 1; r < R; ++r) {
-                const auto w = ld_tab<TL>(&tw[jm * r * (tab_len<TL>() / (NS * R))]);
+                const auto w = ld_tab<TL>(&tw[tw_pos<TL>(jm * r * (tab_len<TL>() / (NS * R)))]);
                 u[r] = DIR < 0 ? pmul(u[r], w) : pmulc(u[r], w);
                 // bound the number of (hi, lo) twiddles the compiler keeps in
                 // flight: without this it hoists them all and spills
@@ -263,7 +272,7 @@ template <class RT, int N>
 SHG_D void stage_tables(pt<RT>* twS, pt<RT>* pS, const pt<RT>* tw, const pt<RT>* p) {
     for (int k = threadIdx.x; k < 3 * N; k += blockDim.x) {
         if (k < N)
-            cp_async(&twS[k], &tw[k * (1024 / N)]);
+            cp_async(&twS[tw_pos<N>(k)], &tw[k * (1024 / N)]);
         else
             cp_async(&pS[k - N], &p[k - N]);
     }

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     const Inst3<R>& qg = qs[blockIdx.y];
     for (int k = threadIdx.x; k < 4 * NX; k += kPassThreads) {
         if (k < NX)
-            cp_async(&twS[k], &tw[k * (1024 / NX)]);
+            cp_async(&twS[tw_pos<NX>(k)], &tw[k * (1024 / NX)]);
         else
             cp_async(&pS[k - NX], &qg.d.px[k - NX]);
     }
@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     const bool active = x < nx;
     for (int k = threadIdx.x; k < 4 * NY; k += kPassThreads) {
         if (k < NY)
-            cp_async(&twS[k], &tw[k * (1024 / NY)]);
+            cp_async(&twS[tw_pos<NY>(k)], &tw[k * (1024 / NY)]);
         else
             cp_async(&pS[k - NY], &d.py[k - NY]);
     }
