@@ -13,6 +13,7 @@ namespace shg {
 #define SHG_F32_SMALL_COL_SIZES(X) X(8) X(16) X(32) X(64) X(128) X(256) X(512)
 
 bool has_col_step_small_f32(int n) { return n >= 8 && n <= 512; }
+bool has_col_step_wide_f32(int n) { return n == 512 || n == 1024; }
 
 // v: the row flavour (0, 1, 3, 4) without the row-pass bits.
 cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
@@ -50,10 +51,17 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
     return cudaErrorInvalidValue;
 }
 
-// v: 3 for 128-thread CTAs (lengths up to 512: half the columns per CTA), else
-// 256-thread CTAs.
+// v: 3 for 128-thread CTAs (lengths up to 512: half the columns per CTA), 5
+// for 512-thread CTAs (lengths 512 and 1024: twice the columns, so that a
+// warp reads whole 32-byte sectors of each row), else 256-thread CTAs.
 cudaError_t col_f32_step(int ny, int v, const void* descs, int ninst, int nx, int nz, int s,
                          const void* tw, int hy, cudaStream_t st) {
+    if (v == 5) {
+        switch (ny) {
+            case 512: return col_step_launch<512, 512>(descs, ninst, nx, nz, s, tw, hy, st);
+            case 1024: return col_step_launch<1024, 512>(descs, ninst, nx, nz, s, tw, hy, st);
+        }
+    }
     if (v == 3) {
         switch (ny) {
 #define X(n) case n: return col_step_launch<n, 128>(descs, ninst, nx, nz, s, tw, hy, st);
@@ -80,6 +88,8 @@ cudaError_t attr_f32_step() {
     if (e == cudaSuccess) e = col_step_attr<n, 128>();
     SHG_F32_SMALL_COL_SIZES(X)
 #undef X
+    if (e == cudaSuccess) e = col_step_attr<512, 512>();
+    if (e == cudaSuccess) e = col_step_attr<1024, 512>();
 #define X(n)                                                                           \
     if (e == cudaSuccess) e = row_attr<float, n, 1, true, kPassThreads, false, true>(); \
     if (e == cudaSuccess) e = row_attr<float, n, 0, true, 128, false, true>();          \

@@ -134,3 +134,12 @@ def test_column_layout_pass_in_128_thread_ctas(n, monkeypatch):
     monkeypatch.setenv("SHG_CLUSTER", "0")
     monkeypatch.setenv("SHG_FFT_VARIANT", "3")
     _check(W.depleted_absorbing(n=n, nz=5, tgrid=(9, 7, 4), p1=400.0))
+
+
+@pytest.mark.parametrize("n,nz", [(512, 4), (1024, 3)])
+def test_column_layout_pass_in_512_thread_ctas(n, nz, monkeypatch):
+    """SHG_FFT_VARIANT=5 forces the column-layout pass in 512-thread CTAs
+    (lengths 512 and 1024: twice the columns per CTA)."""
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+    monkeypatch.setenv("SHG_FFT_VARIANT", "5")
+    _check(W.depleted_absorbing(n=n, nz=nz, tgrid=(9, 7, 3), p1=400.0))
