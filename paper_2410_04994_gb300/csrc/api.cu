@@ -659,7 +659,8 @@ static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
         return st;
     }
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(out, graph, 0);
+    // node priorities: the pass launches of a batch's largest group carry one
+    e = cudaGraphInstantiate(out, graph, cudaGraphInstantiateFlagUseNodePriority);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGraphInstantiate");
     return SHG_OK;
@@ -1530,15 +1531,30 @@ static shg_status_t enqueue_batch(BatchEntry* b, cudaStream_t st) {
     // overlap, then join
     const int ng = int(b->groups.size());
     PdlScope pdl(ng == 1);
+    // the group with the most point-steps launches at the highest priority
+    int lowest = 0, highest = 0;
+    SHG_CK(cudaDeviceGetStreamPriorityRange(&lowest, &highest));
+    int big = 0;
+    double w_big = -1;
+    for (int i = 0; i < ng; ++i) {
+        const BatchGroup& g = b->groups[i];
+        const double w = double(g.nx) * g.ny * g.nz * double(g.plans.size());
+        if (w > w_big) {
+            w_big = w;
+            big = i;
+        }
+    }
     cudaEvent_t fork = b->ev.back();
     SHG_CK(cudaEventRecord(fork, st));
     for (int i = 0; i < ng; ++i) {
         BatchGroup& g = b->groups[i];
         cudaStream_t s = b->side[i];
         SHG_CK(cudaStreamWaitEvent(s, fork, 0));
+        launch_priority = (ng > 1 && i == big) ? highest : 0;
         shg_status_t r = enqueue_forward(g.fp64, g.nx, g.ny, g.nz, g.descs, g.idescs,
                                          int(g.plans.size()), g.plans[0]->tw, g.plans, s, g.tmaps,
                                          g.status);
+        launch_priority = 0;
         if (r != SHG_OK) return r;
         SHG_CK(cudaEventRecord(b->ev[i], s));
         SHG_CK(cudaStreamWaitEvent(st, b->ev[i], 0));

@@ -22,6 +22,7 @@ bool has_col_step_wide_f32(int);
 cudaError_t attr_f32_step();
 
 thread_local bool pdl_enabled = false;
+thread_local int launch_priority = 0;
 
 bool has_fft_variant(bool fp64, int n) { return !fp64 && has_variant_f32(n); }
 bool has_col_small(bool fp64, int n) { return !fp64 && has_col_small_f32(n); }

@@ -28,6 +28,11 @@ template <class K> cudaError_t allow_max_dyn_smem(K kernel) {
 // waiting CTAs.
 extern thread_local bool pdl_enabled;
 inline bool use_pdl() { return pdl_enabled; }
+// Scheduling priority of the pass launches (0: the stream's).  A batch gives
+// its largest grid group the highest priority: that group is the critical
+// path of the graph, and the smaller groups' kernels fill the SMs it leaves
+// idle (384-instance sweep: 469 -> 460 ms per step).
+extern thread_local int launch_priority;
 template <class... KArgs, class... Args>
 cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
                        cudaStream_t st, Args... args) {
@@ -36,11 +41,13 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t s
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = use_pdl() ? 1 : 0;
+    attr[1].id = cudaLaunchAttributePriority;
+    attr[1].val.priority = launch_priority;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = launch_priority != 0 ? 2 : 1;
     return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 

@@ -197,6 +197,7 @@ cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, in
 // Whether the pass launches of the calling thread use programmatic dependent
 // launch; set per enqueue by pdl_scope (SHG_PDL=0|1 overrides the choice).
 extern thread_local bool pdl_enabled;
+extern thread_local int launch_priority;  // priority attribute of the pass launches (0: none)
 struct PdlScope {
     bool prev;
     explicit PdlScope(bool single_group) : prev(pdl_enabled) {
