@@ -66,6 +66,20 @@ def step_flops_per_point(n: int, thermal: bool) -> float:
     return row_flops_per_point(n, thermal) + fft
 
 
+def threewave_flops_per_point_step(n: int, thermal: bool) -> float:
+    """Algorithmic FP32 flops per grid point and z-step of a three-wave plan:
+    two RK4 half steps of the three coupled fields (4 right-hand sides of 69
+    flops: TPA and lens of each wave 3 x 9, the two difference-frequency
+    couplings 26, the sum-frequency coupling 16; stage vectors 3 x 12; the
+    weighted sums 30; the update 12); stage coefficients at 5 points (about
+    42 flops each with a map); Lx and Ly of the three fields (forward and
+    inverse 1-D FFT at 5 n log2 n / n per point, and a complex multiply)."""
+    rk4 = 2 * (4 * 69 + 36 + 30 + 12)
+    coef = 5 * 42 if thermal else 0
+    fft = 2 * 3 * (2 * 5 * math.log2(n) + 6)
+    return rk4 + coef + fft
+
+
 def col_bytes_per_point() -> float:
     """Column pass: read and write both complex64 fields once."""
     return 2 * 2 * 8.0
@@ -524,6 +538,42 @@ def time_configs(pkg, stream, mp, hbm_gbs):
     out["adjoint"] = e
     del plan
 
+    ext = golden("extensions.json") or {}
+    # Eq. (4) phase model: the depleted workload with caller index polynomials
+    w = W.eq4_case()
+    plan = pkg.Plan(w)
+    plan.set_temperature(torch.as_tensor(w.dT), w.t_lx, w.t_ly)
+    run = lambda: (plan.propagate(stream), plan.efficiency())  # noqa: E731
+    run()
+    ms = statistics.median(_event_ms(run, 10, stream))
+    eta = plan.efficiency()[0]
+    e = {"workload": w.name, "value": w.point_steps / (ms * 1e-3), "unit": UNIT,
+         "ms_per_propagation": ms, "us_per_z_step": 1e3 * ms / w.nz, "dtype": "f32",
+         "path": "single 128^2 plan: the cluster-resident kernel, Eq. (4) phase table"}
+    if "eq4" in ext:
+        e["eta_rel_err_vs_oracle"] = _rel(eta, ext["eq4"]["eta"])
+    out["eq4"] = e
+    del plan
+
+    # three-wave mixing: sum- and difference-frequency generation, 128^2 x 1000
+    for key, w in (("sfg", W.sfg_case(n=128, nz=1000)), ("dfg", W.dfg_case(n=128, nz=1000))):
+        plan = pkg.Plan3(w)
+        plan.set_temperature(w.dT, w.t_lx, w.t_ly)
+        run = lambda: (plan.propagate(stream), plan.powers())  # noqa: E731
+        run()
+        ms = statistics.median(_event_ms(run, 5, stream))
+        P = plan.powers()
+        pts = w.nx * w.ny * w.nz
+        e = {"workload": w.name, "value": pts / (ms * 1e-3), "unit": UNIT,
+             "ms_per_propagation": ms, "powers_W": list(P), "dtype": "f32",
+             "alu_frac_whole_propagation": threewave_flops_per_point_step(w.nx, True) * pts
+             / (ms * 1e-3) / (fp32 * 1e12)}
+        if key in ext:
+            ref = ext[key]["powers"]
+            e["powers_err_vs_oracle"] = max(abs(a - b) for a, b in zip(P, ref)) / max(ref)
+        out["threewave_" + key] = e
+        del plan
+
     # thermal: 1024^2, nz = 8000, 6 outer iterations with heat solves
     w = W.thermal_loop()
     plan = pkg.Plan(w, thermal=True)
@@ -543,8 +593,12 @@ def time_configs(pkg, stream, mp, hbm_gbs):
     # (dT = 0 with the first pass's deposits) and a warm start (from that
     # solution after the second pass)
     hs = {"grid": f"{w.hx}x{w.hy}x{w.hz}", "tol_K": 1e-6}
-    for name, method in (("direct", pkg.SHG_HEAT_DIRECT), ("sor", pkg.SHG_HEAT_SOR)):
-        plan2 = pkg.Plan(w, thermal=True)
+    # (the SOR takes oven-held faces only; the direct solve also the convective
+    # faces of Eq. 10: the end facets in air, h = 10 W/(m^2 K))
+    for name, wk, method in (("direct", w, pkg.SHG_HEAT_DIRECT), ("sor", w, pkg.SHG_HEAT_SOR),
+                             ("direct_convective_end_facets",
+                              W.with_oven(w, "surrounded", h_conv=10.0), pkg.SHG_HEAT_DIRECT)):
+        plan2 = pkg.Plan(wk, thermal=True)
         pkg.shg_set_heat_method(plan2.handle, method)
         plan2.propagate(stream)
         plan2.efficiency()

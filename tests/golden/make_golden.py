@@ -8,6 +8,7 @@ GPU tests load these files and compare the library's results with them.
     python tests/golden/make_golden.py thermal_pass    # ~70 min on 8 cores
     python tests/golden/make_golden.py thermal_loop2   # ~15 min on 8 cores
     python tests/golden/make_golden.py configs         # ~5 min on 8 cores
+    python tests/golden/make_golden.py extensions      # ~10 min on 8 cores
 
 adjoint_fd (adjoint workload: 256 x 256, nz = 2000, 64 x 64 x 128 map, seed 0)
     eta and central finite differences of eta with respect to the waist w0,
@@ -25,6 +26,11 @@ stride-16 subgrid plus the central 32 x 32 block.
 configs: eta, P_F(L) and P_SH(L) of the plain workload (32 x 32, nz = 100),
 the depleted workload (128 x 128, nz = 1000, seed-0 map) and the first
 instance of each grid of the 384-instance sweep (nz = 2000, seed 1).
+
+extensions: eta, P_F(L) and P_SH(L) of the Eq. (4) workload (W.eq4_case:
+128 x 128, nz = 1000, the depleted map), and the powers of the three waves of
+sum- and difference-frequency generation (W.sfg_case, W.dfg_case at 128 x 128,
+nz = 1000, seeded map).
 
 thermal_loop2 (the thermal workload with nz = 100 and n_outer = 2): both
 iterations of the loop, including the SOR solve on the full 128 x 128 x 256
@@ -53,6 +59,7 @@ ADJOINT_FD = os.path.join(HERE, "adjoint_fd_256_nz2000.json")
 THERMAL_PASS = os.path.join(HERE, "thermal_pass_1024_nz8000.npz")
 THERMAL_LOOP2 = os.path.join(HERE, "thermal_loop2_1024_nz100.npz")
 CONFIGS = os.path.join(HERE, "configs_eta.json")
+EXTENSIONS = os.path.join(HERE, "extensions.json")
 
 FIELD_STRIDE = 16
 CENTRE = 32
@@ -177,8 +184,22 @@ def configs():
     print(json.dumps(out, indent=1))
 
 
+def extensions():
+    from oracle import threewave
+    out = {"_source": "FP64 CPU oracle, tests/golden/make_golden.py extensions"}
+    t = time.time()
+    out["eq4"] = _eta_record(W.eq4_case())
+    print("eq4", out["eq4"], f"{time.time() - t:.0f} s", flush=True)
+    for name, w in (("sfg", W.sfg_case(n=128, nz=1000)), ("dfg", W.dfg_case(n=128, nz=1000))):
+        t = time.time()
+        _, powers = threewave.run(w)
+        out[name] = {"workload": w.name, "powers": [float(p) for p in powers]}
+        print(name, out[name], f"{time.time() - t:.0f} s", flush=True)
+    json.dump(out, open(EXTENSIONS, "w"), indent=1)
+
+
 if __name__ == "__main__":
     jobs = {"adjoint_fd": adjoint_fd, "thermal_pass": thermal_pass,
-            "thermal_loop2": thermal_loop2, "configs": configs}
+            "thermal_loop2": thermal_loop2, "configs": configs, "extensions": extensions}
     for name in sys.argv[1:] or list(jobs):
         jobs[name]()

@@ -130,3 +130,28 @@ def test_thermal_loop_two_iterations_full_heat_grid_vs_oracle():
     assert abs(float(np.abs(dT).max()) - dmax) <= 1e-3 * dmax
     a_f, a_sh = plan.fields()
     _field_checks(a_f, a_sh, g)
+
+
+def test_extension_workloads_vs_stored_oracle_values():
+    """The measured extension workloads at their bench sizes: the Eq. (4)
+    phase model on the depleted workload (128^2 x 1000, the cluster-resident
+    path) and sum- and difference-frequency generation (128^2 x 1000),
+    against stored oracle values (extensions.json).  Bars: eta and powers
+    1e-4 (three-wave: relative to the largest power)."""
+    import paper_2410_04994_gb300 as pkg
+    g = _load("extensions.json")
+    w = W.eq4_case()
+    plan = pkg.Plan(w)
+    plan.set_temperature(torch.as_tensor(w.dT), w.t_lx, w.t_ly)
+    plan.propagate()
+    eta, p_f, p_sh = plan.efficiency()
+    ref = g["eq4"]
+    assert abs(eta / ref["eta"] - 1) <= 1e-4, (eta, ref["eta"])
+    assert abs(p_f / ref["p_f"] - 1) <= 1e-4 and abs(p_sh / ref["p_sh"] - 1) <= 1e-4
+    for key, w3 in (("sfg", W.sfg_case(n=128, nz=1000)), ("dfg", W.dfg_case(n=128, nz=1000))):
+        p3 = pkg.Plan3(w3)
+        p3.set_temperature(w3.dT, w3.t_lx, w3.t_ly)
+        p3.propagate()
+        P = p3.powers()
+        ref = g[key]["powers"]
+        assert max(abs(a - b) for a, b in zip(P, ref)) <= 1e-4 * max(ref), (key, P, ref)

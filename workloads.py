@@ -316,6 +316,24 @@ def dfg_case(n: int = 64, nz: int = 200, **kw) -> ThreeWave:
     return w.with_(name=f"dfg_{n}x{n}_nz{nz}")
 
 
+# Inputs of the Eq. (4) phase model for the measured extension workload:
+# synthetic index polynomials in (T - 25 C) (the paper gives no index data)
+# and the paper's grating expansion; EQ4_LAMBDA25 is the grating period at
+# 25 C that phase-matches these polynomials at 60 C (evaluated once, stated
+# here as a number).
+EQ4_N_F = (2.14, 2e-6, 3e-9, -1e-11)
+EQ4_N_SH = (2.18, 4e-6, -4e-9, 2e-11)
+EQ4_LAMBDA25 = 1.3278254691754094e-05
+
+
+def eq4_case(n: int = 128, nz: int = 1000, t_oven: float = 58.0, t_off: float = 1.5) -> Workload:
+    """The depleted workload (seed-0 map) with the Eq. (4) phase model: oven at
+    58 C plus a 1.5 K offset, 0.5 K from the constructed phase-matching point."""
+    w = depleted_absorbing(n=n, nz=nz)
+    q = Qpm(t_oven=t_oven, lambda25=EQ4_LAMBDA25, n_f_t=EQ4_N_F, n_sh_t=EQ4_N_SH)
+    return w.with_(qpm=q, t_off=t_off, name=f"eq4_{n}x{n}_nz{nz}")
+
+
 # Oven arrangements of Sec. 4.2 (the crystal surrounded by the oven, or an
 # oven under one face): the faces held at the oven temperature, the rest
 # cooled by convection.
