@@ -668,7 +668,9 @@ static shg_status_t capture(cudaStream_t cap, Fn fn, cudaGraphExec_t* out) {
 
 static shg_status_t plan_forward(shg_plan* p, cudaStream_t st) {
     if (p->w3) {
-        // three-wave mixing: its own passes, captured into the plan's graph
+        // three-wave mixing: its own passes, captured into the plan's graph,
+        // with programmatic dependent launch between them
+        PdlScope pdl(true);
         auto body3 = [&](cudaStream_t q) { return enqueue_forward3(p, q); };
         if (!use_graphs()) return body3(st);
         if (!p->gvalid) {

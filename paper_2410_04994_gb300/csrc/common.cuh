@@ -182,7 +182,10 @@ template <class C> SHG_D void cp_async_stream(C* smem_dst, const C* gsrc, uint64
 // next kernel of the stream be scheduled now (its prologue overlaps this
 // kernel's tail); pdl_wait blocks until the previous kernel of the stream has
 // completed and its writes are visible.  Both are no-ops for a kernel
-// launched without the programmatic-serialisation attribute.
+// launched without the programmatic-serialisation attribute.  The passes
+// stage their constant tables, wait, and trigger only then, so that at most
+// the next pass's CTAs sit resident and waiting: a trigger at kernel entry lets
+// the CTAs of several later passes pile up on the SMs.
 SHG_D void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 SHG_D void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 

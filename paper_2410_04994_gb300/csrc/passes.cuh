@@ -149,7 +149,6 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     // shared copies of the twiddles and of the row factors of both fields
     pt<R>* twS = reinterpret_cast<pt<R>*>(smem_raw + G::fields + (UM ? slot_bytes<R, NTH>() : 0));
     pt<R>* pS = twS + NX;
-    pdl_trigger();
     {
         // constant tables first: they do not depend on the previous kernel
         const InstDesc<R>& dg = descs[blockIdx.y];
@@ -160,6 +159,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
         pdl_wait();  // the fields are the previous pass's output
+        pdl_trigger();
         C* rowF = dg.field + size_t(y) * NX;
         C* rowS = dg.field + (size_t(ny) + y) * NX;
         if (active) {
@@ -418,9 +418,9 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = blockIdx.x * TILE + c;
     const bool active = x < nx;
-    pdl_trigger();
     stage_tables<R, NY>(twS, pS, tw, descs[blockIdx.y].py);  // independent of the previous pass
     pdl_wait();
+    pdl_trigger();
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
         if (active) {
@@ -492,7 +492,6 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
     const bool dep = descs[blockIdx.y].Q != nullptr;
     const int nb = dep ? TILE * descs[blockIdx.y].hy : 0;
     for (int i = threadIdx.x; i < nb; i += NTH) bins[i] = 0.f;
-    pdl_trigger();
     {
         const InstDesc<float>& dg = descs[blockIdx.y];
         stage_tables<float, NY>(twS, pS, tw, dg.py);
@@ -502,6 +501,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
             zsh[threadIdx.x] = stage_z(dg, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
         }
         pdl_wait();  // the fields are the previous pass's output
+        pdl_trigger();
         if (active) {
 #pragma unroll
             for (int f = 0; f < 2; ++f) {
@@ -694,7 +694,6 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     uint64_t* bar = reinterpret_cast<uint64_t*>(pS + 2 * NY);
     const InstDesc<float>& d = descs[blockIdx.y];
     const int x0 = blockIdx.x * TILE;
-    pdl_trigger();
     if (threadIdx.x == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -703,6 +702,7 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     stage_tables<float, NY>(twS, pS, tw, d.py);  // independent of the previous pass
     __syncthreads();
     pdl_wait();
+    pdl_trigger();
     if (threadIdx.x == 0) {
         // one barrier per field, so that field 0 is transformed while field 1 lands
         const CUtensorMap* tm = tmaps + blockIdx.y;

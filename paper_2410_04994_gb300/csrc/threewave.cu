@@ -5,6 +5,7 @@
 #include <mutex>
 #include <vector>
 
+#include "launch_passes.cuh"
 #include "plan.h"
 #include "threewave.cuh"
 
@@ -154,18 +155,16 @@ static cudaError_t row3(const void* q, int ninst, int ny, int nz, int s, const v
                         cudaStream_t st) {
     using G = Row3Geom<R, N>;
     dim3 grid((ny + G::ROWS - 1) / G::ROWS, ninst);
-    k_row3<R, N><<<grid, kPassThreads, G::smem, st>>>(static_cast<const Inst3<R>*>(q), ny, nz, s,
-                                                     static_cast<const pt<R>*>(tw));
-    return cudaGetLastError();
+    return launch_pdl(k_row3<R, N>, grid, dim3(nth3<R, N>()), G::smem, st,
+                      static_cast<const Inst3<R>*>(q), ny, nz, s, static_cast<const pt<R>*>(tw));
 }
 
 template <class R, int N>
 static cudaError_t col3(const void* q, int ninst, int nx, const void* tw, cudaStream_t st) {
     using G = Col3Geom<R, N>;
     dim3 grid((nx + G::TILE - 1) / G::TILE, ninst);
-    k_col3<R, N><<<grid, kPassThreads, G::smem, st>>>(static_cast<const Inst3<R>*>(q), nx,
-                                                     static_cast<const pt<R>*>(tw));
-    return cudaGetLastError();
+    return launch_pdl(k_col3<R, N>, grid, dim3(nth3<R, N>()), G::smem, st,
+                      static_cast<const Inst3<R>*>(q), nx, static_cast<const pt<R>*>(tw));
 }
 
 static cudaError_t launch_row3(bool fp64, int nx, const void* q, int ny, int nz, int s,

@@ -116,21 +116,29 @@ SHG_D void rk4_3(const Inst3<R>& q, cx<R> (&A)[3], const Coef3<R>& c0, const Coe
     }
 }
 
-template <class R, int N> struct Row3Geom {
+// Block size of the three-wave passes: 64 threads for transform groups of at
+// most 16 threads, so that a single instance spreads over four times as many
+// CTAs as with 256 (a 128^2 instance: 16 instead of 4) while a column tile
+// still spans a whole 32-byte sector per row (TILE >= 4); else 256.
+template <class R, int N> constexpr int nth3() {
+    return FftCfg<R, N, 0>::T <= 16 ? 64 : kPassThreads;
+}
+
+template <class R, int N, int NTH = nth3<R, N>()> struct Row3Geom {
     using F = FftCfg<R, N, 0>;
     static constexpr int T = F::T;
-    static constexpr int ROWS = kPassThreads / T;
+    static constexpr int ROWS = NTH / T;
     static constexpr int S = padded_len<R>(N, T < Bank<R>::W ? T : 1);
     static constexpr size_t fields = size_t(3) * ROWS * S * sizeof(cx<R>);
     static constexpr size_t smem = fields + size_t(4) * N * sizeof(pt<R>);  // twiddles + 3 rows
 };
 
 // Row pass R(s) of the three fields.  grid = (ceil(ny / ROWS), instances).
-template <class R, int NX>
-__global__ void __launch_bounds__(kPassThreads, 1)
+template <class R, int NX, int NTH = nth3<R, NX>()>
+__global__ void __launch_bounds__(NTH, 1)
     k_row3(const Inst3<R>* __restrict__ qs, int ny, int nz, int s, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = Row3Geom<R, NX>;
+    using G = Row3Geom<R, NX, NTH>;
     constexpr int E = FftCfg<R, NX, 0>::E, T = G::T, ROWS = G::ROWS, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Inst3<R> qsh;
@@ -142,7 +150,7 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     const int y = blockIdx.x * ROWS + lr;
     const bool active = y < ny;
     const Inst3<R>& qg = qs[blockIdx.y];
-    for (int k = threadIdx.x; k < 4 * NX; k += kPassThreads) {
+    for (int k = threadIdx.x; k < 4 * NX; k += NTH) {
         if (k < NX)
             cp_async(&twS[tw_pos<NX>(k)], &tw[k * (1024 / NX)]);
         else
@@ -153,6 +161,8 @@ __global__ void __launch_bounds__(kPassThreads, 1)
         const int q = 4 * s - 2 + threadIdx.x;
         zsh[threadIdx.x] = stage_z(qg.d, q < 0 ? 0 : (q > 4 * nz ? 4 * nz : q));
     }
+    pdl_wait();  // the fields are the previous pass's output
+    pdl_trigger();
     if (active) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
@@ -213,21 +223,21 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     }
 }
 
-template <class R, int N> struct Col3Geom {
+template <class R, int N, int NTH = nth3<R, N>()> struct Col3Geom {
     using F = FftCfg<R, N, 0>;
     static constexpr int T = F::T;
-    static constexpr int TILE = kPassThreads / T;
+    static constexpr int TILE = NTH / T;
     static constexpr int S = padded_len<R>(N, TILE < Bank<R>::W ? Bank<R>::W / TILE : 1);
     static constexpr size_t fields = size_t(3) * TILE * S * sizeof(cx<R>);
     static constexpr size_t smem = fields + size_t(4) * N * sizeof(pt<R>);
 };
 
 // Column pass C(s) of the three fields.  grid = (ceil(nx / TILE), instances).
-template <class R, int NY>
-__global__ void __launch_bounds__(kPassThreads, 1)
+template <class R, int NY, int NTH = nth3<R, NY>()>
+__global__ void __launch_bounds__(NTH, 1)
     k_col3(const Inst3<R>* __restrict__ qs, int nx, const pt<R>* __restrict__ tw) {
     using C = cx<R>;
-    using G = Col3Geom<R, NY>;
+    using G = Col3Geom<R, NY, NTH>;
     constexpr int E = FftCfg<R, NY, 0>::E, T = G::T, TILE = G::TILE, S = G::S;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     C* smem = reinterpret_cast<C*>(smem_raw);
@@ -238,12 +248,14 @@ __global__ void __launch_bounds__(kPassThreads, 1)
     const int c = threadIdx.x % TILE, t = threadIdx.x / TILE;
     const int x = blockIdx.x * TILE + c;
     const bool active = x < nx;
-    for (int k = threadIdx.x; k < 4 * NY; k += kPassThreads) {
+    for (int k = threadIdx.x; k < 4 * NY; k += NTH) {
         if (k < NY)
             cp_async(&twS[tw_pos<NY>(k)], &tw[k * (1024 / NY)]);
         else
             cp_async(&pS[k - NY], &d.py[k - NY]);
     }
+    pdl_wait();  // the fields are the previous pass's output
+    pdl_trigger();
     if (active) {
 #pragma unroll
         for (int f = 0; f < 3; ++f) {
