@@ -565,7 +565,10 @@ def time_configs(pkg, stream, mp, hbm_gbs):
         P = plan.powers()
         pts = w.nx * w.ny * w.nz
         e = {"workload": w.name, "value": pts / (ms * 1e-3), "unit": UNIT,
-             "ms_per_propagation": ms, "powers_W": list(P), "dtype": "f32",
+             "ms_per_propagation": ms, "us_per_z_step": 1e3 * ms / w.nz,
+             "path": "single 128^2 plan: the cluster-resident three-wave kernel, map through "
+                     "the per-point table",
+             "powers_W": list(P), "dtype": "f32",
              "alu_frac_whole_propagation": threewave_flops_per_point_step(w.nx, True) * pts
              / (ms * 1e-3) / (fp32 * 1e12)}
         if key in ext:

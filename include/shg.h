@@ -409,7 +409,13 @@ typedef struct {
  * monitor, phase model, adjoint, heat, batches, pass timing) return
  * SHG_ERR_INVALID_ARG or SHG_ERR_STATE.  SHG_ERR_INVALID_ARG for a non-finite
  * value, a non-positive length, wavelength, index or waist, a negative
- * power, no input power, or another flag. */
+ * power, no input power, or another flag.
+ * Propagation: FP32 plans on a 64 x 64 or 128 x 128 grid run the whole
+ * z-march in one thread-block-cluster launch (the fields resident in the
+ * cluster's shared memory; a map through the per-point table, when one step
+ * spans less than one map layer); other plans run a row pass and a column
+ * pass per step (the map sampled at its nodes).  SHG_CLUSTER=0 in the
+ * environment selects the passes for every plan. */
 shg_status_t shg_plan_create_3w(const shg_grid_t *grid, const shg_crystal3_t *crystal,
                                 const shg_beams3_t *beams, int flags, shg_plan_t **out);
 

@@ -14,7 +14,7 @@ LIB = os.path.join(HERE, "libshg.so")
 
 SOURCES = ["api.cu", "aux.cu", "passes_f32.cu", "passes_f32_lean.cu", "passes_f32_step.cu", "passes_f64.cu", "adjoint.cu", "adjoint_f32.cu",
            "adjoint_f64.cu", "heat.cu", "heat_direct.cu", "noalloc.cu", "peaks.cu",
-           "cluster_f32.cu", "threewave.cu"]
+           "cluster_f32.cu", "cluster3_f32.cu", "threewave.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

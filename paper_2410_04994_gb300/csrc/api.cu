@@ -1241,8 +1241,13 @@ shg_status_t shg_plan_create_3w(const shg_grid_t* grid, const shg_crystal3_t* c,
     b2.z_focus = b->z_focus[0];
     b2.t_oven_offset = b->t_oven_offset;
     b2.undepleted = b->undepleted;
+    // FP32 square grids with a cluster-resident kernel read the map through the
+    // per-point table; the streaming three-wave passes sample it at its nodes
+    // (cluster3_size also sets that kernel's attributes, outside any capture)
+    const bool c3 = !(flags & SHG_FLAG_FP64) && grid->nx == grid->ny && cluster3_size(grid->nx) > 0;
     shg_plan_t* p = nullptr;
-    shg_status_t st = shg_plan_create(grid, &c2, &b2, flags | SHG_FLAG_NODE_SAMPLER, &p);
+    shg_status_t st =
+        shg_plan_create(grid, &c2, &b2, flags | (c3 ? 0 : SHG_FLAG_NODE_SAMPLER), &p);
     if (st != SHG_OK) return st;
     auto fail = [&](shg_status_t s2) {
         shg_plan_destroy(p);

@@ -220,6 +220,10 @@ bool cluster_path(const std::vector<shg_plan*>& plans);
 int cluster_size(int n);
 cudaError_t launch_cluster(int n, const void* descs, int ninst, int nz, const void* tw,
                            cudaStream_t st);
+// The cluster-resident three-wave propagation (FP32, N = 64, 128; single plans).
+bool cluster3_path(const shg_plan* p);
+int cluster3_size(int n);
+cudaError_t launch_cluster3(int n, const void* q, int nz, const void* tw, cudaStream_t st);
 
 // Three-wave plans (threewave.cu).
 shg_status_t three_wave_alloc(shg_plan* p, const shg_crystal3_t* c, const shg_beams3_t* b);

@@ -353,8 +353,8 @@ shg_status_t three_wave_alloc(shg_plan* p, const shg_crystal3_t* c, const shg_be
     return SHG_OK;
 }
 
-// The whole three-wave propagation of one plan on `st`: initial fields,
-// 2 nz + 1 passes, powers.
+// The whole three-wave propagation of one plan on `st`: initial fields, the
+// cluster-resident kernel (one launch) or 2 nz + 1 passes, powers.
 shg_status_t enqueue_forward3(shg_plan* p, cudaStream_t st) {
     const int nx = p->g.nx, ny = p->g.ny, nz = p->g.nz;
     const Init3 d = make_init3(p);
@@ -366,9 +366,13 @@ shg_status_t enqueue_forward3(shg_plan* p, cudaStream_t st) {
         k_init3_write<float><<<kRedBlocks, kRed3Threads, 0, st>>>(
             d, static_cast<float2*>(p->field), nx, ny);
     SHG_CK(cudaGetLastError());
-    for (int s = 0; s <= nz; ++s) {
-        SHG_CK(launch_row3(p->fp64, nx, p->w3->q, ny, nz, s, p->tw, st));
-        if (s < nz) SHG_CK(launch_col3(p->fp64, ny, p->w3->q, nx, p->tw, st));
+    if (cluster3_path(p)) {
+        SHG_CK(launch_cluster3(nx, p->w3->q, nz, p->tw, st));
+    } else {
+        for (int s = 0; s <= nz; ++s) {
+            SHG_CK(launch_row3(p->fp64, nx, p->w3->q, ny, nz, s, p->tw, st));
+            if (s < nz) SHG_CK(launch_col3(p->fp64, ny, p->w3->q, nx, p->tw, st));
+        }
     }
     if (p->fp64)
         k_power3_partial<double><<<kRedBlocks, kRed3Threads, 0, st>>>(

@@ -103,3 +103,34 @@ def test_three_wave_plans_refuse_shg_only_calls():
         pkg.shg_plan_create_3w(*pkg.structs3_from(w.with_(p=(0.0, 0.0, 0.0))))
     with pytest.raises(pkg.ShgError):
         pkg.shg_plan_create_3w(*pkg.structs3_from(w), pkg.SHG_FLAG_THERMAL)
+
+
+@pytest.mark.parametrize("case,n,nz", [("sfg", 64, 41), ("sfg", 128, 40), ("dfg", 128, 33),
+                                       ("dfg", 64, 48)])
+def test_cluster_resident_path_matches_oracle(case, n, nz):
+    """Single FP32 plans of 64^2 and 128^2 whose map layers one step does not
+    outrun (nz >= tz) run the whole z-march in one cluster launch; odd and
+    even nz end in either layout.  Walk-off, a phase offset and the map."""
+    mk = W.sfg_case if case == "sfg" else W.dfg_case
+    w = mk(n=n, nz=nz).with_(walkoff=(1e-3, -2e-3, 3e-3), dk0=30.0, t_off=0.3)
+    _check(w, 1e-4)
+
+
+@pytest.mark.parametrize("n", [64, 128])
+def test_cluster_resident_path_without_map_and_undepleted(n):
+    _check(W.sfg_case(n=n, nz=25, with_map=False), 1e-4)
+    _check(W.sfg_case(n=n, nz=25, with_map=False).with_(undepleted=True), 1e-4)
+
+
+def test_cluster_resident_path_equals_the_passes(monkeypatch):
+    """The same plan through the cluster kernel and through the row and
+    column passes (SHG_CLUSTER=0): the same arithmetic in another rounding
+    order (L applied as Lx Ly or Ly Lx; the map through the per-point table
+    or sampled at its nodes)."""
+    w = W.sfg_case(n=128, nz=200)
+    _, P_c, A_c = _gpu(w)
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+    _, P_p, A_p = _gpu(w)
+    for j in range(3):
+        assert abs(P_c[j] / P_p[j] - 1) < 2e-5, (j, P_c[j], P_p[j])
+        assert float((A_c[j] - A_p[j]).norm()) <= 2e-5 * float(A_p[j].norm())
