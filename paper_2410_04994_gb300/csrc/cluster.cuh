@@ -144,8 +144,8 @@ __global__ void __launch_bounds__(ClusterGeom<N, K>::NT, 1)
         float2 v[E];
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = line[pidx<float>(t + T * m)];
-        __syncthreads();  // the transform's exchanges reuse the buffer
-        fft_mul_ifft<float, N, V, N>(v, line, t, twS, fac + gf * N);
+        group_sync<true>();  // the exchanges reuse the line (a line's threads share a warp)
+        fft_mul_ifft<float, N, V, N, true>(v, line, t, twS, fac + gf * N);
 #pragma unroll
         for (int m = 0; m < E; ++m) line[pidx<float>(t + T * m)] = v[m];
     };

@@ -218,32 +218,44 @@ template <int E, int T, class C> SHG_D void reload(C (&v)[E], const C* sm, int t
     for (int m = 0; m < E; ++m) v[m] = sm[pidx<RT>(t + T * m)];
 }
 
+// Barrier between the exchanges of a transform group.  WS: the group's
+// threads are consecutive and lie within one warp (T <= 32, group = thread
+// index / T), so the warp barrier orders its shared-memory exchanges;
+// otherwise (groups strided across warps) the block barrier.
+template <bool WS> SHG_D void group_sync() {
+    if constexpr (WS)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
 // Forward (DIR = -1) or inverse (DIR = +1, unnormalised) transform of one
-// sequence held as E registers per thread.  Every thread of the block must
-// call this (it contains __syncthreads).
-template <class RT, int N, int V, int DIR, int TL = 0, class C>
+// sequence held as E registers per thread.  Every thread of the block (WS:
+// of the warp) must call this (it contains the barriers of group_sync).
+template <class RT, int N, int V, int DIR, int TL = 0, bool WS = false, class C>
 SHG_D void fft1(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw) {
     using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
     constexpr int R0 = F::R0, R1 = F::R1, R2 = F::R2, R3 = F::R3;
     constexpr bool L0 = (F::NST == 1), L1 = (F::NST == 2), L2 = (F::NST == 3);
+    static_assert(!WS || T <= 32, "a warp-synchronous group lies within one warp");
     stage<N, E, T, R0, 1, L0, DIR, TL>(a, sa, t, tw);
     if constexpr (F::NST >= 2) {
-        __syncthreads();
+        group_sync<WS>();
         reload<E, T>(a, sa, t);
-        __syncthreads();
+        group_sync<WS>();
         stage<N, E, T, (R1 > 1 ? R1 : 2), R0, L1, DIR, TL>(a, sa, t, tw);
     }
     if constexpr (F::NST >= 3) {
-        __syncthreads();
+        group_sync<WS>();
         reload<E, T>(a, sa, t);
-        __syncthreads();
+        group_sync<WS>();
         stage<N, E, T, (R2 > 1 ? R2 : 2), R0 * R1, L2, DIR, TL>(a, sa, t, tw);
     }
     if constexpr (F::NST >= 4) {
-        __syncthreads();
+        group_sync<WS>();
         reload<E, T>(a, sa, t);
-        __syncthreads();
+        group_sync<WS>();
         stage<N, E, T, (R3 > 1 ? R3 : 2), R0 * R1 * R2, true, DIR, TL>(a, sa, t, tw);
     }
 }
@@ -254,15 +266,15 @@ SHG_D void fft1(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restr
 // the two transforms: every thread has passed the barrier that follows the
 // forward transform's last reload before any inverse store happens.  With
 // TL = N the twiddles (W_N^k) and the factors p are read from shared memory.
-template <class RT, int N, int V = 0, int TL = 0, class C>
+template <class RT, int N, int V = 0, int TL = 0, bool WS = false, class C>
 SHG_D void fft_mul_ifft(C (&a)[FftCfg<RT, N, V>::E], C* sa, int t, const pt<RT>* __restrict__ tw,
                         const pt<RT>* __restrict__ p) {
     using F = FftCfg<RT, N, V>;
     constexpr int E = F::E, T = F::T;
-    fft1<RT, N, V, -1, TL>(a, sa, t, tw);
+    fft1<RT, N, V, -1, TL, WS>(a, sa, t, tw);
 #pragma unroll
     for (int m = 0; m < E; ++m) a[m] = pmul(a[m], ld_tab<TL>(&p[t + T * m]));
-    fft1<RT, N, V, +1, TL>(a, sa, t, tw);
+    fft1<RT, N, V, +1, TL, WS>(a, sa, t, tw);
 }
 
 // Copy the twiddles W_N^k (every (1024/N)-th entry of the plan's table) and

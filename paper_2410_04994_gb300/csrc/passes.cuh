@@ -137,6 +137,10 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
     using C = cx<R>;
     using G = RowGeom<R, NX, V, NTH>;
     constexpr int E = FftCfg<R, NX, V>::E, T = G::T, ROWS = G::ROWS, S = G::S;
+    // A row's T threads are consecutive: with T <= 32 they share a warp, and
+    // everything that passes between them (staged points, transform
+    // exchanges, the nonlinear part's pairs) needs only the warp barrier.
+    constexpr bool WS = T <= 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<R> dsh;
     __shared__ StageZ<R> zsh[5];
@@ -208,14 +212,14 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             C v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
-            __syncthreads();  // the transform's exchanges reuse the buffer
-            fft_mul_ifft<R, NX, V, NX>(v, sb, t, twS, pS + f * NX);
+            group_sync<WS>();  // the transform's exchanges reuse the buffer
+            fft_mul_ifft<R, NX, V, NX, WS>(v, sb, t, twS, pS + f * NX);
             if (active) {
 #pragma unroll
                 for (int m = 0; m < E; ++m) sb[pidx<R>(t + T * m)] = v[m];
             }
         }
-        __syncthreads();  // the nonlinear part reads points other threads transformed
+        group_sync<WS>();  // the nonlinear part reads points other threads of the row transformed
     }
     const R h = R(0.5) * d.dz;
     const int l_dep = dep ? d.hlz[s] : -1;
@@ -351,7 +355,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
             sS[pidx<R>(x1)] = aS1;
         }
     }
-    __syncthreads();  // the transforms read points that other threads advanced
+    group_sync<WS>();  // the transforms read points that other threads of the row advanced
     if (mon) {
         // per-warp FP64 sums, one atomic pair per warp
         double vF = double(monF), vS = double(monS);
@@ -386,8 +390,8 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * (kPassThreads / NTH
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         if (s < nz) {
-            __syncthreads();  // the transform's first stores reuse the staging buffer
-            fft_mul_ifft<R, NX, V, NX>(v, sb, t, twS, pS + f * NX);
+            group_sync<WS>();  // the transform's first stores reuse the staging buffer
+            fft_mul_ifft<R, NX, V, NX, WS>(v, sb, t, twS, pS + f * NX);
         }
         if (active) {
 #pragma unroll

@@ -140,6 +140,7 @@ __global__ void __launch_bounds__(NTH, 1)
     using C = cx<R>;
     using G = Row3Geom<R, NX, NTH>;
     constexpr int E = FftCfg<R, NX, 0>::E, T = G::T, ROWS = G::ROWS, S = G::S;
+    constexpr bool WS = T <= 32;  // a row's threads share a warp (see k_row_pass)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ Inst3<R> qsh;
     __shared__ StageZ<R> zsh[5];
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(NTH, 1)
             for (int f = 0; f < 3; ++f) smem[(f * ROWS + lr) * S + pidx<R>(xi)] = A[f];
         }
     }
-    __syncthreads();
+    group_sync<WS>();  // the transforms read points that other threads of the row advanced
 #pragma unroll 1
     for (int f = 0; f < 3; ++f) {
         C* sb = smem + (f * ROWS + lr) * S;
@@ -213,8 +214,8 @@ __global__ void __launch_bounds__(NTH, 1)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
         if (s < nz) {
-            __syncthreads();
-            fft_mul_ifft<R, NX, 0, NX>(v, sb, t, twS, pS + f * NX);
+            group_sync<WS>();
+            fft_mul_ifft<R, NX, 0, NX, WS>(v, sb, t, twS, pS + f * NX);
         }
         if (active) {
 #pragma unroll
