@@ -451,11 +451,12 @@ static int supported_flavour(bool fp64, int n, int pass, int f) {
 static int step_key(int which, int ninst) { return 8 + which + (ninst <= kFewInstances ? 4 : 0); }
 
 // Flavour of a step kernel: which = 0, the row-layout pass (row flavours 0,
-// 1, 3, 4); which = 1, the column-layout pass (3: 128-thread CTAs, 5:
-// 512-thread CTAs, where they exist, else 0).
+// 1, 3, 4); which = 1, the column-layout pass (1: the 8-element shape, 3:
+// 128-thread CTAs, 5: 512-thread CTAs, where they exist, else 0).
 static int supported_step_flavour(bool fp64, int n, int which, int f) {
     if (which == 0) return supported_flavour(fp64, n, 0, f == 2 || f == 5 ? 0 : f);
     if (f == 5) return has_col_step_wide(n) ? 5 : 0;
+    if (f == 1) return has_col_step_v1(n) ? 1 : 0;
     return (f == 3 || f == 4) && has_col_step_small(n) ? 3 : 0;
 }
 
@@ -505,6 +506,7 @@ shg_status_t tune_group(bool fp64, int nx, int ny, int nz, const void* descs, in
         std::vector<int> cand;
         if (pass == 2) {
             cand.push_back(0);
+            if (has_col_step_v1(n)) cand.push_back(1);
             if (has_col_step_small(n)) cand.push_back(3);
             if (has_col_step_wide(n)) cand.push_back(5);
         } else {

@@ -19,6 +19,7 @@ cudaError_t row_f32_step(int, int, const void*, int, int, int, int, const void*,
 cudaError_t col_f32_step(int, int, const void*, int, int, int, int, const void*, int, cudaStream_t);
 bool has_col_step_small_f32(int);
 bool has_col_step_wide_f32(int);
+bool has_col_step_v1_f32(int);
 cudaError_t attr_f32_step();
 
 thread_local bool pdl_enabled = false;
@@ -58,6 +59,7 @@ cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz
 
 bool has_col_step_small(int n) { return has_col_step_small_f32(n); }
 bool has_col_step_wide(int n) { return has_col_step_wide_f32(n); }
+bool has_col_step_v1(int n) { return has_col_step_v1_f32(n); }
 
 cudaError_t setup_pass_attributes() {
     cudaError_t e = attr_f32();

@@ -103,20 +103,20 @@ cudaError_t col_tma_launch(const void* tmaps, const void* descs, int ninst, int 
 // The column-layout pass of the one-pass-per-step schedule (FP32).
 // Dynamic shared memory of the column-layout pass: transform buffers, table
 // prefetch slots, constant tables and the [TILE][hy] deposit bins.
-template <int N, int NTH = kPassThreads> size_t col_step_smem(int hy) {
-    using G = ColGeom<float, N, 0, NTH>;
+template <int N, int NTH = kPassThreads, int V = 0> size_t col_step_smem(int hy) {
+    using G = ColGeom<float, N, V, NTH>;
     return G::fields + slot_bytes<float, NTH>() + size_t(3) * N * sizeof(pt<float>) +
            size_t(G::TILE) * hy * sizeof(float);
 }
-template <int N, int NTH = kPassThreads> cudaError_t col_step_attr() {
-    return allow_max_dyn_smem(k_col_step<N, NTH>);
+template <int N, int NTH = kPassThreads, int V = 0> cudaError_t col_step_attr() {
+    return allow_max_dyn_smem(k_col_step<N, NTH, V>);
 }
-template <int N, int NTH = kPassThreads>
+template <int N, int NTH = kPassThreads, int V = 0>
 cudaError_t col_step_launch(const void* descs, int ninst, int nx, int nz, int s, const void* tw,
                             int hy, cudaStream_t st) {
-    using G = ColGeom<float, N, 0, NTH>;
+    using G = ColGeom<float, N, V, NTH>;
     dim3 grid((nx + G::TILE - 1) / G::TILE, ninst);
-    return launch_pdl(k_col_step<N, NTH>, grid, dim3(NTH), col_step_smem<N, NTH>(hy), st,
+    return launch_pdl(k_col_step<N, NTH, V>, grid, dim3(NTH), col_step_smem<N, NTH, V>(hy), st,
                       static_cast<const InstDesc<float>*>(descs), nx, nz, s,
                       static_cast<const pt<float>*>(tw));
 }

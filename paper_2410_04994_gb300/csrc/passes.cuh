@@ -472,14 +472,15 @@ __global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
 // fields are staged as in k_col_pass.  Pair i of a thread is the columns
 // (x0 + 2 jj, x0 + 2 jj + 1) of row y, whose table entry is
 // [l][y][x0 / 2 + jj]; it is streamed into the thread's slots one iteration
-// ahead, as in the row pass.
-template <int NY, int NTH = kPassThreads>
-__global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
+// ahead, as in the row pass.  V: the transform shape (0: 16 elements per
+// thread; 1: 8, in CTAs of which three fit per SM, with half the columns).
+template <int NY, int NTH = kPassThreads, int V = 0>
+__global__ void __launch_bounds__(NTH, MinBlocks<V>::value * kPassThreads / NTH)
     k_col_step(const InstDesc<float>* __restrict__ descs, int nx, int nz, int s,
                const pt<float>* __restrict__ tw) {
     using C = cx<float>;
-    using G = ColGeom<float, NY, 0, NTH>;
-    constexpr int E = FftCfg<float, NY, 0>::E, T = G::T, TILE = G::TILE, S = G::S;
+    using G = ColGeom<float, NY, V, NTH>;
+    constexpr int E = FftCfg<float, NY, V>::E, T = G::T, TILE = G::TILE, S = G::S;
     constexpr int NP = E / 2;  // pairs per thread
     static_assert((TILE / 2) * NY == NP * NTH, "whole pairs per thread");
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -564,7 +565,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
 #pragma unroll
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<float>(t + T * m)] : mk<C>(0.f, 0.f);
         __syncthreads();  // the transform's exchanges reuse the buffer
-        fft_mul_ifft<float, NY, 0, NY>(v, sb, t, twS, pS + f * NY);
+        fft_mul_ifft<float, NY, V, NY>(v, sb, t, twS, pS + f * NY);
         if (active) {
 #pragma unroll
             for (int m = 0; m < E; ++m) sb[pidx<float>(t + T * m)] = v[m];
@@ -654,7 +655,7 @@ __global__ void __launch_bounds__(NTH, MinBlocks<0>::value * kPassThreads / NTH)
         for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<float>(t + T * m)] : mk<C>(0.f, 0.f);
         if (s < nz) {
             __syncthreads();
-            fft_mul_ifft<float, NY, 0, NY>(v, sb, t, twS, pS + f * NY);
+            fft_mul_ifft<float, NY, V, NY>(v, sb, t, twS, pS + f * NY);
         }
         if (active) {
             C* col = d.field + size_t(f) * NY * nx + x;

@@ -14,6 +14,7 @@ namespace shg {
 
 bool has_col_step_small_f32(int n) { return n >= 8 && n <= 512; }
 bool has_col_step_wide_f32(int n) { return n == 512 || n == 1024; }
+bool has_col_step_v1_f32(int n) { return n == 64 || n == 128 || n == 256; }
 
 // v: the row flavour (0, 1, 3, 4) without the row-pass bits.
 cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, int nz, int s,
@@ -53,9 +54,18 @@ cudaError_t row_f32_step(int nx, int v, const void* descs, int ninst, int ny, in
 
 // v: 3 for 128-thread CTAs (lengths up to 512: half the columns per CTA), 5
 // for 512-thread CTAs (lengths 512 and 1024: twice the columns, so that a
-// warp reads whole 32-byte sectors of each row), else 256-thread CTAs.
+// warp reads whole 32-byte sectors of each row), 1 for the 8-element shape in
+// 256-thread CTAs (lengths 64 to 256: three CTAs per SM), else the 16-element
+// shape in 256-thread CTAs.
 cudaError_t col_f32_step(int ny, int v, const void* descs, int ninst, int nx, int nz, int s,
                          const void* tw, int hy, cudaStream_t st) {
+    if (v == 1) {
+        switch (ny) {
+#define X(n) case n: return col_step_launch<n, kPassThreads, 1>(descs, ninst, nx, nz, s, tw, hy, st);
+            SHG_F32_VARIANT_SIZES(X)
+#undef X
+        }
+    }
     if (v == 5) {
         switch (ny) {
             case 512: return col_step_launch<512, 512>(descs, ninst, nx, nz, s, tw, hy, st);
@@ -90,6 +100,10 @@ cudaError_t attr_f32_step() {
 #undef X
     if (e == cudaSuccess) e = col_step_attr<512, 512>();
     if (e == cudaSuccess) e = col_step_attr<1024, 512>();
+#define X(n) \
+    if (e == cudaSuccess) e = col_step_attr<n, kPassThreads, 1>();
+    SHG_F32_VARIANT_SIZES(X)
+#undef X
 #define X(n)                                                                           \
     if (e == cudaSuccess) e = row_attr<float, n, 1, true, kPassThreads, false, true>(); \
     if (e == cudaSuccess) e = row_attr<float, n, 0, true, 128, false, true>();          \

@@ -147,6 +147,7 @@ cudaError_t launch_col_step(int ny, const void* descs, int ninst, int nx, int nz
                             const void* tw, int hy, cudaStream_t st, int variant);
 bool has_col_step_small(int n);  // the column-layout pass in 128-thread CTAs (flavour 3)
 bool has_col_step_wide(int n);   // the column-layout pass in 512-thread CTAs (flavour 5)
+bool has_col_step_v1(int n);     // the column-layout pass in the 8-element shape (flavour 1)
 int col_tma_tile(bool fp64, int ny);
 bool has_fft_variant(bool fp64, int n);
 bool has_col_small(bool fp64, int n);  // row and column passes in 128/64-thread CTAs (flavours 3, 4)

@@ -100,11 +100,15 @@ def test_pass_times_report_the_step_kernels():
     assert 0.3 < g["col_ms"] / g["row_ms"] < 3
 
 
-def test_heat_deposits_agree_between_the_schedules(monkeypatch):
+@pytest.mark.parametrize("variant", [None, "1"])
+def test_heat_deposits_agree_between_the_schedules(variant, monkeypatch):
     """A THERMAL plan with a map deposits q_dot dV at every z_s in whichever
     layout the pass runs; the heat grid and eta agree with the two-pass
-    schedule (deposit order differs: float bins, double atomics)."""
+    schedule (deposit order differs: float bins, double atomics).  Variant
+    "1": both step passes in the 8-element shape."""
     import numpy as np
+    if variant is not None:
+        monkeypatch.setenv("SHG_FFT_VARIANT", variant)
     import paper_2410_04994_gb300 as pkg
     w = W.thermal_loop(n=128, nz=60, heat=(32, 24, 40), p1=100.0, n_outer=1)
     dT = np.asarray(W.depleted_absorbing(n=128, nz=60, tgrid=(12, 12, 20)).dT)
@@ -143,3 +147,15 @@ def test_column_layout_pass_in_512_thread_ctas(n, nz, monkeypatch):
     monkeypatch.setenv("SHG_CLUSTER", "0")
     monkeypatch.setenv("SHG_FFT_VARIANT", "5")
     _check(W.depleted_absorbing(n=n, nz=nz, tgrid=(9, 7, 3), p1=400.0))
+
+
+@pytest.mark.parametrize("n,nz", [(64, 6), (256, 5)])
+def test_column_layout_pass_in_the_8_element_shape(n, nz, monkeypatch):
+    """SHG_FFT_VARIANT=1 forces the 8-element shape for both step passes
+    (lengths 64 to 256; 256-thread CTAs, three per SM), which the tuner may
+    also pick; a rectangular grid takes it along y alone."""
+    monkeypatch.setenv("SHG_CLUSTER", "0")
+    monkeypatch.setenv("SHG_FFT_VARIANT", "1")
+    w = W.depleted_absorbing(n=n, nz=nz, tgrid=(9, 7, 4), p1=400.0)
+    _check(w)
+    _check(w.with_(nx=32, ny=n, lx=w.lx * 32 / n))
