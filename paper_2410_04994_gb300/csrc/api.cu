@@ -360,7 +360,7 @@ static void load_tune_cache() {
     if (!f) return;
     int fp64, n, pass, v;
     while (fscanf(f, "%d %d %d %d", &fp64, &n, &pass, &v) == 4)
-        if (v >= 0 && v <= 4) g_tuned.emplace(std::make_tuple(fp64 != 0, n, pass), v);
+        if (v >= 0 && v <= 5) g_tuned.emplace(std::make_tuple(fp64 != 0, n, pass), v);  // flavours 0-5
     fclose(f);
 }
 static void save_tune_decision(bool fp64, int n, int pass, int v) {
