@@ -747,37 +747,4 @@ __global__ void __launch_bounds__(kPassThreads, 2)
     }
 }
 
-// Per-point temperature table: the bilinear sample (dT, C) of map layer l at
-// field point (x, y), with the same cell arithmetic as the passes' node
-// sampler, stored per adjacent point pair as (dT_2j, dT_2j+1, C_2j, C_2j+1)
-// ([tz][ny][nx/2] float4).  grid = (ceil(nx / 256), ny, tz); block = 256.
-template <class R>
-SHG_D void upsample_point(const InstDesc<R>& d, cx<R>* __restrict__ out, int nx, int ny, int x,
-                          int y, int l) {
-    const MapView<R> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
-    TempSampler<R> ts;
-    make_sampler(d, mv, x, row_cell(d, y), ts);
-    const cx<R> v = ts.bil(l);
-    // pair layout: (dT_2j, dT_2j+1, C_2j, C_2j+1) at pair j = x / 2
-    R* o = reinterpret_cast<R*>(out) + ((size_t(l) * ny + y) * (nx / 2) + x / 2) * 4 + (x & 1);
-    o[0] = v.x;
-    o[2] = v.y;
-}
-
-template <class R>
-__global__ void k_upsample_map(const InstDesc<R>* __restrict__ dp, cx<R>* __restrict__ out,
-                               int nx, int ny) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    if (x < nx) upsample_point(*dp, out, nx, ny, x, blockIdx.y, blockIdx.z);
-}
-
-// The same for n plans of one grid: blockIdx.z = plan * tz + layer.
-template <class R>
-__global__ void k_upsample_map_batch(const InstDesc<R>* const* __restrict__ dps,
-                                     cx<R>* const* __restrict__ outs, int nx, int ny, int tz) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int k = blockIdx.z / tz, l = blockIdx.z - k * tz;
-    if (x < nx) upsample_point(*dps[k], outs[k], nx, ny, x, blockIdx.y, l);
-}
-
 }  // namespace shg

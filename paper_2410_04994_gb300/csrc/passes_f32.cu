@@ -110,22 +110,54 @@ cudaError_t col_f32(int ny, int v, const void* descs, int ninst, int nx, const v
     return cudaErrorInvalidValue;
 }
 
+// Per-point temperature table: the bilinear sample (dT, C) of map layer l at
+// field point (x, y), with the same cell arithmetic as the passes' node
+// sampler, stored per adjacent point pair as (dT_2j, dT_2j+1, C_2j, C_2j+1)
+// ([tz][ny][nx/2] float4, FP32).  One thread samples both points of pair j
+// and writes the entry with one 16-byte store.
+SHG_D void upsample_pair(const InstDesc<float>& d, float4* __restrict__ out, int nx, int ny, int j,
+                         int y, int l) {
+    const MapView<float> mv{d.ttab, d.tx, d.tx * d.ty, 0, 0, 0};
+    const RowCell<float> rc = row_cell(d, y);
+    TempSampler<float> s0, s1;
+    make_sampler(d, mv, 2 * j, rc, s0);
+    make_sampler(d, mv, 2 * j + 1, rc, s1);
+    const float2 a = s0.bil(l), b = s1.bil(l);
+    out[(size_t(l) * ny + y) * (nx / 2) + j] = make_float4(a.x, b.x, a.y, b.y);
+}
+
+// grid = (ceil(nx / 2 / kUpsThreads), ny, tz)
+constexpr int kUpsThreads = 128;
+__global__ void k_upsample_map(const InstDesc<float>* __restrict__ dp, float4* __restrict__ out,
+                               int nx, int ny) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j < nx / 2) upsample_pair(*dp, out, nx, ny, j, blockIdx.y, blockIdx.z);
+}
+
+// The same for n plans of one grid: blockIdx.z = plan * tz + layer.
+__global__ void k_upsample_map_batch(const InstDesc<float>* const* __restrict__ dps,
+                                     float4* const* __restrict__ outs, int nx, int ny, int tz) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    const int k = blockIdx.z / tz, l = blockIdx.z - k * tz;
+    if (j < nx / 2) upsample_pair(*dps[k], outs[k], nx, ny, j, blockIdx.y, l);
+}
+
 cudaError_t launch_upsample_map(const void* desc, void* umap, int nx, int ny, int tz,
                                 cudaStream_t st) {
     if (tz > 65535) return cudaErrorInvalidValue;
-    dim3 grid((nx + 255) / 256, ny, tz);
-    k_upsample_map<float><<<grid, 256, 0, st>>>(static_cast<const InstDesc<float>*>(desc),
-                                                static_cast<cx<float>*>(umap), nx, ny);
+    dim3 grid((nx / 2 + kUpsThreads - 1) / kUpsThreads, ny, tz);
+    k_upsample_map<<<grid, kUpsThreads, 0, st>>>(static_cast<const InstDesc<float>*>(desc),
+                                                static_cast<float4*>(umap), nx, ny);
     return cudaGetLastError();
 }
 
 cudaError_t launch_upsample_map_batch(const void* const* descs, void* const* umaps, int n, int nx,
                                       int ny, int tz, cudaStream_t st) {
     if (size_t(n) * tz > 65535) return cudaErrorInvalidValue;
-    dim3 grid((nx + 255) / 256, ny, n * tz);
-    k_upsample_map_batch<float><<<grid, 256, 0, st>>>(
+    dim3 grid((nx / 2 + kUpsThreads - 1) / kUpsThreads, ny, n * tz);
+    k_upsample_map_batch<<<grid, kUpsThreads, 0, st>>>(
         reinterpret_cast<const InstDesc<float>* const*>(descs),
-        reinterpret_cast<cx<float>* const*>(umaps), nx, ny, tz);
+        reinterpret_cast<float4* const*>(umaps), nx, ny, tz);
     return cudaGetLastError();
 }
 
