@@ -15,6 +15,7 @@ __global__ void __launch_bounds__(NTH, 2 * (kPassThreads / NTH))
     using C = cx<R>;
     using G = RowGeom<R, NX, 0, NTH>;
     constexpr int E = FftCfg<R, NX>::E, T = G::T, ROWS = G::ROWS, S = G::S;
+    constexpr bool WS = T <= 32;  // a row's threads share a warp (as in k_row_pass)
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ InstDesc<R> dsh;
     __shared__ StageZ<R> zsh[5];
@@ -53,9 +54,9 @@ __global__ void __launch_bounds__(NTH, 2 * (kPassThreads / NTH))
             C v[E];
 #pragma unroll
             for (int m = 0; m < E; ++m) v[m] = active ? sb[pidx<R>(t + T * m)] : mk<C>(R(0), R(0));
-            __syncthreads();
-            fft_mul_ifft<R, NX, 0, NX>(v, sb, t, twS, pS + f * NX);
-            __syncthreads();
+            group_sync<WS>();
+            fft_mul_ifft<R, NX, 0, NX, WS>(v, sb, t, twS, pS + f * NX);
+            group_sync<WS>();
 #pragma unroll
             for (int m = 0; m < E; ++m) sb[pidx<R>(t + T * m)] = v[m];
         }
